@@ -1,0 +1,379 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle, the tests and the bench.
+
+This module only *prepares inputs*: it builds sparse SPD matrices in CSR form and
+right-hand sides.  It holds none of the method's arithmetic (no block extraction,
+factorisation, preconditioner application, Lanczos or CG).  The paper generates
+"sparse, Hermitian, positive-definite matrices" of size N without saying how
+(Sec. 4.2, Sec. 5.1); the recipes below stand in for them and are stated
+precisely so both sides read bit-identical inputs.
+
+Conventions
+-----------
+* CSR arrays: ``row_ptr`` int32 [N+1], ``col`` int32 [nnz] (sorted, unique per row,
+  explicit diagonal), ``val`` float64 or float32 [nnz].
+* Grids are numbered lexicographically with x fastest: p = i + n*j + n*n*k.
+* Every random stream comes from ``numpy.random.default_rng(seed)``.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class CSR:
+    """A square sparse matrix in CSR form (host numpy arrays)."""
+
+    row_ptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.row_ptr.shape[0] - 1)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.shape[0])
+
+    def to_scipy(self):
+        import scipy.sparse as sp
+
+        return sp.csr_matrix((self.val, self.col, self.row_ptr), shape=(self.n, self.n))
+
+    def to_dense(self) -> np.ndarray:
+        d = np.zeros((self.n, self.n), dtype=np.float64)
+        rows = np.repeat(np.arange(self.n), np.diff(self.row_ptr))
+        d[rows, self.col] = self.val
+        return d
+
+
+def _csr_from_padded(cols: np.ndarray, vals: np.ndarray, mask: np.ndarray) -> CSR:
+    """Compress an (N, w) table of candidate entries (already column-sorted per row)."""
+    counts = mask.sum(axis=1)
+    row_ptr = np.zeros(cols.shape[0] + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    if row_ptr[-1] >= 2**31:
+        raise ValueError("nnz exceeds int32 indexing")
+    return CSR(row_ptr.astype(np.int32), cols[mask].astype(np.int32), vals[mask])
+
+
+def rhs(n: int, seed: int = 0) -> np.ndarray:
+    """b ~ N(0, 1) with ``default_rng(seed).standard_normal(n)`` (float64)."""
+    return np.random.default_rng(seed).standard_normal(n)
+
+
+# ---------------------------------------------------------------------------
+# 2D 5-point Poisson (small plain-method workload)
+# ---------------------------------------------------------------------------
+def poisson2d(n: int) -> CSR:
+    """5-point Laplacian on an n x n grid, Dirichlet boundary: 4 on the diagonal,
+    -1 for each grid neighbour.  nnz = 5 n^2 - 4 n."""
+    N = n * n
+    p = np.arange(N, dtype=np.int64)
+    i = p % n
+    j = p // n
+    cols = np.stack([p - n, p - 1, p, p + 1, p + n], axis=1)
+    mask = np.stack([j > 0, i > 0, np.ones(N, bool), i < n - 1, j < n - 1], axis=1)
+    vals = np.broadcast_to(np.array([-1.0, -1.0, 4.0, -1.0, -1.0]), (N, 5)).copy()
+    A = _csr_from_padded(cols, vals, mask)
+    A.meta = {"kind": "poisson2d", "n": n}
+    return A
+
+
+def poisson1d(n: int) -> CSR:
+    """tridiag(-1, 2, -1) of size n (Dirichlet 1D Laplacian)."""
+    p = np.arange(n, dtype=np.int64)
+    cols = np.stack([p - 1, p, p + 1], axis=1)
+    mask = np.stack([p > 0, np.ones(n, bool), p < n - 1], axis=1)
+    vals = np.broadcast_to(np.array([-1.0, 2.0, -1.0]), (n, 3)).copy()
+    A = _csr_from_padded(cols, vals, mask)
+    A.meta = {"kind": "poisson1d", "n": n}
+    return A
+
+
+# ---------------------------------------------------------------------------
+# 3D 7-point variable-coefficient diffusion
+# ---------------------------------------------------------------------------
+def diffusion3d_faces(n: int, sigma: float, seed: int = 1):
+    """Face coefficients c_f = exp(sigma * g), g ~ N(0,1) i.i.d., one per face including
+    the 6 n^2 boundary faces.  Drawn in the order cx, cy, cz from one stream.
+
+    cx[k, j, i], i in 0..n : face between cells (i-1, j, k) and (i, j, k) (i=0, n: boundary)
+    cy[k, j, i], j in 0..n : face between cells (i, j-1, k) and (i, j, k)
+    cz[k, j, i], k in 0..n : face between cells (i, j, k-1) and (i, j, k)
+    """
+    rng = np.random.default_rng(seed)
+    cx = np.exp(sigma * rng.standard_normal((n, n, n + 1)))
+    cy = np.exp(sigma * rng.standard_normal((n, n + 1, n)))
+    cz = np.exp(sigma * rng.standard_normal((n + 1, n, n)))
+    return cx, cy, cz
+
+
+def diffusion3d_from_faces(n: int, cx: np.ndarray, cy: np.ndarray, cz: np.ndarray) -> CSR:
+    """Assemble A from face coefficients: A_pq = -c_f for the face f shared by p and q,
+    A_pp = sum of the coefficients of all six faces of p (a Dirichlet boundary face adds
+    to the diagonal only).  nnz = 7 n^3 - 6 n^2."""
+    N = n ** 3
+    cxm = cx[:, :, :n].reshape(N)      # face on the x- side of each cell
+    cxp = cx[:, :, 1:].reshape(N)      # face on the x+ side
+    cym = cy[:, :n, :].reshape(N)
+    cyp = cy[:, 1:, :].reshape(N)
+    czm = cz[:n, :, :].reshape(N)
+    czp = cz[1:, :, :].reshape(N)
+    p = np.arange(N, dtype=np.int64)
+    i = p % n
+    j = (p // n) % n
+    k = p // (n * n)
+    diag = ((((cxm + cxp) + cym) + cyp) + czm) + czp
+    cols = np.stack([p - n * n, p - n, p - 1, p, p + 1, p + n, p + n * n], axis=1)
+    vals = np.stack([-czm, -cym, -cxm, diag, -cxp, -cyp, -czp], axis=1)
+    mask = np.stack([k > 0, j > 0, i > 0, np.ones(N, bool), i < n - 1, j < n - 1, k < n - 1], axis=1)
+    A = _csr_from_padded(cols, vals, mask)
+    A.meta = {"kind": "diffusion3d", "n": n}
+    return A
+
+
+def diffusion3d(n: int, sigma: float, seed: int = 1) -> CSR:
+    """3D 7-point variable-coefficient diffusion on an n^3 grid with log-normal face
+    coefficients (sigma); see ``diffusion3d_faces`` for the draw order."""
+    cx, cy, cz = diffusion3d_faces(n, sigma, seed)
+    A = diffusion3d_from_faces(n, cx, cy, cz)
+    A.meta.update({"sigma": sigma, "seed": seed})
+    return A
+
+
+def diffusion3d_face_grad(n: int, grad_val_fn) -> tuple:
+    """Chain rule of ``diffusion3d_from_faces``: given a function g(p, q) that returns
+    dL/dA_pq for arrays of (row, col) index pairs, return dL/dc for every face
+    (cx, cy, cz shapes).  Interior face between p and q: g(p,p)+g(q,q)-g(p,q)-g(q,p);
+    boundary face of p: g(p,p)."""
+    N = n ** 3
+    p = np.arange(N, dtype=np.int64).reshape(n, n, n)   # [k, j, i]
+    out = []
+    for axis, stride in ((2, 1), (1, n), (0, n * n)):
+        shape = [n, n, n]
+        shape[axis] += 1
+        g = np.zeros(shape)
+        # interior faces
+        sl_hi = [slice(None)] * 3
+        sl_lo = [slice(None)] * 3
+        sl_hi[axis] = slice(1, n)
+        sl_lo[axis] = slice(0, n - 1)
+        q_hi = p[tuple(sl_hi)].ravel()   # cell on the + side of the face
+        q_lo = p[tuple(sl_lo)].ravel()   # cell on the - side
+        gi = grad_val_fn(q_hi, q_hi) + grad_val_fn(q_lo, q_lo) - grad_val_fn(q_hi, q_lo) - grad_val_fn(q_lo, q_hi)
+        face_int = [slice(None)] * 3
+        face_int[axis] = slice(1, n)
+        g[tuple(face_int)] = gi.reshape(p[tuple(sl_hi)].shape)
+        # boundary faces (index 0 belongs to the first cell, index n to the last cell)
+        for fidx, cidx in ((0, 0), (n, n - 1)):
+            fsl = [slice(None)] * 3
+            fsl[axis] = slice(fidx, fidx + 1)
+            csl = [slice(None)] * 3
+            csl[axis] = slice(cidx, cidx + 1)
+            q = p[tuple(csl)].ravel()
+            g[tuple(fsl)] = grad_val_fn(q, q).reshape(p[tuple(csl)].shape)
+        out.append(g)
+    return tuple(out)
+
+
+# ---------------------------------------------------------------------------
+# Batched random-geometric-graph Laplacians
+# ---------------------------------------------------------------------------
+def morton30(pts: np.ndarray) -> np.ndarray:
+    """30-bit Morton code of points in [0,1)^3 (10 bits per axis, x in the lowest bit)."""
+    q = np.minimum((pts * 1024.0).astype(np.int64), 1023)
+    code = np.zeros(pts.shape[0], dtype=np.int64)
+    for b in range(10):
+        for d in range(3):
+            code |= ((q[:, d] >> b) & 1) << (3 * b + d)
+    return code
+
+
+def rgg_laplacian(points: np.ndarray, shift: float = 1e-3) -> CSR:
+    """Unweighted graph Laplacian of the random geometric graph with radius
+    r = (9 / (pi N))^(1/3) (12 expected neighbours in the interior), nodes ordered by
+    30-bit Morton code, plus shift * I."""
+    from scipy.spatial import cKDTree
+    import scipy.sparse as sp
+
+    N = points.shape[0]
+    order = np.argsort(morton30(points), kind="stable")
+    pts = points[order]
+    r = (9.0 / (math.pi * N)) ** (1.0 / 3.0)
+    pairs = cKDTree(pts).query_pairs(r, output_type="ndarray")
+    i = np.concatenate([pairs[:, 0], pairs[:, 1]])
+    j = np.concatenate([pairs[:, 1], pairs[:, 0]])
+    adj = sp.csr_matrix((np.ones(i.shape[0]), (i, j)), shape=(N, N))
+    deg = np.asarray(adj.sum(axis=1)).ravel()
+    L = (sp.diags(deg + shift) - adj).tocsr()
+    L.sort_indices()
+    A = CSR(L.indptr.astype(np.int32), L.indices.astype(np.int32), L.data.astype(np.float64))
+    A.meta = {"kind": "rgg", "n": N}
+    return A
+
+
+@dataclass
+class Batch:
+    """Concatenated CSR of independent systems.  System s owns rows
+    [sys_row[s], sys_row[s+1]) and nnz [sys_nnz[s], sys_nnz[s+1]); its column indices
+    are local (0 .. N_s-1)."""
+
+    row_ptr: np.ndarray   # int32 [sum N_s + 1], global nnz offsets
+    col: np.ndarray       # int32 [sum nnz_s], local column indices
+    val: np.ndarray       # float64
+    sys_row: np.ndarray   # int64 [n_sys + 1]
+    sys_nnz: np.ndarray   # int64 [n_sys + 1]
+    bs: np.ndarray        # int32 [n_sys]
+    systems: list         # list of CSR (host views)
+
+    @property
+    def n_sys(self) -> int:
+        return len(self.systems)
+
+
+def concat_batch(systems: list, bss) -> Batch:
+    n_sys = len(systems)
+    sys_row = np.zeros(n_sys + 1, dtype=np.int64)
+    sys_nnz = np.zeros(n_sys + 1, dtype=np.int64)
+    for s, A in enumerate(systems):
+        sys_row[s + 1] = sys_row[s] + A.n
+        sys_nnz[s + 1] = sys_nnz[s] + A.nnz
+    row_ptr = np.empty(sys_row[-1] + 1, dtype=np.int64)
+    for s, A in enumerate(systems):
+        row_ptr[sys_row[s]:sys_row[s + 1]] = A.row_ptr[:-1].astype(np.int64) + sys_nnz[s]
+    row_ptr[-1] = sys_nnz[-1]
+    if sys_nnz[-1] >= 2**31:
+        raise ValueError("batched nnz exceeds int32 indexing")
+    col = np.concatenate([A.col for A in systems]).astype(np.int32)
+    val = np.concatenate([A.val.astype(np.float64) for A in systems])
+    return Batch(row_ptr.astype(np.int32), col, val, sys_row, sys_nnz,
+                 np.asarray(bss, dtype=np.int32), systems)
+
+
+def rgg_batch(n_sys: int = 512, seed: int = 3, n_min: float = 1e3, n_max: float = 2e5,
+              block_sizes=(4, 8, 16, 32, 64)) -> Batch:
+    """Independent RGG-Laplacian systems: N_s = floor(exp(U(ln n_min, ln n_max))),
+    per-system block size uniform over ``block_sizes``, points U[0,1]^3; one stream
+    draws sizes, then block sizes, then each system's points in order."""
+    rng = np.random.default_rng(seed)
+    sizes = np.floor(np.exp(rng.uniform(math.log(n_min), math.log(n_max), n_sys))).astype(np.int64)
+    bss = rng.choice(np.asarray(block_sizes), n_sys)
+    systems = [rgg_laplacian(rng.random((int(N), 3))) for N in sizes]
+    return concat_batch(systems, bss)
+
+
+# ---------------------------------------------------------------------------
+# Large power-law SPD
+# ---------------------------------------------------------------------------
+def _powerlaw_exponent(w_min: int, w_max: int, mean: float) -> float:
+    w = np.arange(w_min, w_max + 1, dtype=np.float64)
+
+    def m(g):
+        p = w ** (-g)
+        return float((w * p).sum() / p.sum())
+
+    lo, hi = 0.0, 10.0   # mean decreases with the exponent
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if m(mid) > mean:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def powerlaw_spd(n: int = 8_000_000, seed: int = 5, w_min: int = 8, w_max: int = 1999,
+                 mean_deg: float = 31.0, cap: int = 2000, rcm: bool = True,
+                 dtype=np.float32) -> CSR:
+    """Random sparse SPD with power-law row lengths.
+
+    Expected off-diagonal degrees w_i follow a discrete power law on [w_min, w_max]
+    whose exponent gives mean ``mean_deg``; edges are drawn Chung-Lu style (both ends
+    proportional to w, sum(w)/2 draws), symmetrised, de-duplicated, self loops removed,
+    and rows are capped at ``cap`` entries including the diagonal.  Off-diagonal values
+    U(-1, 0) (rounded to float32), diagonal = sum |off| + 1e-2 formed from the rounded
+    off-diagonals and then rounded.  Rows are reverse-Cuthill-McKee reordered."""
+    import scipy.sparse as sp
+
+    rng = np.random.default_rng(seed)
+    g = _powerlaw_exponent(w_min, w_max, mean_deg)
+    support = np.arange(w_min, w_max + 1, dtype=np.float64)
+    pw = support ** (-g)
+    pw /= pw.sum()
+    w = rng.choice(support, size=n, p=pw)
+    n_draw = int(round(w.sum() / 2.0))
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    u = rng.random(n_draw)
+    a = np.searchsorted(cdf, u, side="right").astype(np.int64)
+    del u
+    u = rng.random(n_draw)
+    b = np.searchsorted(cdf, u, side="right").astype(np.int64)
+    del u
+    np.minimum(a, n - 1, out=a)
+    np.minimum(b, n - 1, out=b)
+    keep = a != b
+    lo = np.minimum(a[keep], b[keep])
+    hi = np.maximum(a[keep], b[keep])
+    del a, b, keep
+    key = np.unique(lo * n + hi)
+    del lo, hi
+    lo = key // n
+    hi = key % n
+    del key
+    # cap: drop an undirected edge if it falls beyond the (cap-1)-th entry of either end
+    deg_cap = cap - 1
+    ends = np.concatenate([lo, hi])
+    order = np.argsort(ends, kind="stable")
+    counts = np.bincount(ends, minlength=n)
+    starts = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=starts[1:])
+    rank = np.empty_like(order)
+    rank[order] = np.arange(order.shape[0]) - np.repeat(starts[:-1], counts)
+    m_e = lo.shape[0]
+    ok = (rank[:m_e] < deg_cap) & (rank[m_e:] < deg_cap)
+    del ends, order, rank, counts, starts
+    lo = lo[ok]
+    hi = hi[ok]
+    offv = (-rng.random(lo.shape[0])).astype(np.float32)
+    rows = np.concatenate([lo, hi])
+    cols = np.concatenate([hi, lo])
+    vals = np.concatenate([offv, offv])
+    del lo, hi, offv
+    absum = np.bincount(rows, weights=np.abs(vals.astype(np.float64)), minlength=n)
+    diag = (absum + 1e-2).astype(np.float32)
+    rows = np.concatenate([rows, np.arange(n, dtype=np.int64)])
+    cols = np.concatenate([cols, np.arange(n, dtype=np.int64)])
+    vals = np.concatenate([vals, diag])
+    M = sp.csr_matrix((vals, (rows.astype(np.int32), cols.astype(np.int32))), shape=(n, n), dtype=np.float32)
+    del rows, cols, vals
+    if rcm:
+        from scipy.sparse.csgraph import reverse_cuthill_mckee
+
+        perm = reverse_cuthill_mckee(M, symmetric_mode=True)
+        M = M[perm][:, perm].tocsr()
+    M.sort_indices()
+    A = CSR(M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data.astype(dtype))
+    A.meta = {"kind": "powerlaw", "n": n, "exponent": g, "seed": seed}
+    return A
+
+
+# ---------------------------------------------------------------------------
+# Named workloads
+# ---------------------------------------------------------------------------
+def workload(name: str):
+    """Named synthetic workloads: returns (A, b)."""
+    if name == "poisson2d_64":
+        A = poisson2d(64)
+    elif name.startswith("diffusion3d_"):
+        # diffusion3d_<n>_s<sigma>
+        parts = name.split("_")
+        A = diffusion3d(int(parts[1]), float(parts[2][1:]))
+    else:
+        raise KeyError(name)
+    return A, rhs(A.n, 0)
