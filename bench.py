@@ -1,0 +1,409 @@
+"""Benchmark: block-Jacobi PCG to relative residual 1e-10 on the 3D variable-coefficient
+diffusion workload (128^3 grid, 7-point stencil, log-normal face coefficients with
+sigma = 2, b ~ N(0,1) seed 0), mixed precision (FP32 block factors, FP64 CG) against
+all-FP64.
+
+One step = pcg_solve through the C ABI: block extraction + batched block Cholesky/inverse
+(setup) and the persistent CG solve to ||r||/||b|| <= 1e-10 with the true-residual check.
+
+value   = algorithmic bytes of the step / step time (GB/s), inputs resident in HBM.
+          bytes = setup (CSR read + factor writes) + per-solve extras (initial and final
+          residual, final x update) + iterations * B_it, where
+          B_it = CSR (val+col+row_ptr) + M^{-1} factor + 11 vector streams of 8N bytes.
+e2e     = the same metric through the C ABI with host buffers: the CSR and b are copied
+          from pinned host memory to the device and x back inside the timed region.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank solves its own replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2410_02408_gb300 import workloads as W  # noqa: E402
+
+METRIC = "PCG+precond GB/s (% HBM peak), mixed vs FP64, to rel. residual 1e-10"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=128, help="grid points per axis")
+    ap.add_argument("--sigma", type=float, default=2.0)
+    ap.add_argument("--bs", type=int, default=32)
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "tf32"])
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--maxit", type=int, default=200000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample-iters", type=int, default=0, help="oracle CG iterations per sample (0 = auto)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- byte accounting
+def csr_bytes(n, nnz, val_bytes):
+    return val_bytes * nnz + 4 * nnz + 4 * (n + 1)
+
+
+def layout_units(n, bs):
+    if bs <= 32:
+        U = (32 // bs) * bs
+        S = 1
+    else:
+        U = bs
+        S = 2
+    return (n + U - 1) // U, S
+
+
+def factor_bytes(n, bs, fac_bytes):
+    units, S = layout_units(n, bs)
+    minv = units * (bs // 2 + 1) * S * 32 * fac_bytes
+    linv = units * bs * S * 32 * fac_bytes
+    return minv, linv
+
+
+def step_bytes(n, nnz, bs, prec, iters, val_bytes=8):
+    fb = 4 if prec != "fp64" else 8
+    C = csr_bytes(n, nnz, val_bytes)
+    Fm, Fl = factor_bytes(n, bs, fb)
+    v = 8 * n
+    b_it = C + Fm + 11 * v
+    setup = C + Fm + Fl
+    extras = 2 * C + Fm + 13 * v
+    return setup + extras + iters * b_it, b_it, iters * b_it + extras
+
+
+# ---------------------------------------------------------------- environment helpers
+def measured_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        except Exception:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2410_02408_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(fn.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(bs, prec):
+    """DRAM bytes per CG iteration of the persistent kernel from the committed ncu summary,
+    or None if absent or if the kernel sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "pcg_kernel_diffusion3d_128.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_source_hash:\s*(\w+)", txt)
+    if not m or m.group(1) != kernel_source_hash():
+        return None
+    m = re.search(rf"dram_bytes_per_iteration\[bs={bs},prec={prec}\]:\s*([0-9.eE+]+)", txt)
+    return float(m.group(1)) if m else None
+
+
+# ---------------------------------------------------------------- distributed plumbing
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, None
+    import torch
+    import torch.distributed as dist
+
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    dist.init_process_group(backend=backend)
+    return dist.get_rank(), ws, dist
+
+
+def max_over_ranks(v, dist):
+    if dist is None:
+        return v
+    import torch
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- oracle (CPU) timing
+def oracle_sample(A, b, bs, sample_iters):
+    """Oracle setup + a bounded number of CG iterations on the full matrix (single thread)."""
+    import oracle
+
+    t0 = time.perf_counter()
+    L, f = oracle.factor(A, bs)
+    t1 = time.perf_counter()
+    r = oracle.pcg(A, b, bs, 1e-10, max_iter=sample_iters, L=L)
+    t2 = time.perf_counter()
+    it = r["iterations"]
+    setup_b = csr_bytes(A.n, A.nnz, 8) + factor_bytes(A.n, bs, 8)[0] + factor_bytes(A.n, bs, 8)[1]
+    _, b_it, _ = step_bytes(A.n, A.nnz, bs, "fp64", 0)
+    byt = setup_b + it * b_it
+    return byt / (t2 - t0) / 1e9, {"setup_s": t1 - t0, "cg_s": t2 - t1, "iterations": it}
+
+
+def run_reference(args):
+    rank, ws, dist = dist_init()
+    if rank != 0:
+        return
+    A = W.diffusion3d(args.n, args.sigma)
+    b = W.rhs(A.n, 0)
+    iters = args.cpu_sample_iters or 8
+    vals = []
+    for s in range(args.warmup + args.steps):
+        v, meta = oracle_sample(A, b, args.bs, iters)
+        if s >= args.warmup:
+            vals.append(v)
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"diffusion3d_{args.n}_sigma{args.sigma:g}", "n": A.n, "nnz": A.nnz,
+                   "block_size": args.bs, "prec": "fp64"},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"oracle setup + {iters} CG iterations on the full matrix per step"},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import torch
+
+    rank, ws, dist = dist_init()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    import paper_2410_02408_gb300 as pc
+
+    pc.load()
+    A = W.diffusion3d(args.n, args.sigma)
+    b = W.rhs(A.n, 0)
+    Ad = pc.csr(A)
+    bd = torch.from_numpy(b).cuda()
+    n, nnz = A.n, A.nnz
+
+    def solve(prec):
+        x, info = pc.pcg(Ad, bd, args.bs, tol=args.tol, max_iter=args.maxit, prec=prec)
+        return x, info
+
+    for _ in range(args.warmup):
+        x, info = solve(args.prec)
+    torch.cuda.synchronize()
+    barrier(dist)
+    st = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    infos = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        barrier(dist)
+        e0.record(st)
+        for _ in range(args.steps):
+            x, info = solve(args.prec)
+            infos.append(info)
+        e1.record(st)
+        torch.cuda.synchronize()
+        barrier(dist)
+    ms_total = e0.elapsed_time(e1)
+    ms_total = max_over_ranks(ms_total, dist)
+    ms_step = ms_total / args.steps
+    iters = infos[-1]["iterations"]
+    total_bytes = 0
+    for inf in infos:
+        sb, b_it, kb = step_bytes(n, nnz, args.bs, args.prec, inf["iterations"])
+        total_bytes += sb
+    value = total_bytes * ws / (ms_total / 1e3) / 1e9
+    # dominant kernel: the persistent CG kernel (one launch per step), CUDA-event timed
+    kern_ms = statistics.mean(i["solve_ms"] for i in infos)
+    _, b_it, kern_bytes = step_bytes(n, nnz, args.bs, args.prec, iters)
+    peak, peak_kind = measured_hbm()
+    achieved = kern_bytes / (kern_ms / 1e3) / 1e9
+    traffic_it = profiled_traffic(args.bs, args.prec)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": (traffic_it * iters if traffic_it is not None else None),
+                "peak_kind": peak_kind, "kernel": "pcg_kernel (persistent, one launch per solve)",
+                "algorithmic_bytes_per_iteration": b_it}
+    xr = x.cpu().numpy()
+    true_res = float(np.linalg.norm(b - A.to_scipy() @ xr) / np.linalg.norm(b))   # report only
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"diffusion3d_{args.n}_sigma{args.sigma:g}", "n": n, "nnz": nnz,
+                   "block_size": args.bs, "prec": "mixed (fp32 factors, fp64 CG)" if args.prec != "fp64" else "fp64",
+                   "tol": args.tol, "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (CSR %.0f MB + factor)" % (csr_bytes(n, nnz, 8) / 1e6)},
+        "iterations": iters, "true_rel_residual": true_res,
+        "setup_ms": statistics.mean(i["setup_ms"] for i in infos), "solve_ms": kern_ms,
+        "frac_of_hbm_peak": value / peak,
+        "roofline": roofline,
+        "gpu_launches": 3 * args.steps,
+    }
+    line["clocks"] = clk.summary()
+
+    if rank == 0 and not args.no_fp64_compare and args.prec != "fp64":
+        torch.cuda.synchronize()
+        solve("fp64")
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(st)
+        reps = 2
+        finf = []
+        for _ in range(reps):
+            _, fi = solve("fp64")
+            finf.append(fi)
+        t1.record(st)
+        torch.cuda.synchronize()
+        fms = t0.elapsed_time(t1) / reps
+        fb = sum(step_bytes(n, nnz, args.bs, "fp64", fi["iterations"])[0] for fi in finf) / reps
+        line["fp64"] = {"value": fb / (fms / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": fms,
+                        "iterations": finf[-1]["iterations"], "solve_ms": finf[-1]["solve_ms"],
+                        "setup_ms": finf[-1]["setup_ms"]}
+        line["mixed_speedup_vs_fp64"] = fms / ms_step
+
+    if not args.no_e2e:
+        # end to end through the C ABI from pinned host buffers
+        hrp = torch.from_numpy(A.row_ptr).pin_memory()
+        hci = torch.from_numpy(A.col).pin_memory()
+        hva = torch.from_numpy(A.val).pin_memory()
+        hb = torch.from_numpy(b).pin_memory()
+        hx = torch.empty(n, dtype=torch.float64).pin_memory()
+        drp = torch.empty_like(hrp, device="cuda")
+        dci = torch.empty_like(hci, device="cuda")
+        dva = torch.empty_like(hva, device="cuda")
+        db = torch.empty_like(hb, device="cuda")
+        h2d = sum(t.numel() * t.element_size() for t in (hrp, hci, hva, hb))
+        d2h = hx.numel() * hx.element_size()
+        torch.cuda.synchronize()
+        barrier(dist)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(st)
+        eb = 0
+        ksteps = max(1, min(args.steps, 3))
+        for _ in range(ksteps):
+            drp.copy_(hrp, non_blocking=True)
+            dci.copy_(hci, non_blocking=True)
+            dva.copy_(hva, non_blocking=True)
+            db.copy_(hb, non_blocking=True)
+            xd, ei = pc.pcg(pc.CSR(drp, dci, dva), db, args.bs, tol=args.tol, max_iter=args.maxit, prec=args.prec)
+            hx.copy_(xd, non_blocking=True)
+            eb += step_bytes(n, nnz, args.bs, args.prec, ei["iterations"])[0]
+        t1.record(st)
+        torch.cuda.synchronize()
+        ems = max_over_ranks(t0.elapsed_time(t1), dist)
+        line["e2e"] = {"value": eb * ws / (ems / 1e3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h, "ms_per_step": ems / ksteps}
+
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        sample = args.cpu_sample_iters or 8
+        v, meta = oracle_sample(A, b, args.bs, sample)
+        line["cpu_baseline"] = {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                                "sample": f"oracle FP64 setup + {meta['iterations']} CG iterations on the full "
+                                          f"matrix ({meta['setup_s'] + meta['cg_s']:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

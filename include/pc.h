@@ -1,0 +1,242 @@
+/*
+ * pc.h - C ABI of libpc: GB300-native block-Jacobi preconditioning, Lanczos condition
+ * number estimation and preconditioned CG for sparse SPD systems A x = b.
+ *
+ * What the paper defines (arXiv 2410.02408):
+ *   Sec. 3.1  A is sparse, Hermitian (here: real symmetric) positive definite; the cost
+ *             driver is kappa(A) = ||A|| ||A^{-1}|| (= lambda_max / lambda_min for SPD).
+ *   Sec. 3.2  A and b are partitioned into contiguous diagonal blocks A_1..A_k of size nb.
+ *   Sec. 3.3  each block is preconditioned (point Jacobi M_i = diag(A_i)^{-1} in the
+ *             paper; here the full block, M = blockdiag(A_kk) = blockdiag(L_k L_k^T), which
+ *             equals the paper's preconditioner at block_size 1).
+ *   Sec. 3.6  block solutions are concatenated (z = M^{-1} r writes disjoint slices).
+ *   Sec. 3.7  accuracy is the relative residual ||A x - b|| / ||b||.
+ *
+ * Conventions for every entry point:
+ *   - All array arguments are DEVICE pointers owned by the caller, unless stated.  They
+ *     are read (or written) during the call only; nothing is retained, except that a
+ *     pc_handle keeps the CSR pointers given to pc_setup and reads them in later
+ *     pc_apply / pcg_solve_h calls, so the caller keeps that CSR alive and unchanged
+ *     until pc_destroy.
+ *   - Handles and their workspaces are owned by the library: created by pc_setup,
+ *     released by pc_destroy.
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default stream).  Work is
+ *     enqueued on it; calls that report a device-side status (setup, solve, kappa)
+ *     synchronise the stream before returning.
+ *   - No call aborts, prints or traps.  Every failure is a pc_status; details are in the
+ *     info structs.  Device-side waits are bounded (PC_ERR_TIMEOUT).
+ *   - CSR: square, int32 indices, column indices sorted and unique in each row, explicit
+ *     diagonal.  n < 2^31, nnz < 2^31.
+ *   - Block partition: block k covers rows [k*bs, min(n, (k+1)*bs)); the last block may
+ *     be shorter and is padded with the identity internally (the result is unchanged).
+ *     1 <= block_size <= 64.
+ */
+#ifndef PC_H_
+#define PC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PC_OK = 0,
+  PC_ERR_INVALID_ARG = 1,    /* bad size, pointer, block size, mode or precision      */
+  PC_ERR_NOT_SPD = 2,        /* a block's Cholesky pivot <= tol * max diag of the block */
+  PC_ERR_BREAKDOWN = 3,      /* CG: p.q <= 0, r.z <= 0 or a non-finite scalar          */
+  PC_ERR_NO_CONVERGENCE = 4, /* max_iter reached (x holds the last iterate)            */
+  PC_ERR_TIMEOUT = 5,        /* a bounded device-side wait gave up                    */
+  PC_ERR_CUDA = 6,           /* a CUDA runtime call failed                            */
+  PC_ERR_OOM = 7             /* device allocation failed                              */
+} pc_status;
+
+typedef enum { PC_F64 = 0, PC_F32 = 1 } pc_dtype; /* type of the CSR values */
+
+/* Precision of the block factors and of their application.  PC_PREC_FP64: factor and
+ * apply in FP64.  PC_PREC_FP32: factor and apply in FP32 (FP32 accumulation); CG vectors,
+ * residual update, dot products and scalars stay FP64, so the outer FP64 CG is the
+ * iterative refinement that recovers full accuracy.  PC_PREC_TF32 is accepted as the
+ * FP32 path (same arithmetic). */
+typedef enum { PC_PREC_FP64 = 0, PC_PREC_FP32 = 1, PC_PREC_TF32 = 2 } pc_prec;
+
+/* pc_apply modes (L_k is the Cholesky factor of the diagonal block A_kk):
+ *   INV   : out = M^{-1} in = L^{-T} L^{-1} in          (the PCG preconditioner)
+ *   SYM   : out = L^{-1} A L^{-T} in                    (symmetric preconditioned operator;
+ *                                                        same spectrum as M^{-1} A)
+ *   LINV  : out = L^{-1} in
+ *   LTINV : out = L^{-T} in                                                            */
+typedef enum { PC_APPLY_INV = 0, PC_APPLY_SYM = 1, PC_APPLY_LINV = 2, PC_APPLY_LTINV = 3 } pc_apply_mode;
+
+typedef struct {
+  int64_t n;               /* rows = columns                                  */
+  int64_t nnz;             /* stored entries                                  */
+  const int32_t *row_ptr;  /* device [n+1], row_ptr[0] = 0, row_ptr[n] = nnz */
+  const int32_t *col_idx;  /* device [nnz]                                    */
+  const void *val;         /* device [nnz], double (PC_F64) or float (PC_F32) */
+  int32_t dtype;           /* pc_dtype                                        */
+} pc_csr;
+
+typedef struct pc_handle pc_handle; /* opaque, library-owned */
+
+typedef struct {
+  int32_t status;            /* same value the call returns                           */
+  int32_t iterations;        /* CG iterations (matrix-vector products with p)         */
+  int32_t restarts;          /* true-residual restarts taken                          */
+  int32_t failed_block;      /* PC_ERR_NOT_SPD: first failing block index, else -1    */
+  double rel_residual;       /* recurrence ||r|| / ||b|| at exit                      */
+  double true_rel_residual;  /* ||b - A x|| / ||b|| recomputed at exit                */
+  double setup_ms;           /* pc_setup time inside pcg_solve (0 for pcg_solve_h)    */
+  double solve_ms;           /* CG kernel time (CUDA events on the stream)            */
+  int32_t grid_ctas;         /* CTAs of the persistent CG launch                      */
+  int32_t block_size;
+  int32_t prec;              /* pc_prec used                                          */
+  int32_t reserved;
+} pc_solve_info;
+
+typedef struct {
+  int32_t status;
+  int32_t steps;         /* Lanczos steps taken (<= max_steps)              */
+  double kappa;          /* theta_max / theta_min of the Lanczos tridiagonal */
+  double lambda_min;     /* theta_min                                      */
+  double lambda_max;     /* theta_max                                      */
+  double *alpha;         /* optional HOST array [max_steps] (caller-owned) receiving the
+                            tridiagonal's diagonal, or NULL                  */
+  double *beta;          /* optional HOST array [max_steps]: beta[j] = ||w_j|| after step
+                            j (the off-diagonal for j < steps-1), or NULL     */
+  double elapsed_ms;
+} pc_kappa_info;
+
+/* ---------------------------------------------------------------------------------
+ * pc_setup - build the block-Jacobi preconditioner (Sec. 3.2-3.3): extract the diagonal
+ * blocks A_kk from CSR and factor each one, A_kk = L_k L_k^T, storing L_k^{-1} and
+ * M_k^{-1} = L_k^{-T} L_k^{-1} on the device.
+ *   A          CSR (device arrays; kept by the handle, see conventions).
+ *   block_size 1..64.
+ *   tol        pivot threshold: a pivot <= tol * max_i (A_kk)_ii fails (PC_ERR_NOT_SPD).
+ *   prec       pc_prec.
+ *   out        receives the new handle (NULL on failure, except PC_ERR_NOT_SPD, where
+ *              the handle is still returned so that pc_handle_failed_block can be read;
+ *              destroy it with pc_destroy).
+ */
+pc_status pc_setup(const pc_csr *A, int32_t block_size, double tol, int32_t prec, void *stream,
+                   pc_handle **out);
+
+/* First failing block of the last pc_setup on h (-1 if none). */
+int64_t pc_handle_failed_block(const pc_handle *h);
+
+/* pc_apply - out = op(in) for op in pc_apply_mode; in and out are device [n] doubles and
+ * must not overlap.  Stream-ordered, does not synchronise. */
+pc_status pc_apply(pc_handle *h, int32_t mode, const double *in, double *out, void *stream);
+
+/* pc_get_factor - copy the stored factor of h into dense row-major blocks
+ * out[k][i][j] (device, nblocks * bs * bs doubles): which = 0 gives L_k^{-1} (lower
+ * triangular), which = 1 gives M_k^{-1}.  Padding rows/columns of the last block are
+ * written as the identity. */
+pc_status pc_get_factor(const pc_handle *h, int32_t which, double *out, void *stream);
+
+/* pc_destroy - free the handle and its device workspace (synchronises nothing; the
+ * caller must not have work using h still in flight). */
+pc_status pc_destroy(pc_handle *h);
+
+/* pc_extract_blocks - the diagonal blocks of the partition (Sec. 3.2) as dense row-major
+ * tiles out[k][i][j] = A(k*bs+i, k*bs+j) (0 where not stored or beyond n), device
+ * nblocks * bs * bs doubles.  Values are copied bit-exactly (float values are widened). */
+pc_status pc_extract_blocks(const pc_csr *A, int32_t block_size, double *out, void *stream);
+
+/* pc_spmv - y = A x (device [n] doubles). */
+pc_status pc_spmv(const pc_csr *A, const double *x, double *y, void *stream);
+
+/* pc_dot - *result = x . y (device scalar), fixed-order reduction (bit-reproducible). */
+pc_status pc_dot(int64_t n, const double *x, const double *y, double *result, void *stream);
+
+/* ---------------------------------------------------------------------------------
+ * kappa_estimate - Lanczos estimate of kappa (Sec. 3.1) for A (block_size == 0) or for
+ * the block-Jacobi preconditioned operator L^{-1} A L^{-T} (block_size > 0, FP64
+ * factors), whose spectrum is that of M^{-1} A.
+ *   max_steps  Lanczos steps m (<= 256).
+ *   tol        early stop when beta_j <= tol * max(|alpha|, |beta|) so far.
+ *   v0         device [n] start vector (q_1 = v0/||v0||, or L^{-1} v0 / ||L^{-1} v0||
+ *              when preconditioned); must be non-zero.
+ *   reorth     0: plain three-term recurrence; 1: full reorthogonalisation against all
+ *              previous Lanczos vectors, classical Gram-Schmidt applied twice.
+ * The extreme Ritz values are found by Sturm-count bisection in FP64 on the device.
+ * Workspace (max_steps * n doubles for the basis) is allocated and freed by the call. */
+pc_status kappa_estimate(const pc_csr *A, int32_t block_size, int32_t max_steps, double tol,
+                         const double *v0, int32_t reorth, pc_kappa_info *info, void *stream);
+
+/* Same on an existing handle (any precision; NULL handle = unpreconditioned, then A is
+ * taken from the csr argument). */
+pc_status kappa_estimate_h(pc_handle *h, const pc_csr *A, int32_t max_steps, double tol,
+                           const double *v0, int32_t reorth, pc_kappa_info *info, void *stream);
+
+/* ---------------------------------------------------------------------------------
+ * pcg_solve - solve A x = b by block-Jacobi preconditioned CG until the recurrence
+ * residual satisfies ||r|| <= tol ||b|| (Sec. 3.7), then recompute b - A x; if that is
+ * above tol, restart from x (at most 3 times).  The whole iteration runs in one
+ * persistent cooperative kernel (two reductions and one plain grid barrier per step).
+ *   x    device [n]: in = initial guess x0, out = solution (last iterate on failure).
+ *   prec pc_prec of the preconditioner; CG itself is FP64.
+ * pcg_solve builds (and frees) the preconditioner; pcg_solve_h reuses a handle. */
+pc_status pcg_solve(const pc_csr *A, int32_t block_size, const double *b, double *x, double tol,
+                    int32_t max_iter, int32_t prec, pc_solve_info *info, void *stream);
+
+pc_status pcg_solve_h(pc_handle *h, const double *b, double *x, double tol, int32_t max_iter,
+                      pc_solve_info *info, void *stream);
+
+/* pc_grad_val - adjoint of x = A^{-1} b with respect to the stored entries of A:
+ * grad_val[e] = -lambda[row(e)] * x[col(e)] for every stored entry e, where lambda solves
+ * A^T lambda = dL/dx (A symmetric here).  Device arrays: lambda, x [n]; grad_val [nnz]. */
+pc_status pc_grad_val(const pc_csr *A, const double *lambda, const double *x, double *grad_val,
+                      void *stream);
+
+/* ---------------------------------------------------------------------------------
+ * Batched mode: many independent SPD systems of uneven size, each with its own block
+ * size, set up and solved in ONE persistent launch (each system is owned by one
+ * thread-block cluster; cluster barriers replace grid barriers).
+ *   n_sys          number of systems.
+ *   sys_row        device int64 [n_sys+1]: system s owns rows [sys_row[s], sys_row[s+1])
+ *                  of the concatenated CSR; row_ptr holds global nnz offsets.
+ *   col_idx        LOCAL column indices (0 .. N_s - 1) of each system.
+ *   block_size     device int32 [n_sys], each 1..64.
+ *   b, x           device [total rows]; x is overwritten (x0 = 0).
+ *   iters, status  device int32 [n_sys] outputs; relres device double [n_sys] outputs
+ *                  (true relative residual per system).
+ * Returns PC_OK if every system converged, else the first non-OK status. */
+typedef struct {
+  int32_t n_sys;
+  int64_t n_rows;           /* total rows */
+  int64_t nnz;              /* total nnz  */
+  const int64_t *sys_row;   /* device [n_sys+1] */
+  const int32_t *row_ptr;   /* device [n_rows+1] */
+  const int32_t *col_idx;   /* device [nnz], local */
+  const double *val;        /* device [nnz] */
+  const int32_t *block_size;/* device [n_sys] */
+  int32_t max_block_size;   /* host: max over block_size (<= 64) */
+} pc_batch;
+
+pc_status pcg_solve_batched(const pc_batch *B, const double *b, double *x, double tol,
+                            int32_t max_iter, int32_t prec, int32_t *iters, int32_t *status,
+                            double *relres, pc_solve_info *info, void *stream);
+
+/* ---------------------------------------------------------------------------------
+ * Library options and diagnostics. */
+
+/* Cycle budget of every bounded device-side wait (grid barrier spin).  <= 0 restores the
+ * default (about 4e9 cycles).  Process-wide; not thread-safe against concurrent calls. */
+void pc_set_wait_budget(int64_t cycles);
+
+/* Number of CTAs per SM used by the persistent CG kernel (0 = occupancy maximum). */
+void pc_set_ctas_per_sm(int32_t ctas);
+
+/* Static description of a status code. */
+const char *pc_status_string(int32_t status);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int32_t pc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PC_H_ */

@@ -4,21 +4,22 @@ preconditioned CG for sparse SPD systems (the classical GPU stage of arXiv 2410.
 The compute path is the CUDA library ``libpc.so`` (C-ABI, ``include/pc.h``); the Python
 layer in ``binding`` only marshals torch device tensors and the current stream into it.
 """
+import importlib
+
 from . import workloads  # noqa: F401  (input generators; no method arithmetic)
+
+_BINDING_NAMES = ("setup", "apply", "kappa", "pcg", "spmv", "dot", "extract_blocks", "Handle", "csr", "CSR",
+                  "pcg_batched", "grad_val", "status_string", "PcError", "set_wait_budget", "set_ctas_per_sm")
 
 
 def load():
     """Load the CUDA library; raises if it was not built."""
-    from . import binding
-
-    return binding.lib()
+    return importlib.import_module(".binding", __name__).lib()
 
 
 def __getattr__(name):
-    if name in ("setup", "apply", "kappa", "pcg", "spmv", "dot", "extract_blocks",
-                "Handle", "PcgSolve", "pcg_batched", "BatchHandle", "grad_val", "binding",
-                "setup_batched", "status_string", "PcError"):
-        from . import binding
-
-        return getattr(binding, name) if name != "binding" else binding
+    if name in _BINDING_NAMES:
+        return getattr(importlib.import_module(".binding", __name__), name)
+    if name == "PcgSolve":
+        return importlib.import_module(".autograd", __name__).PcgSolve
     raise AttributeError(name)

@@ -1,0 +1,341 @@
+"""Thin ctypes binding of libpc (include/pc.h).
+
+Only argument marshalling happens here: torch CUDA tensors supply device pointers and
+``torch.cuda.current_stream()`` supplies the stream; every step of the computation runs in
+the CUDA library.  If ``libpc.so`` is missing or cannot be loaded, every entry point raises
+(there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpc.so")
+
+PC_OK, PC_ERR_INVALID_ARG, PC_ERR_NOT_SPD, PC_ERR_BREAKDOWN = 0, 1, 2, 3
+PC_ERR_NO_CONVERGENCE, PC_ERR_TIMEOUT, PC_ERR_CUDA, PC_ERR_OOM = 4, 5, 6, 7
+STATUS_NAMES = {0: "ok", 1: "invalid_arg", 2: "not_spd", 3: "breakdown", 4: "no_convergence",
+                5: "timeout", 6: "cuda_error", 7: "oom"}
+PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "mixed": 1}
+APPLY = {"inv": 0, "sym": 1, "linv": 2, "ltinv": 3}
+
+
+class PcError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = int(status)
+        self.name = STATUS_NAMES.get(self.status, str(status))
+        super().__init__(f"{what}: {self.name} ({status_string(self.status)})" if what else self.name)
+
+
+class pc_csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("col_idx", ctypes.c_void_p), ("val", ctypes.c_void_p), ("dtype", ctypes.c_int32)]
+
+
+class pc_solve_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("restarts", ctypes.c_int32),
+                ("failed_block", ctypes.c_int32), ("rel_residual", ctypes.c_double),
+                ("true_rel_residual", ctypes.c_double), ("setup_ms", ctypes.c_double),
+                ("solve_ms", ctypes.c_double), ("grid_ctas", ctypes.c_int32), ("block_size", ctypes.c_int32),
+                ("prec", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def to_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        d["status_name"] = STATUS_NAMES.get(self.status, str(self.status))
+        return d
+
+
+class pc_kappa_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("steps", ctypes.c_int32), ("kappa", ctypes.c_double),
+                ("lambda_min", ctypes.c_double), ("lambda_max", ctypes.c_double),
+                ("alpha", ctypes.c_void_p), ("beta", ctypes.c_void_p), ("elapsed_ms", ctypes.c_double)]
+
+
+class pc_batch(ctypes.Structure):
+    _fields_ = [("n_sys", ctypes.c_int32), ("n_rows", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("sys_row", ctypes.c_void_p), ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p),
+                ("val", ctypes.c_void_p), ("block_size", ctypes.c_void_p), ("max_block_size", ctypes.c_int32)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+
+
+def lib():
+    """Load libpc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "pc_setup": (_I32, [ctypes.POINTER(pc_csr), _I32, _D, _I32, _P, ctypes.POINTER(_P)]),
+        "pc_handle_failed_block": (_I64, [_P]),
+        "pc_apply": (_I32, [_P, _I32, _P, _P, _P]),
+        "pc_get_factor": (_I32, [_P, _I32, _P, _P]),
+        "pc_destroy": (_I32, [_P]),
+        "pc_extract_blocks": (_I32, [ctypes.POINTER(pc_csr), _I32, _P, _P]),
+        "pc_spmv": (_I32, [ctypes.POINTER(pc_csr), _P, _P, _P]),
+        "pc_dot": (_I32, [_I64, _P, _P, _P, _P]),
+        "kappa_estimate": (_I32, [ctypes.POINTER(pc_csr), _I32, _I32, _D, _P, _I32,
+                                  ctypes.POINTER(pc_kappa_info), _P]),
+        "kappa_estimate_h": (_I32, [_P, ctypes.POINTER(pc_csr), _I32, _D, _P, _I32,
+                                    ctypes.POINTER(pc_kappa_info), _P]),
+        "pcg_solve": (_I32, [ctypes.POINTER(pc_csr), _I32, _P, _P, _D, _I32, _I32,
+                             ctypes.POINTER(pc_solve_info), _P]),
+        "pcg_solve_h": (_I32, [_P, _P, _P, _D, _I32, ctypes.POINTER(pc_solve_info), _P]),
+        "pc_grad_val": (_I32, [ctypes.POINTER(pc_csr), _P, _P, _P, _P]),
+        "pcg_solve_batched": (_I32, [ctypes.POINTER(pc_batch), _P, _P, _D, _I32, _I32, _P, _P, _P,
+                                     ctypes.POINTER(pc_solve_info), _P]),
+        "pc_set_wait_budget": (None, [_I64]),
+        "pc_set_ctas_per_sm": (None, [_I32]),
+        "pc_status_string": (ctypes.c_char_p, [_I32]),
+        "pc_version": (_I32, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def status_string(s: int) -> str:
+    return lib().pc_status_string(int(s)).decode()
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream():
+    return ctypes.c_void_p(_torch().cuda.current_stream().cuda_stream)
+
+
+def _dev(t, dtype):
+    torch = _torch()
+    if isinstance(t, np.ndarray):
+        t = torch.from_numpy(np.ascontiguousarray(t))
+    if t.device.type != "cuda":
+        t = t.to("cuda", non_blocking=False)
+    t = t.to(dtype).contiguous()
+    return t
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _check(status: int, what: str, allow=()):
+    if status != PC_OK and status not in allow:
+        raise PcError(status, what)
+    return status
+
+
+@dataclass
+class CSR:
+    """Device CSR (torch CUDA tensors) with its pc_csr descriptor."""
+
+    row_ptr: object
+    col: object
+    val: object
+
+    @property
+    def n(self) -> int:
+        return int(self.row_ptr.numel() - 1)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.numel())
+
+    def desc(self) -> pc_csr:
+        torch = _torch()
+        return pc_csr(self.n, self.nnz, self.row_ptr.data_ptr(), self.col.data_ptr(), self.val.data_ptr(),
+                      1 if self.val.dtype == torch.float32 else 0)
+
+
+def csr(row_ptr, col=None, val=None) -> CSR:
+    """Device CSR from (row_ptr, col, val) arrays or from an object with those attributes.
+    float32 values stay float32 (PC_F32); anything else becomes float64."""
+    torch = _torch()
+    if col is None:
+        A = row_ptr
+        row_ptr, col, val = A.row_ptr, A.col, A.val
+    vdt = torch.float32 if (getattr(val, "dtype", None) in (np.float32, torch.float32)) else torch.float64
+    return CSR(_dev(row_ptr, torch.int32), _dev(col, torch.int32), _dev(val, vdt))
+
+
+def _as_csr(A) -> CSR:
+    return A if isinstance(A, CSR) else csr(A)
+
+
+class Handle:
+    """A block-Jacobi preconditioner built by pc_setup (owns device factors)."""
+
+    def __init__(self, A, block_size: int, tol: float = 0.0, prec: str = "fp64"):
+        self.A = _as_csr(A)
+        self.block_size = int(block_size)
+        self.prec = prec
+        self._d = self.A.desc()
+        h = ctypes.c_void_p()
+        st = lib().pc_setup(ctypes.byref(self._d), self.block_size, float(tol), PREC[prec], _stream(),
+                            ctypes.byref(h))
+        self._h = h
+        if st != PC_OK:
+            self.failed_block = int(lib().pc_handle_failed_block(h)) if h.value else -1
+            self.destroy()
+            raise PcError(st, f"pc_setup (failed block {self.failed_block})")
+        self.failed_block = -1
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _torch().cuda.current_stream().synchronize()
+            lib().pc_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def apply(self, mode: str, v, out=None):
+        torch = _torch()
+        v = _dev(v, torch.float64)
+        out = torch.empty_like(v) if out is None else out
+        _check(lib().pc_apply(self._h, APPLY[mode], _ptr(v), _ptr(out), _stream()), f"pc_apply({mode})")
+        return out
+
+    def factor(self, which: str = "minv"):
+        torch = _torch()
+        nb = (self.A.n + self.block_size - 1) // self.block_size
+        out = torch.empty((nb, self.block_size, self.block_size), dtype=torch.float64, device="cuda")
+        _check(lib().pc_get_factor(self._h, 0 if which == "linv" else 1, _ptr(out), _stream()), "pc_get_factor")
+        return out
+
+    def pcg(self, b, x0=None, tol: float = 1e-10, max_iter: int = 100000, check: bool = True):
+        torch = _torch()
+        b = _dev(b, torch.float64)
+        x = torch.zeros_like(b) if x0 is None else _dev(x0, torch.float64).clone()
+        info = pc_solve_info()
+        st = lib().pcg_solve_h(self._h, _ptr(b), _ptr(x), float(tol), int(max_iter), ctypes.byref(info), _stream())
+        if check:
+            _check(st, "pcg_solve_h")
+        return x, info.to_dict()
+
+    def kappa(self, v0, max_steps: int = 200, tol: float = 1e-12, reorth: bool = True):
+        return _kappa(self._h, self.A, v0, max_steps, tol, reorth)
+
+
+def setup(A, block_size: int, tol: float = 0.0, prec: str = "fp64") -> Handle:
+    return Handle(A, block_size, tol, prec)
+
+
+def _kappa(h, A, v0, max_steps, tol, reorth):
+    torch = _torch()
+    v0 = _dev(v0, torch.float64)
+    d = A.desc()
+    alpha = np.zeros(max_steps)
+    beta = np.zeros(max_steps)
+    info = pc_kappa_info()
+    info.alpha = alpha.ctypes.data
+    info.beta = beta.ctypes.data
+    st = lib().kappa_estimate_h(h, ctypes.byref(d), int(max_steps), float(tol), _ptr(v0), int(bool(reorth)),
+                                ctypes.byref(info), _stream())
+    _check(st, "kappa_estimate")
+    k = info.steps
+    return {"kappa": info.kappa, "lambda_min": info.lambda_min, "lambda_max": info.lambda_max, "steps": k,
+            "alpha": alpha[:k].copy(), "beta": beta[:k].copy(), "elapsed_ms": info.elapsed_ms}
+
+
+def kappa(A, v0, block_size: int = 0, max_steps: int = 200, tol: float = 1e-12, reorth: bool = True):
+    """Lanczos kappa estimate of A (block_size 0) or of L^{-1} A L^{-T} (FP64 factors)."""
+    torch = _torch()
+    A = _as_csr(A)
+    v0 = _dev(v0, torch.float64)
+    d = A.desc()
+    alpha = np.zeros(max_steps)
+    beta = np.zeros(max_steps)
+    info = pc_kappa_info()
+    info.alpha = alpha.ctypes.data
+    info.beta = beta.ctypes.data
+    st = lib().kappa_estimate(ctypes.byref(d), int(block_size), int(max_steps), float(tol), _ptr(v0),
+                              int(bool(reorth)), ctypes.byref(info), _stream())
+    _check(st, "kappa_estimate")
+    k = info.steps
+    return {"kappa": info.kappa, "lambda_min": info.lambda_min, "lambda_max": info.lambda_max, "steps": k,
+            "alpha": alpha[:k].copy(), "beta": beta[:k].copy(), "elapsed_ms": info.elapsed_ms}
+
+
+def pcg(A, b, block_size: int, tol: float = 1e-10, max_iter: int = 100000, prec: str = "fp64", x0=None,
+        check: bool = True):
+    """Block-Jacobi PCG (setup + solve in one call).  Returns (x, info dict)."""
+    torch = _torch()
+    A = _as_csr(A)
+    b = _dev(b, torch.float64)
+    x = torch.zeros_like(b) if x0 is None else _dev(x0, torch.float64).clone()
+    d = A.desc()
+    info = pc_solve_info()
+    st = lib().pcg_solve(ctypes.byref(d), int(block_size), _ptr(b), _ptr(x), float(tol), int(max_iter),
+                         PREC[prec], ctypes.byref(info), _stream())
+    if check:
+        _check(st, "pcg_solve")
+    return x, info.to_dict()
+
+
+def spmv(A, x, out=None):
+    torch = _torch()
+    A = _as_csr(A)
+    x = _dev(x, torch.float64)
+    out = torch.empty_like(x) if out is None else out
+    d = A.desc()
+    _check(lib().pc_spmv(ctypes.byref(d), _ptr(x), _ptr(out), _stream()), "pc_spmv")
+    return out
+
+
+def dot(x, y) -> float:
+    torch = _torch()
+    x = _dev(x, torch.float64)
+    y = _dev(y, torch.float64)
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    _check(lib().pc_dot(int(x.numel()), _ptr(x), _ptr(y), _ptr(out), _stream()), "pc_dot")
+    return float(out.item())
+
+
+def extract_blocks(A, block_size: int):
+    torch = _torch()
+    A = _as_csr(A)
+    nb = (A.n + block_size - 1) // block_size
+    out = torch.empty((nb, block_size, block_size), dtype=torch.float64, device="cuda")
+    d = A.desc()
+    _check(lib().pc_extract_blocks(ctypes.byref(d), int(block_size), _ptr(out), _stream()), "pc_extract_blocks")
+    return out
+
+
+def grad_val(A, lam, x):
+    torch = _torch()
+    A = _as_csr(A)
+    lam = _dev(lam, torch.float64)
+    x = _dev(x, torch.float64)
+    out = torch.empty(A.nnz, dtype=torch.float64, device="cuda")
+    d = A.desc()
+    _check(lib().pc_grad_val(ctypes.byref(d), _ptr(lam), _ptr(x), _ptr(out), _stream()), "pc_grad_val")
+    return out
+
+
+def set_wait_budget(cycles: int):
+    lib().pc_set_wait_budget(int(cycles))
+
+
+def set_ctas_per_sm(ctas: int):
+    lib().pc_set_ctas_per_sm(int(ctas))

@@ -1,0 +1,511 @@
+// Host side of the libpc C ABI (include/pc.h): argument checks, handle and workspace
+// management, kernel dispatch and status reporting.  No call prints, aborts or traps.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "pc.h"
+#include "pc_kernels.cuh"
+
+using pc::Layout;
+
+struct pc_handle {
+  pc_csr A;
+  int32_t bs;
+  int32_t prec;
+  double tol;
+  Layout L;
+  bool val_f32;
+  bool fac_f32;
+  void* minv;
+  void* linv;
+  double* tmp;
+  unsigned long long* failed_d;
+  int64_t failed_block;
+  // CG workspace (allocated on first solve)
+  double* cg;            // r, z, p, q: 4 n
+  double* part;          // grid * 2
+  double* res;           // 2
+  int64_t* split;        // grid + 1
+  unsigned char* ctl;    // GridSync + PcgOut
+  int grid;
+  int block;
+};
+
+namespace {
+
+long long g_budget = 0;          // 0 = default
+int g_ctas_per_sm = 0;           // 0 = occupancy maximum
+const long long kDefaultBudget = 4000000000LL;
+
+long long wait_budget() {
+  if (g_budget > 0) return g_budget;
+  const char* e = getenv("PC_WAIT_BUDGET");
+  if (e) {
+    long long v = atoll(e);
+    if (v > 0) return v;
+  }
+  return kDefaultBudget;
+}
+
+pc_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return PC_OK;
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? PC_ERR_OOM : PC_ERR_CUDA;
+}
+
+#define PC_TRY(expr)                         \
+  do {                                       \
+    cudaError_t _e = (expr);                 \
+    if (_e != cudaSuccess) return from_cuda(_e); \
+  } while (0)
+
+template <typename T>
+pc_status dalloc(T** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? PC_ERR_OOM : PC_ERR_CUDA;
+  }
+  return PC_OK;
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+bool csr_ok(const pc_csr* A) {
+  if (!A) return false;
+  if (A->n <= 0 || A->n >= (int64_t)INT32_MAX || A->nnz < 0 || A->nnz >= (int64_t)INT32_MAX) return false;
+  if (!A->row_ptr || !A->col_idx || (A->nnz > 0 && !A->val)) return false;
+  if (A->dtype != PC_F64 && A->dtype != PC_F32) return false;
+  return true;
+}
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+// Per-device scratch for pc_dot.
+std::mutex g_mu;
+double* g_dot_scratch[64] = {nullptr};
+
+}  // namespace
+
+extern "C" {
+
+int32_t pc_version(void) { return 100; }
+
+void pc_set_wait_budget(int64_t cycles) { g_budget = cycles > 0 ? (long long)cycles : 0; }
+
+void pc_set_ctas_per_sm(int32_t ctas) { g_ctas_per_sm = ctas > 0 ? ctas : 0; }
+
+const char* pc_status_string(int32_t s) {
+  switch (s) {
+    case PC_OK: return "ok";
+    case PC_ERR_INVALID_ARG: return "invalid argument";
+    case PC_ERR_NOT_SPD: return "diagonal block is not SPD (Cholesky pivot below threshold)";
+    case PC_ERR_BREAKDOWN: return "CG breakdown (non-positive or non-finite curvature)";
+    case PC_ERR_NO_CONVERGENCE: return "no convergence within max_iter";
+    case PC_ERR_TIMEOUT: return "bounded device-side wait timed out";
+    case PC_ERR_CUDA: return "CUDA runtime error";
+    case PC_ERR_OOM: return "device allocation failed";
+    default: return "unknown status";
+  }
+}
+
+pc_status pc_destroy(pc_handle* h) {
+  if (!h) return PC_ERR_INVALID_ARG;
+  dfree(h->minv);
+  dfree(h->linv);
+  dfree(h->tmp);
+  dfree(h->failed_d);
+  dfree(h->cg);
+  dfree(h->part);
+  dfree(h->res);
+  dfree(h->split);
+  dfree(h->ctl);
+  delete h;
+  return PC_OK;
+}
+
+int64_t pc_handle_failed_block(const pc_handle* h) { return h ? h->failed_block : -1; }
+
+pc_status pc_setup(const pc_csr* A, int32_t block_size, double tol, int32_t prec, void* stream, pc_handle** out) {
+  if (!out) return PC_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!csr_ok(A) || block_size < 1 || block_size > 64 || !(tol >= 0.0)) return PC_ERR_INVALID_ARG;
+  if (prec != PC_PREC_FP64 && prec != PC_PREC_FP32 && prec != PC_PREC_TF32) return PC_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  pc_handle* h = new pc_handle();
+  memset(h, 0, sizeof(*h));
+  h->A = *A;
+  h->bs = block_size;
+  h->prec = prec;
+  h->tol = tol;
+  h->L = pc::make_layout(A->n, block_size);
+  h->val_f32 = A->dtype == PC_F32;
+  h->fac_f32 = prec != PC_PREC_FP64;
+  h->failed_block = -1;
+  const size_t es = h->fac_f32 ? 4 : 8;
+  pc_status s = dalloc(&h->minv, es * (size_t)(h->L.n_units * pc::unit_elems_minv(h->L)));
+  if (s == PC_OK) s = dalloc(&h->linv, es * (size_t)(h->L.n_units * pc::unit_elems_linv(h->L)));
+  if (s == PC_OK) s = dalloc(&h->tmp, sizeof(double) * (size_t)A->n);
+  if (s == PC_OK) s = dalloc(&h->failed_d, sizeof(unsigned long long));
+  if (s != PC_OK) {
+    pc_destroy(h);
+    return s;
+  }
+  cudaError_t e = cudaMemsetAsync(h->failed_d, 0xff, sizeof(unsigned long long), st);
+  pc::SetupArgs a;
+  a.lay = h->L;
+  a.row_ptr = A->row_ptr;
+  a.col = A->col_idx;
+  a.val = A->val;
+  a.tol = tol;
+  a.minv = h->minv;
+  a.linv = h->linv;
+  a.failed = h->failed_d;
+  if (e == cudaSuccess) e = pc::launch_setup(a, h->val_f32, h->fac_f32, st);
+  unsigned long long failed = ~0ull;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&failed, h->failed_d, sizeof(failed), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    pc_destroy(h);
+    return from_cuda(e);
+  }
+  *out = h;
+  if (failed != ~0ull) {
+    h->failed_block = (int64_t)failed;
+    return PC_ERR_NOT_SPD;
+  }
+  return PC_OK;
+}
+
+pc_status pc_apply(pc_handle* h, int32_t mode, const double* in, double* out, void* stream) {
+  if (!h || !in || !out || in == out) return PC_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (mode) {
+    case PC_APPLY_INV: return from_cuda(pc::launch_apply(h->L, h->minv, h->fac_f32, 0, in, out, st));
+    case PC_APPLY_LINV: return from_cuda(pc::launch_apply(h->L, h->linv, h->fac_f32, 2, in, out, st));
+    case PC_APPLY_LTINV: return from_cuda(pc::launch_apply(h->L, h->linv, h->fac_f32, 3, in, out, st));
+    case PC_APPLY_SYM: {
+      PC_TRY(pc::launch_apply(h->L, h->linv, h->fac_f32, 3, in, h->tmp, st));
+      pc::SymPhase2Args a;
+      memset(&a, 0, sizeof(a));
+      a.lay = h->L;
+      a.rp = h->A.row_ptr;
+      a.ci = h->A.col_idx;
+      a.va = h->A.val;
+      a.linv = h->linv;
+      a.t = h->tmp;
+      a.out = out;
+      return from_cuda(pc::launch_sym_phase2(a, h->val_f32, h->fac_f32, 0, st));
+    }
+    default: return PC_ERR_INVALID_ARG;
+  }
+}
+
+pc_status pc_get_factor(const pc_handle* h, int32_t which, double* out, void* stream) {
+  if (!h || !out || (which != 0 && which != 1)) return PC_ERR_INVALID_ARG;
+  return from_cuda(pc::launch_get_factor(h->L, which == 0 ? h->linv : h->minv, h->fac_f32, which, out,
+                                         (cudaStream_t)stream));
+}
+
+pc_status pc_extract_blocks(const pc_csr* A, int32_t block_size, double* out, void* stream) {
+  if (!csr_ok(A) || block_size < 1 || !out) return PC_ERR_INVALID_ARG;
+  return from_cuda(pc::launch_extract(A->n, A->row_ptr, A->col_idx, A->val, A->dtype == PC_F32, block_size, out,
+                                      (cudaStream_t)stream));
+}
+
+pc_status pc_spmv(const pc_csr* A, const double* x, double* y, void* stream) {
+  if (!csr_ok(A) || !x || !y || x == y) return PC_ERR_INVALID_ARG;
+  return from_cuda(pc::launch_spmv(A->n, A->row_ptr, A->col_idx, A->val, A->dtype == PC_F32, x, y,
+                                   (cudaStream_t)stream));
+}
+
+pc_status pc_dot(int64_t n, const double* x, const double* y, double* result, void* stream) {
+  if (n < 0 || !x || !y || !result) return PC_ERR_INVALID_ARG;
+  int dev = 0;
+  PC_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return PC_ERR_INVALID_ARG;
+  double* scratch;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_dot_scratch[dev]) {
+      pc_status s = dalloc(&g_dot_scratch[dev], sizeof(double) * (size_t)pc::dot_partials());
+      if (s != PC_OK) return s;
+    }
+    scratch = g_dot_scratch[dev];
+  }
+  return from_cuda(pc::launch_dot(n, x, y, result, scratch, (cudaStream_t)stream));
+}
+
+pc_status pc_grad_val(const pc_csr* A, const double* lambda, const double* x, double* grad_val, void* stream) {
+  if (!csr_ok(A) || !lambda || !x || !grad_val) return PC_ERR_INVALID_ARG;
+  return from_cuda(pc::launch_grad_val(A->n, A->row_ptr, A->col_idx, lambda, x, grad_val, (cudaStream_t)stream));
+}
+
+// ------------------------------------------------------------------ PCG
+static pc_status ensure_cg_workspace(pc_handle* h, cudaStream_t st) {
+  const int block = 256;
+  int per_sm = 0;
+  PC_TRY(pc::pcg_occupancy(h->L, h->val_f32, h->fac_f32, block, &per_sm));
+  if (per_sm < 1) return PC_ERR_CUDA;
+  if (g_ctas_per_sm > 0 && g_ctas_per_sm < per_sm) per_sm = g_ctas_per_sm;
+  int grid = per_sm * sm_count();
+  const int64_t max_useful = (h->L.n_units + 7) / 8;   // at least 8 warp units per CTA
+  if (grid > max_useful) grid = (int)(max_useful > 0 ? max_useful : 1);
+  if (h->cg && h->grid == grid) return PC_OK;
+  dfree(h->part);
+  dfree(h->split);
+  h->part = nullptr;
+  h->split = nullptr;
+  pc_status s = PC_OK;
+  if (!h->cg) s = dalloc(&h->cg, sizeof(double) * 4 * (size_t)h->A.n);
+  if (s == PC_OK && !h->res) s = dalloc(&h->res, sizeof(double) * 4);
+  if (s == PC_OK && !h->ctl) s = dalloc(&h->ctl, sizeof(pc::GridSync) + sizeof(pc::PcgOut));
+  if (s == PC_OK) s = dalloc(&h->part, sizeof(double) * 2 * (size_t)grid);
+  if (s == PC_OK) s = dalloc(&h->split, sizeof(int64_t) * (size_t)(grid + 1));
+  if (s != PC_OK) return s;
+  PC_TRY(pc::launch_split(h->A.n, h->A.nnz, h->A.row_ptr, grid, h->split, st));
+  h->grid = grid;
+  h->block = block;
+  return PC_OK;
+}
+
+pc_status pcg_solve_h(pc_handle* h, const double* b, double* x, double tol, int32_t max_iter, pc_solve_info* info,
+                      void* stream) {
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->failed_block = -1;
+  }
+  if (!h || !b || !x || !(tol >= 0.0) || max_iter < 0) return PC_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  pc_status s = ensure_cg_workspace(h, st);
+  if (s != PC_OK) return s;
+  const int64_t n = h->A.n;
+  pc::PcgArgs a;
+  a.lay = h->L;
+  a.rp = h->A.row_ptr;
+  a.ci = h->A.col_idx;
+  a.va = h->A.val;
+  a.minv = h->minv;
+  a.b = b;
+  a.x = x;
+  a.r = h->cg;
+  a.z = h->cg + n;
+  a.p = h->cg + 2 * n;
+  a.q = h->cg + 3 * n;
+  a.part = h->part;
+  a.res = h->res;
+  a.split = h->split;
+  a.gs = reinterpret_cast<pc::GridSync*>(h->ctl);
+  a.out = reinterpret_cast<pc::PcgOut*>(h->ctl + sizeof(pc::GridSync));
+  a.tol = tol;
+  a.max_iter = max_iter;
+  a.max_restarts = 3;
+  a.budget = wait_budget();
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  PC_TRY(cudaEventCreate(&e0));
+  cudaError_t e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->ctl, 0, sizeof(pc::GridSync) + sizeof(pc::PcgOut), st);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+  if (e == cudaSuccess) e = pc::launch_pcg(a, h->val_f32, h->fac_f32, h->grid, h->block, st);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  unsigned char hostctl[sizeof(pc::GridSync) + sizeof(pc::PcgOut)];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hostctl, h->ctl, sizeof(hostctl), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  float ms = 0.f;
+  if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return from_cuda(e);
+  pc::GridSync gs;
+  pc::PcgOut out;
+  memcpy(&gs, hostctl, sizeof(gs));
+  memcpy(&out, hostctl + sizeof(gs), sizeof(out));
+  pc_status status = gs.status != 0 ? (pc_status)gs.status : (pc_status)out.status;
+  if (info) {
+    info->status = status;
+    info->iterations = out.iterations;
+    info->restarts = out.restarts;
+    info->rel_residual = out.rel_residual;
+    info->true_rel_residual = out.true_rel_residual;
+    info->solve_ms = ms;
+    info->grid_ctas = h->grid;
+    info->block_size = h->bs;
+    info->prec = h->prec;
+  }
+  return status;
+}
+
+pc_status pcg_solve(const pc_csr* A, int32_t block_size, const double* b, double* x, double tol, int32_t max_iter,
+                    int32_t prec, pc_solve_info* info, void* stream) {
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->failed_block = -1;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  PC_TRY(cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce == cudaSuccess) ce = cudaEventRecord(e0, st);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return from_cuda(ce);
+  }
+  pc_handle* h = nullptr;
+  pc_status s = pc_setup(A, block_size, 0.0, prec, stream, &h);
+  float setup_ms = 0.f;
+  if (cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess)
+    cudaEventElapsedTime(&setup_ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != PC_OK) {
+    if (info) {
+      info->status = s;
+      info->failed_block = h ? (int32_t)h->failed_block : -1;
+      info->setup_ms = setup_ms;
+    }
+    if (h) pc_destroy(h);
+    return s;
+  }
+  s = pcg_solve_h(h, b, x, tol, max_iter, info, stream);
+  if (info) info->setup_ms = setup_ms;
+  pc_destroy(h);
+  return s;
+}
+
+// ------------------------------------------------------------------ Lanczos
+pc_status kappa_estimate_h(pc_handle* h, const pc_csr* A, int32_t max_steps, double tol, const double* v0,
+                           int32_t reorth, pc_kappa_info* info, void* stream) {
+  double* ha = info ? info->alpha : nullptr;
+  double* hb = info ? info->beta : nullptr;
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->alpha = ha;
+    info->beta = hb;
+  }
+  const pc_csr* M = h ? &h->A : A;
+  if (!csr_ok(M) || !v0 || max_steps < 1 || max_steps > 256 || !(tol >= 0.0) || (reorth != 0 && reorth != 1))
+    return PC_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = M->n;
+  const int m = max_steps;
+  const int G = pc::lanczos_grid();
+  pc::LanczosState s;
+  memset(&s, 0, sizeof(s));
+  s.n = n;
+  s.m = m;
+  s.tol = tol;
+  double* small = nullptr;
+  unsigned char* ctlbuf = nullptr;
+  pc_status st_ = dalloc(&s.V, sizeof(double) * (size_t)m * (size_t)n);
+  if (st_ == PC_OK) st_ = dalloc(&s.w, sizeof(double) * (size_t)n);
+  if (st_ == PC_OK) st_ = dalloc(&s.t, sizeof(double) * (size_t)n);
+  if (st_ == PC_OK) st_ = dalloc(&small, sizeof(double) * (size_t)(4 * m + 4));
+  if (st_ == PC_OK) st_ = dalloc(&s.part, sizeof(double) * (size_t)G * (size_t)m);
+  if (st_ == PC_OK) st_ = dalloc(&ctlbuf, 64);
+  auto cleanup = [&]() {
+    dfree(s.V);
+    dfree(s.w);
+    dfree(s.t);
+    dfree(small);
+    dfree(s.part);
+    dfree(ctlbuf);
+  };
+  if (st_ != PC_OK) {
+    cleanup();
+    return st_;
+  }
+  s.alpha = small;
+  s.beta = small + m;
+  s.coef = small + 2 * m;
+  s.result = small + 4 * m;
+  s.tnorm = small + 4 * m + 2;
+  s.counter = reinterpret_cast<unsigned*>(ctlbuf);
+  s.ctl = reinterpret_cast<int*>(ctlbuf + 16);
+  const bool precond = h != nullptr;
+  const Layout L = precond ? h->L : pc::make_layout(n, 1);
+  const void* linv = precond ? h->linv : nullptr;
+  const bool f32 = precond ? h->fac_f32 : false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+  if (e == cudaSuccess) e = pc::lanczos_configure(m);
+  if (e == cudaSuccess) e = pc::lanczos_init(s, v0, precond, L, linv, f32, st);
+  for (int j = 0; j < m && e == cudaSuccess; ++j) {
+    e = pc::lanczos_step(s, j, reorth, precond, L, M->row_ptr, M->col_idx, M->val, M->dtype == PC_F32, linv, f32,
+                         st);
+    if (e == cudaSuccess && (j % 16) == 15 && j + 1 < m) {
+      int done = 0;
+      e = cudaMemcpyAsync(&done, s.ctl, sizeof(int), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e == cudaSuccess && done) break;
+    }
+  }
+  if (e == cudaSuccess) e = pc::lanczos_finish(s, st);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  double res[2] = {0.0, 0.0};
+  int ctl[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(res, s.result, sizeof(res), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ctl, s.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && ha) e = cudaMemcpyAsync(ha, s.alpha, sizeof(double) * m, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && hb) e = cudaMemcpyAsync(hb, s.beta, sizeof(double) * m, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  float ms = 0.f;
+  if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cleanup();
+  if (e != cudaSuccess) return from_cuda(e);
+  if (info) {
+    info->status = PC_OK;
+    info->steps = ctl[1];
+    info->lambda_min = res[0];
+    info->lambda_max = res[1];
+    info->kappa = res[1] / res[0];
+    info->elapsed_ms = ms;
+  }
+  return PC_OK;
+}
+
+pc_status kappa_estimate(const pc_csr* A, int32_t block_size, int32_t max_steps, double tol, const double* v0,
+                         int32_t reorth, pc_kappa_info* info, void* stream) {
+  if (block_size < 0 || block_size > 64) return PC_ERR_INVALID_ARG;
+  if (block_size == 0) return kappa_estimate_h(nullptr, A, max_steps, tol, v0, reorth, info, stream);
+  pc_handle* h = nullptr;
+  pc_status s = pc_setup(A, block_size, 0.0, PC_PREC_FP64, stream, &h);
+  if (s != PC_OK) {
+    if (h) pc_destroy(h);
+    if (info) info->status = s;
+    return s;
+  }
+  s = kappa_estimate_h(h, A, max_steps, tol, v0, reorth, info, stream);
+  pc_destroy(h);
+  return s;
+}
+
+// ------------------------------------------------------------------ batched (see pc_batched.cu)
+pc_status pc_batched_impl(const pc_batch* B, const double* b, double* x, double tol, int32_t max_iter, int32_t prec,
+                          int32_t* iters, int32_t* status, double* relres, pc_solve_info* info, void* stream);
+
+pc_status pcg_solve_batched(const pc_batch* B, const double* b, double* x, double tol, int32_t max_iter,
+                            int32_t prec, int32_t* iters, int32_t* status, double* relres, pc_solve_info* info,
+                            void* stream) {
+  return pc_batched_impl(B, b, x, tol, max_iter, prec, iters, status, relres, info, stream);
+}
+
+}  // extern "C"

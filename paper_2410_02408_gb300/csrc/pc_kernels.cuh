@@ -1,0 +1,124 @@
+// Kernel argument structs and host-side launchers shared between the libpc translation
+// units (internal; the public interface is include/pc.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pc_common.cuh"
+
+namespace pc {
+
+struct SetupArgs {
+  Layout lay;
+  const int32_t* row_ptr;
+  const int32_t* col;
+  const void* val;
+  double tol;
+  void* minv;                     // unit layout, FT
+  void* linv;                     // unit layout, FT
+  unsigned long long* failed;     // min failing block index (init: all ones)
+};
+
+struct PcgOut {
+  int32_t status;
+  int32_t iterations;
+  int32_t restarts;
+  int32_t pad;
+  double rel_residual;
+  double true_rel_residual;
+};
+
+struct PcgArgs {
+  Layout lay;
+  const int32_t* rp;
+  const int32_t* ci;
+  const void* va;
+  const void* minv;
+  const double* b;
+  double* x;
+  double* r;
+  double* z;
+  double* p;
+  double* q;
+  double* part;          // gridDim * 2 doubles
+  double* res;           // 2 doubles
+  const int64_t* split;  // gridDim + 1 SpMV row boundaries
+  GridSync* gs;
+  PcgOut* out;
+  double tol;
+  int32_t max_iter;
+  int32_t max_restarts;
+  long long budget;
+};
+
+// pc_setup.cu
+cudaError_t launch_setup(const SetupArgs& a, bool val_f32, bool fac_f32, cudaStream_t st);
+cudaError_t launch_extract(int64_t n, const int32_t* rp, const int32_t* ci, const void* va, bool val_f32,
+                           int32_t bs, double* out, cudaStream_t st);
+cudaError_t launch_get_factor(const Layout& L, const void* fac, bool fac_f32, int which, double* out,
+                              cudaStream_t st);
+
+// pc_ops.cu
+cudaError_t launch_spmv(int64_t n, const int32_t* rp, const int32_t* ci, const void* va, bool val_f32,
+                        const double* x, double* y, cudaStream_t st);
+cudaError_t launch_dot(int64_t n, const double* x, const double* y, double* result, double* part,
+                       cudaStream_t st);
+int dot_partials();
+cudaError_t launch_apply(const Layout& L, const void* fac, bool fac_f32, int mode, const double* in,
+                         double* out, cudaStream_t st);
+// out = L^{-1} (A t) (+ optional Lanczos epilogue, see pc_ops.cu)
+struct SymPhase2Args {
+  Layout lay;
+  const int32_t* rp;
+  const int32_t* ci;
+  const void* va;
+  const void* linv;
+  const double* t;      // L^{-T} v
+  double* out;
+  // Lanczos epilogue (q_prev == nullptr: none)
+  const double* q_cur;
+  const double* q_prev;
+  const double* beta;   // device scalar array, beta[j-1] used
+  int32_t j;
+  double* part;         // per-CTA partial of q_cur . out
+  unsigned* counter;
+  double* alpha_out;    // alpha[j]
+  const int* done;
+};
+cudaError_t launch_sym_phase2(const SymPhase2Args& a, bool val_f32, bool fac_f32, int grid, cudaStream_t st);
+cudaError_t launch_split(int64_t n, int64_t nnz, const int32_t* rp, int parts, int64_t* split, cudaStream_t st);
+cudaError_t launch_grad_val(int64_t n, const int32_t* rp, const int32_t* ci, const double* lam, const double* x,
+                            double* g, cudaStream_t st);
+
+// pc_pcg_*.cu
+cudaError_t launch_pcg(const PcgArgs& a, bool val_f32, bool fac_f32, int grid, int block, cudaStream_t st);
+cudaError_t pcg_occupancy(const Layout& L, bool val_f32, bool fac_f32, int block, int* ctas_per_sm);
+
+// pc_lanczos.cu
+struct LanczosState {
+  int64_t n;
+  int32_t m;
+  double tol;
+  double* V;          // m * n
+  double* w;          // n
+  double* t;          // n (L^{-T} q_j)
+  double* alpha;      // m
+  double* beta;       // m
+  double* coef;       // 2 * m
+  double* part;       // grid * m
+  unsigned* counter;  // 1
+  int* ctl;           // [0] done, [1] steps
+  double* tnorm;      // 1
+  double* result;     // [0] theta_min [1] theta_max
+};
+cudaError_t lanczos_init(const LanczosState& s, const double* v0, bool precond, const Layout& L, const void* linv,
+                         bool fac_f32, cudaStream_t st);
+cudaError_t lanczos_step(const LanczosState& s, int j, int reorth, bool precond, const Layout& L,
+                         const int32_t* rp, const int32_t* ci, const void* va, bool val_f32, const void* linv,
+                         bool fac_f32, cudaStream_t st);
+cudaError_t lanczos_finish(const LanczosState& s, cudaStream_t st);
+cudaError_t lanczos_configure(int m);
+int lanczos_grid();
+
+}  // namespace pc

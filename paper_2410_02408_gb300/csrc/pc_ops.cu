@@ -1,0 +1,179 @@
+// Stand-alone operators: CSR SpMV, fixed-order dot product, block preconditioner
+// application (M^{-1}, L^{-1}, L^{-T}), the second phase of the symmetric operator
+// L^{-1} A L^{-T} (SpMV with a fused per-unit L^{-1} epilogue), the SpMV row split of
+// the persistent CG kernel, and the adjoint gradient on the sparsity pattern.
+#include "pc_kernels.cuh"
+
+namespace pc {
+
+template <typename VT>
+__global__ void __launch_bounds__(256) spmv_kernel(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                                   const VT* __restrict__ va, const double* __restrict__ x,
+                                                   double* __restrict__ y) {
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n; row += (int64_t)gridDim.x * blockDim.x)
+    y[row] = spmv_row<VT, false>(rp, ci, va, x, row);
+}
+
+constexpr int DOT_CTAS = 512;
+int dot_partials() { return DOT_CTAS + 1; }
+
+__global__ void __launch_bounds__(256) dot_kernel(int64_t n, const double* __restrict__ x, const double* __restrict__ y,
+                                                  double* part, unsigned* counter, double* out) {
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc = fma(x[i], y[i], acc);
+  last_cta_sum1(acc, part, counter, out);
+}
+
+template <typename FT>
+__global__ void __launch_bounds__(256) apply_kernel(Layout L, const FT* __restrict__ fac, int mode,
+                                                    const double* __restrict__ in, double* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t uM = unit_elems_minv(L), uL = unit_elems_linv(L);
+  for (int64_t u = gw; u < L.n_units; u += tw) {
+    double r[2], z[2];
+    int64_t rows[2];
+    bool ok[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      bool valid;
+      const int rho = unit_row(L, lane, s, valid);
+      rows[s] = u * L.U + rho;
+      ok[s] = valid && rows[s] < L.n;
+      r[s] = ok[s] ? in[rows[s]] : 0.0;
+    }
+    if (mode == 0) unit_apply_inv<FT, 0>(L, fac + u * uM, lane, r, z);
+    else if (mode == 2) unit_apply_linv<FT>(L, fac + u * uL, lane, r, z);
+    else unit_apply_ltinv<FT>(L, fac + u * uL, lane, r, z);
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+      if (ok[s]) out[rows[s]] = z[s];
+  }
+}
+
+// out = L^{-1} (A t).  With a Lanczos epilogue: out = L^{-1} A t - beta[j-1] q_prev and
+// alpha[j] = q_cur . out (fixed-order grid sum).
+template <typename VT, typename FT>
+__global__ void __launch_bounds__(256) sym_phase2_kernel(SymPhase2Args a) {
+  if (a.done && *(volatile const int*)a.done) return;
+  const Layout L = a.lay;
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t uL = unit_elems_linv(L);
+  const VT* va = (const VT*)a.va;
+  const FT* fac = (const FT*)a.linv;
+  const bool epi = a.q_cur != nullptr;
+  const double bprev = (epi && a.j > 0) ? a.beta[a.j - 1] : 0.0;
+  double acc = 0.0;
+  for (int64_t u = gw; u < L.n_units; u += tw) {
+    double uu[2], y[2];
+    int64_t rows[2];
+    bool ok[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      bool valid;
+      const int rho = unit_row(L, lane, s, valid);
+      rows[s] = u * L.U + rho;
+      ok[s] = valid && rows[s] < L.n;
+      uu[s] = ok[s] ? spmv_row<VT, false>(a.rp, a.ci, va, a.t, rows[s]) : 0.0;
+    }
+    unit_apply_linv<FT>(L, fac + u * uL, lane, uu, y);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      if (!ok[s]) continue;
+      double w = y[s];
+      if (epi) {
+        if (a.j > 0) w = fma(-bprev, a.q_prev[rows[s]], w);
+        acc = fma(a.q_cur[rows[s]], w, acc);
+      }
+      a.out[rows[s]] = w;
+    }
+  }
+  if (epi) last_cta_sum1(acc, a.part, a.counter, a.alpha_out);
+}
+
+__global__ void split_kernel(int64_t n, int64_t nnz, const int32_t* __restrict__ rp, int parts, int64_t* split) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= parts; c += gridDim.x * blockDim.x) {
+    if (c == parts) {
+      split[c] = n;
+      continue;
+    }
+    const long double tgt = (long double)c * (long double)(n + nnz) / parts;
+    int64_t lo = 0, hi = n;   // smallest r with r + rp[r] >= tgt
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) / 2;
+      if ((long double)(mid + rp[mid]) >= tgt) hi = mid;
+      else lo = mid + 1;
+    }
+    split[c] = lo;
+  }
+}
+
+__global__ void grad_val_kernel(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                const double* __restrict__ lam, const double* __restrict__ x, double* __restrict__ g) {
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n; row += (int64_t)gridDim.x * blockDim.x) {
+    const double l = -lam[row];
+    for (int32_t e = rp[row]; e < rp[row + 1]; ++e) g[e] = l * x[ci[e]];
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+static unsigned grid_for(int64_t work, int per) {
+  int64_t g = (work + per - 1) / per;
+  if (g > 152 * 64) g = 152 * 64;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+cudaError_t launch_spmv(int64_t n, const int32_t* rp, const int32_t* ci, const void* va, bool val_f32,
+                        const double* x, double* y, cudaStream_t st) {
+  if (val_f32)
+    spmv_kernel<float><<<grid_for(n, 256), 256, 0, st>>>(n, rp, ci, (const float*)va, x, y);
+  else
+    spmv_kernel<double><<<grid_for(n, 256), 256, 0, st>>>(n, rp, ci, (const double*)va, x, y);
+  return cudaGetLastError();
+}
+
+// part: dot_partials() doubles of scratch; the last slot is used as the arrival counter.
+cudaError_t launch_dot(int64_t n, const double* x, const double* y, double* result, double* part, cudaStream_t st) {
+  unsigned* counter = reinterpret_cast<unsigned*>(part + DOT_CTAS);
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  dot_kernel<<<DOT_CTAS, 256, 0, st>>>(n, x, y, part, counter, result);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply(const Layout& L, const void* fac, bool fac_f32, int mode, const double* in, double* out,
+                         cudaStream_t st) {
+  const unsigned g = grid_for(L.n_units * 32, 256);
+  if (fac_f32)
+    apply_kernel<float><<<g, 256, 0, st>>>(L, (const float*)fac, mode, in, out);
+  else
+    apply_kernel<double><<<g, 256, 0, st>>>(L, (const double*)fac, mode, in, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sym_phase2(const SymPhase2Args& a, bool val_f32, bool fac_f32, int grid, cudaStream_t st) {
+  const unsigned g = grid > 0 ? (unsigned)grid : grid_for(a.lay.n_units * 32, 256);
+  if (!val_f32 && !fac_f32) sym_phase2_kernel<double, double><<<g, 256, 0, st>>>(a);
+  else if (!val_f32 && fac_f32) sym_phase2_kernel<double, float><<<g, 256, 0, st>>>(a);
+  else if (val_f32 && fac_f32) sym_phase2_kernel<float, float><<<g, 256, 0, st>>>(a);
+  else sym_phase2_kernel<float, double><<<g, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split(int64_t n, int64_t nnz, const int32_t* rp, int parts, int64_t* split, cudaStream_t st) {
+  split_kernel<<<(parts + 256) / 256, 256, 0, st>>>(n, nnz, rp, parts, split);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_val(int64_t n, const int32_t* rp, const int32_t* ci, const double* lam, const double* x,
+                            double* g, cudaStream_t st) {
+  grad_val_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, rp, ci, lam, x, g);
+  return cudaGetLastError();
+}
+
+}  // namespace pc

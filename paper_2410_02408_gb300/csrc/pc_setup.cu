@@ -1,0 +1,258 @@
+// Block-Jacobi setup (Sec. 3.2-3.3): extract each diagonal block A_kk from CSR and
+// factor it, A_kk = L_k L_k^T, then form L_k^{-1} and M_k^{-1} = L_k^{-T} L_k^{-1}.
+//
+// One warp owns one warp unit (whole blocks, see pc_common.cuh).  The unit's blocks sit
+// in shared memory as dense rows (row stride bs+1): lane l owns unit row l (and l+32 for
+// blocks of 33..64 rows).  Extraction, the right-looking Cholesky (lanes = rows, lockstep
+// over the pivot column), the triangular inverse (lanes = columns, independent) and the
+// products for M^{-1} all run from shared memory; the results are written straight into
+// the coalesced unit layouts used by the apply kernels.
+#include "pc_kernels.cuh"
+
+namespace pc {
+
+template <typename VT, typename FT>
+__global__ void __launch_bounds__(128) setup_kernel(SetupArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Layout L = a.lay;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  const int bs = L.bs;
+  const int ld = bs + 1;
+  FT* As = reinterpret_cast<FT*>(smem_raw) + (size_t)warp * 2 * L.U * ld;
+  FT* Xs = As + (size_t)L.U * ld;
+  const VT* va = reinterpret_cast<const VT*>(a.val);
+  FT* Mo = reinterpret_cast<FT*>(a.minv);
+  FT* Lo = reinterpret_cast<FT*>(a.linv);
+  const int64_t uM = unit_elems_minv(L), uL = unit_elems_linv(L);
+
+  for (int64_t u = (int64_t)blockIdx.x * nw + warp; u < L.n_units; u += (int64_t)gridDim.x * nw) {
+    const int64_t urow0 = u * L.U;
+    // ---- zero, then extract (identity on rows past n)
+    for (int t = lane; t < L.U * ld; t += 32) {
+      As[t] = FT(0);
+      Xs[t] = FT(0);
+    }
+    __syncwarp();
+    for (int s = 0; s < L.S; ++s) {
+      const int rho = lane + 32 * s;
+      if (rho >= L.U) continue;
+      const int i = rho % bs;
+      const int64_t row = urow0 + rho;
+      if (row < L.n) {
+        const int64_t bstart = row - i;
+        const int32_t e0 = a.row_ptr[row], e1 = a.row_ptr[row + 1];
+        for (int32_t e = e0; e < e1; ++e) {
+          const int64_t c = a.col[e];
+          if (c >= bstart && c < bstart + bs) As[rho * ld + (int)(c - bstart)] = (FT)va[e];
+        }
+      } else {
+        As[rho * ld + i] = FT(1);
+      }
+    }
+    __syncwarp();
+    // ---- per-block pivot scale: max diagonal entry of the block
+    FT dmax[2] = {FT(0), FT(0)};
+    for (int s = 0; s < L.S; ++s) {
+      const int rho = lane + 32 * s;
+      if (rho >= L.U) continue;
+      const int gb = rho - rho % bs;
+      FT m = FT(0);
+      for (int t = 0; t < bs; ++t)
+        if (urow0 + gb + t < L.n) m = max(m, As[(gb + t) * ld + t]);
+      dmax[s] = m;
+    }
+    // ---- right-looking Cholesky, lanes = rows
+    for (int j = 0; j < bs; ++j) {
+      for (int s = 0; s < L.S; ++s) {
+        const int rho = lane + 32 * s;
+        if (rho >= L.U) continue;
+        if (rho % bs == j) {
+          FT d = As[rho * ld + j];
+          if (urow0 + rho < L.n && (!(d > FT(a.tol) * dmax[s]) || !isfinite((double)d))) {
+            const unsigned long long blk = (unsigned long long)((urow0 + rho) / bs);
+            atomicMin(a.failed, blk);
+            d = FT(1);
+          }
+          As[rho * ld + j] = sqrt(d);
+        }
+      }
+      __syncwarp();
+      for (int s = 0; s < L.S; ++s) {
+        const int rho = lane + 32 * s;
+        if (rho >= L.U) continue;
+        const int i = rho % bs;
+        if (i > j) {
+          const int gb = rho - i;
+          As[rho * ld + j] = As[rho * ld + j] / As[(gb + j) * ld + j];
+        }
+      }
+      __syncwarp();
+      for (int s = 0; s < L.S; ++s) {
+        const int rho = lane + 32 * s;
+        if (rho >= L.U) continue;
+        const int i = rho % bs;
+        if (i > j) {
+          const int gb = rho - i;
+          const FT lij = As[rho * ld + j];
+          for (int k = j + 1; k <= i; ++k) As[rho * ld + k] = fma(-lij, As[(gb + k) * ld + j], As[rho * ld + k]);
+        }
+      }
+      __syncwarp();
+    }
+    // ---- X = L^{-1}: lane owns column c = its row index in the block
+    for (int s = 0; s < L.S; ++s) {
+      const int rho = lane + 32 * s;
+      if (rho >= L.U) continue;
+      const int c = rho % bs;
+      const int gb = rho - c;
+      for (int i = c; i < bs; ++i) {
+        FT acc = (i == c) ? FT(1) : FT(0);
+        for (int k = c; k < i; ++k) acc = fma(-As[(gb + i) * ld + k], Xs[(gb + k) * ld + c], acc);
+        Xs[(gb + i) * ld + c] = acc / As[(gb + i) * ld + i];
+      }
+    }
+    __syncwarp();
+    // ---- M^{-1} (circulant rows) and L^{-1} (by diagonals), coalesced unit stores
+    FT* Mu = Mo + u * uM;
+    FT* Lu = Lo + u * uL;
+    for (int s = 0; s < L.S; ++s) {
+      const int rho = lane + 32 * s;
+      const bool valid = rho < L.U;
+      const int i = valid ? rho % bs : 0;
+      const int gb = valid ? rho - i : 0;
+      for (int k = 0; k <= L.K; ++k) {
+        FT acc = FT(0);
+        if (valid) {
+          int j = i + k;
+          if (j >= bs) j -= bs;
+          const int m0 = i > j ? i : j;
+          for (int m = m0; m < bs; ++m) acc = fma(Xs[(gb + m) * ld + i], Xs[(gb + m) * ld + j], acc);
+        }
+        Mu[(k * L.S + s) * 32 + lane] = acc;
+      }
+      for (int k = 0; k < bs; ++k) {
+        const FT v = (valid && i >= k) ? Xs[rho * ld + (i - k)] : FT(0);
+        Lu[(k * L.S + s) * 32 + lane] = v;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Dense copy of the diagonal blocks (bit-exact value copy; rows past n are zero).
+template <typename VT>
+__global__ void extract_kernel(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                               const VT* __restrict__ va, int32_t bs, int64_t nrows_pad, double* __restrict__ out) {
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < nrows_pad;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = row / bs;
+    const int i = (int)(row % bs);
+    double* o = out + (k * bs + i) * bs;
+    for (int j = 0; j < bs; ++j) o[j] = 0.0;
+    if (row < n) {
+      const int64_t bstart = k * bs;
+      for (int32_t e = rp[row]; e < rp[row + 1]; ++e) {
+        const int64_t c = ci[e];
+        if (c >= bstart && c < bstart + bs) o[c - bstart] = (double)va[e];
+      }
+    }
+  }
+}
+
+// Unit layout -> dense blocks.  which = 0: L^{-1}; which = 1: M^{-1}.
+template <typename FT>
+__global__ void get_factor_kernel(Layout L, const FT* __restrict__ fac, int which, double* __restrict__ out) {
+  const int bs = L.bs;
+  const int64_t total = L.n_blocks * (int64_t)bs * bs;
+  const int64_t uM = unit_elems_minv(L), uL = unit_elems_linv(L);
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = t / ((int64_t)bs * bs);
+    const int i = (int)((t / bs) % bs);
+    const int j = (int)(t % bs);
+    const int64_t u = k / L.G;
+    const int g = (int)(k % L.G);
+    double v;
+    if (which == 0) {
+      if (j > i) {
+        v = 0.0;
+      } else {
+        const int rho = g * bs + i;
+        v = (double)fac[u * uL + ((i - j) * L.S + rho / 32) * 32 + (rho & 31)];
+      }
+    } else {
+      int d = j - i;
+      if (d < 0) d += bs;
+      int row = i;
+      if (d > L.K) {
+        d = i - j;
+        if (d < 0) d += bs;
+        row = j;
+      }
+      const int rho = g * bs + row;
+      v = (double)fac[u * uM + (d * L.S + rho / 32) * 32 + (rho & 31)];
+    }
+    out[t] = v;
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+template <typename VT, typename FT>
+static cudaError_t launch_setup_t(const SetupArgs& a, cudaStream_t st) {
+  const Layout& L = a.lay;
+  const size_t per_warp = (size_t)2 * L.U * (L.bs + 1) * sizeof(FT);
+  int warps = 4;
+  while (warps > 1 && per_warp * warps > 200 * 1024) --warps;
+  const size_t smem = per_warp * warps;
+  cudaError_t e = cudaFuncSetAttribute(setup_kernel<VT, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, setup_kernel<VT, FT>, warps * 32, smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) occ = 1;
+  int64_t need = (L.n_units + warps - 1) / warps;
+  int64_t grid = (int64_t)sms * occ * 4;
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  setup_kernel<VT, FT><<<(unsigned)grid, warps * 32, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_setup(const SetupArgs& a, bool val_f32, bool fac_f32, cudaStream_t st) {
+  if (!val_f32 && !fac_f32) return launch_setup_t<double, double>(a, st);
+  if (!val_f32 && fac_f32) return launch_setup_t<double, float>(a, st);
+  if (val_f32 && fac_f32) return launch_setup_t<float, float>(a, st);
+  return launch_setup_t<float, double>(a, st);
+}
+
+cudaError_t launch_extract(int64_t n, const int32_t* rp, const int32_t* ci, const void* va, bool val_f32,
+                           int32_t bs, double* out, cudaStream_t st) {
+  const int64_t nb = (n + bs - 1) / bs;
+  const int64_t rows = nb * bs;
+  int64_t grid = (rows + 255) / 256;
+  if (grid > 65535 * 8) grid = 65535 * 8;
+  if (val_f32)
+    extract_kernel<float><<<(unsigned)grid, 256, 0, st>>>(n, rp, ci, (const float*)va, bs, rows, out);
+  else
+    extract_kernel<double><<<(unsigned)grid, 256, 0, st>>>(n, rp, ci, (const double*)va, bs, rows, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_get_factor(const Layout& L, const void* fac, bool fac_f32, int which, double* out,
+                              cudaStream_t st) {
+  const int64_t total = L.n_blocks * (int64_t)L.bs * L.bs;
+  int64_t grid = (total + 255) / 256;
+  if (grid > 65535 * 8) grid = 65535 * 8;
+  if (grid < 1) grid = 1;
+  if (fac_f32)
+    get_factor_kernel<float><<<(unsigned)grid, 256, 0, st>>>(L, (const float*)fac, which, out);
+  else
+    get_factor_kernel<double><<<(unsigned)grid, 256, 0, st>>>(L, (const double*)fac, which, out);
+  return cudaGetLastError();
+}
+
+}  // namespace pc
