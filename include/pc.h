@@ -184,6 +184,32 @@ pc_status pcg_solve(const pc_csr *A, int32_t block_size, const double *b, double
 pc_status pcg_solve_h(pc_handle *h, const double *b, double *x, double tol, int32_t max_iter,
                       pc_solve_info *info, void *stream);
 
+/* pcg_solve_noalloc - the same solve as pcg_solve (same kernels, same results), for
+ * callers that cannot allocate device memory.  The paper has no counterpart; this is a
+ * deployment variant.  Examples of such callers: code that runs while a stream is being
+ * captured into a CUDA graph (cudaMalloc/cudaFree are not stream-ordered and cudaFree
+ * synchronises the device), plug-ins hosted by a framework whose caching allocator owns
+ * the device memory, and latency-critical loops that must not enter the driver's
+ * allocator.  The caller passes only inputs and outputs (A, b, x as in pcg_solve); every
+ * byte of scratch (block factors, four CG vectors, reduction partials, barrier words)
+ * comes from one fixed device array of PC_NOALLOC_SCRATCH_BYTES that the library defines
+ * statically, so every GPU that loads libpc holds that much memory until the process exits.
+ *   Limit: the problem must fit, i.e. roughly (K+1 + bs) * n * e + 32 n bytes plus a few KB
+ *   for factors of element size e (8 for PC_PREC_FP64, 4 otherwise), K = bs/2, with the
+ *   factor arrays padded to whole 32-row warp units; larger problems return
+ *   PC_ERR_INVALID_ARG before any work is enqueued.
+ *   The first call on each device looks up the array's device address (cudaGetSymbolAddress
+ *   with that device current) and caches it; make that first call before any stream
+ *   capture.  All calls share the one array and it keeps the previous call's contents (the
+ *   call clears what must start at zero): calls that overlap on the GPU (different
+ *   streams or threads on the same device) race and must be serialised by the caller.
+ *   No cudaMalloc, cudaFree or allocating library routine is called; info->solve_ms and
+ *   info->setup_ms are not measured (0). */
+#define PC_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+pc_status pcg_solve_noalloc(const pc_csr *A, int32_t block_size, const double *b, double *x,
+                            double tol, int32_t max_iter, int32_t prec, pc_solve_info *info,
+                            void *stream);
+
 /* pc_grad_val - adjoint of x = A^{-1} b with respect to the stored entries of A:
  * grad_val[e] = -lambda[row(e)] * x[col(e)] for every stored entry e, where lambda solves
  * A^T lambda = dL/dx (A symmetric here).  Device arrays: lambda, x [n]; grad_val [nnz]. */
