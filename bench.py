@@ -56,7 +56,29 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-iters", type=int, default=0, help="oracle CG iterations per sample (0 = auto)")
+    ap.add_argument("--ctas-per-sm", type=int, default=0, help="persistent CG CTAs per SM (0 = occupancy max)")
+    ap.add_argument("--profile", action="store_true",
+                    help="one solve of the workload and nothing else (for ncu captures); prints a short line")
     return ap.parse_args()
+
+
+def run_profile(args):
+    """A single setup + solve (max_iter may cut it short) for profiler captures."""
+    import torch
+
+    import paper_2410_02408_gb300 as pc
+
+    pc.load()
+    if args.ctas_per_sm:
+        pc.set_ctas_per_sm(args.ctas_per_sm)
+    A = W.diffusion3d(args.n, args.sigma)
+    b = torch.from_numpy(W.rhs(A.n, 0)).cuda()
+    Ad = pc.csr(A)
+    x, info = pc.pcg(Ad, b, args.bs, tol=args.tol, max_iter=args.maxit, prec=args.prec, check=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": True, "n": A.n, "bs": args.bs, "prec": args.prec, "iterations": info["iterations"],
+                      "status": info["status"], "solve_ms": info["solve_ms"], "setup_ms": info["setup_ms"],
+                      "grid_ctas": info["grid_ctas"]}))
 
 
 # ---------------------------------------------------------------- byte accounting
@@ -264,6 +286,8 @@ def run_ours(args):
     import paper_2410_02408_gb300 as pc
 
     pc.load()
+    if args.ctas_per_sm:
+        pc.set_ctas_per_sm(args.ctas_per_sm)
     A = W.diffusion3d(args.n, args.sigma)
     b = W.rhs(A.n, 0)
     Ad = pc.csr(A)
@@ -399,6 +423,9 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.profile:
+        run_profile(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -274,7 +274,7 @@ static pc_status ensure_cg_workspace(pc_handle* h, cudaStream_t st) {
   if (!h->cg) s = dalloc(&h->cg, sizeof(double) * 4 * (size_t)h->A.n);
   if (s == PC_OK && !h->res) s = dalloc(&h->res, sizeof(double) * 4);
   if (s == PC_OK && !h->ctl) s = dalloc(&h->ctl, sizeof(pc::GridSync) + sizeof(pc::PcgOut));
-  if (s == PC_OK) s = dalloc(&h->part, sizeof(double) * 2 * (size_t)grid);
+  if (s == PC_OK) s = dalloc(&h->part, sizeof(double) * 4 * (size_t)grid);   // 2 buffers x 2 values
   if (s == PC_OK) s = dalloc(&h->split, sizeof(int64_t) * (size_t)(grid + 1));
   if (s != PC_OK) return s;
   PC_TRY(pc::launch_split(h->A.n, h->A.nnz, h->A.row_ptr, grid, h->split, st));

@@ -76,17 +76,17 @@ __host__ __device__ inline int64_t unit_elems_linv(const Layout& L) { return (in
 // Read-only for the whole kernel: non-coherent path, no L1 allocation.
 __device__ __forceinline__ double ld_stream(const double* p) {
   double v;
-  asm volatile("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
   return v;
 }
 __device__ __forceinline__ float ld_stream(const float* p) {
   float v;
-  asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
   return v;
 }
 __device__ __forceinline__ int32_t ld_stream(const int32_t* p) {
   int32_t v;
-  asm volatile("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
   return v;
 }
 // Read-only index data that is reused (row pointers): ordinary read-only path.
@@ -113,22 +113,25 @@ __device__ __forceinline__ double spmv_row(const int32_t* __restrict__ rp, const
   const int32_t s = ld_ro(rp + row);
   const int32_t e = ld_ro(rp + row + 1);
   double acc = 0.0;
-  int32_t k = s;
-  for (; k + 8 <= e; k += 8) {
+  // Chunks of 8 entries: all index/value loads of a chunk are issued before the gathers
+  // (clamped to the row's last entry, so every load is in bounds), then the products are
+  // accumulated in storage order for the entries that exist.
+  for (int32_t k0 = s; k0 < e; k0 += 8) {
     int32_t c[8];
     VT v[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
-      c[t] = ld_stream(ci + k + t);
-      v[t] = ld_stream(va + k + t);
+      const int32_t k = min(k0 + t, e - 1);
+      c[t] = ld_stream(ci + k);
+      v[t] = ld_stream(va + k);
     }
     double xv[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) xv[t] = ld_x<COHERENT>(x + c[t]);
 #pragma unroll
-    for (int t = 0; t < 8; ++t) acc = fma((double)v[t], xv[t], acc);
+    for (int t = 0; t < 8; ++t)
+      if (k0 + t < e) acc = fma((double)v[t], xv[t], acc);
   }
-  for (; k < e; ++k) acc = fma((double)ld_stream(va + k), ld_x<COHERENT>(x + ld_stream(ci + k)), acc);
   return acc;
 }
 
@@ -350,10 +353,10 @@ __device__ __forceinline__ void block_sum(double* v, double* sm) {
 
 // ------------------------------------------------------------------ grid barrier
 struct GridSync {
-  unsigned int count;
-  unsigned int gen;
-  int status;       // first error code raised on the device (0 = none)
-  int where;        // diagnostic: barrier index that timed out
+  unsigned int count;   // arrivals, monotonic over the launch (wraps safely)
+  unsigned int pad;
+  int status;           // first error code raised on the device (0 = none)
+  int where;            // diagnostic: barrier index that timed out
 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -361,87 +364,65 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned* p, unsigned v) {
-  unsigned old;
-  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-  return old;
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ int ld_volatile_i32(const int* p) { return *(const volatile int*)p; }
 
-// Grid-wide sum of NV per-thread values with a barrier: every CTA leaves with the
-// same totals in v[] (fixed summation order, independent of arrival order).  The last
-// CTA to arrive sums the per-CTA partials; the others spin (bounded) on a generation
-// counter.  Returns false if the kernel must stop (timeout here or an error elsewhere).
-// part: gridDim.x * NV doubles; res: NV doubles (both device workspace).
-// sm: NV*32 doubles of shared memory; flag: 4 ints of shared memory.
+// Grid-wide sum of NV per-thread values plus a barrier; every CTA leaves with the same
+// totals in v[].  Barrier number `bar` (0, 1, 2, ... in program order, identical in every
+// CTA) completes when the arrival counter reaches (bar+1) * gridDim.x: each CTA adds one
+// with release semantics and thread 0 polls with acquire semantics under a clock64
+// budget.  Each CTA then sums the per-CTA partials itself in CTA-index order, so the
+// result is the same in every CTA and from run to run.  Partials are double-buffered by
+// the barrier's parity (a CTA can run at most one barrier ahead of the slowest reader).
+// Returns false if the kernel must stop (a timeout here or an error raised elsewhere).
+// part: 2 * gridDim.x * NV doubles; sm: NV*32 doubles and flag: 4 ints of shared memory.
 template <int NV>
-__device__ __forceinline__ bool grid_allreduce(double* v, double* part, double* res, GridSync* gs,
-                                               long long budget, double* sm, int* flag, int where) {
+__device__ __forceinline__ bool grid_allreduce(double* v, double* part, GridSync* gs, long long budget,
+                                               double* sm, int* flag, int bar) {
   if constexpr (NV > 0) block_sum<NV>(v, sm);
   else __syncthreads();   // flag[] may still be read from the previous call
+  const unsigned G = gridDim.x;
+  double* pbuf = part + (size_t)(bar & 1) * G * (NV > 0 ? NV : 1);
   if (threadIdx.x == 0) {
-    flag[0] = 0;
     flag[2] = 0;
     if (ld_volatile_i32(&gs->status) != 0) {
       flag[2] = 1;
     } else {
       if constexpr (NV > 0) {
 #pragma unroll
-        for (int i = 0; i < NV; ++i) __stcg(part + (size_t)blockIdx.x * NV + i, v[i]);
+        for (int i = 0; i < NV; ++i) __stcg(pbuf + (size_t)blockIdx.x * NV + i, v[i]);
       }
-      const unsigned my_gen = ld_acquire_u32(&gs->gen);
-      __threadfence();
-      const unsigned old = atom_add_acq_rel_u32(&gs->count, 1u);
-      flag[1] = (int)my_gen;
-      flag[0] = (old == gridDim.x - 1) ? 1 : 0;
-      if (!flag[0]) {
-        const long long t0 = clock64();
-        while (ld_acquire_u32(&gs->gen) == my_gen) {
-          if (clock64() - t0 > budget) {
-            if (atomicCAS(&gs->status, 0, ST_TIMEOUT) == 0) gs->where = where;
-            flag[2] = 1;
-            break;
-          }
-          if (ld_volatile_i32(&gs->status) != 0) {
-            flag[2] = 1;
-            break;
-          }
+      red_release_add_u32(&gs->count, 1u);
+      const unsigned target = (unsigned)(bar + 1) * G;
+      const long long t0 = clock64();
+      while ((int)(ld_acquire_u32(&gs->count) - target) < 0) {
+        if (clock64() - t0 > budget) {
+          if (atomicCAS(&gs->status, 0, ST_TIMEOUT) == 0) gs->where = bar;
+          flag[2] = 1;
+          break;
+        }
+        if (ld_volatile_i32(&gs->status) != 0) {
+          flag[2] = 1;
+          break;
         }
       }
     }
   }
   __syncthreads();
   if (flag[2]) return false;
-  if (flag[0]) {
-    // last arriver: reduce the partials of all CTAs in index order
-    __threadfence();
-    if constexpr (NV > 0) {
-      double acc[NV];
-#pragma unroll
-      for (int i = 0; i < NV; ++i) acc[i] = 0.0;
-      for (int c = threadIdx.x; c < (int)gridDim.x; c += blockDim.x) {
-#pragma unroll
-        for (int i = 0; i < NV; ++i) acc[i] += __ldcg(part + (size_t)c * NV + i);
-      }
-      block_sum<NV>(acc, sm);
-      if (threadIdx.x == 0) {
-#pragma unroll
-        for (int i = 0; i < NV; ++i) __stcg(res + i, acc[i]);
-      }
-    }
-    if (threadIdx.x == 0) {
-      gs->count = 0u;
-      __threadfence();
-      st_release_u32(&gs->gen, (unsigned)flag[1] + 1u);
-    }
-    __syncthreads();
-  }
   if constexpr (NV > 0) {
+    double acc[NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) v[i] = __ldcg(res + i);
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    for (unsigned c = threadIdx.x; c < G; c += blockDim.x) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i) acc[i] += __ldcg(pbuf + (size_t)c * NV + i);
+    }
+    block_sum<NV>(acc, sm);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = acc[i];
   }
   return true;
 }

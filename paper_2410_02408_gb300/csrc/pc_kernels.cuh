@@ -41,8 +41,8 @@ struct PcgArgs {
   double* z;
   double* p;
   double* q;
-  double* part;          // gridDim * 2 doubles
-  double* res;           // 2 doubles
+  double* part;          // 2 * gridDim * 2 doubles (double-buffered per-CTA partials)
+  double* res;           // unused
   const int64_t* split;  // gridDim + 1 SpMV row boundaries
   GridSync* gs;
   PcgOut* out;

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(256, 4) pcg_kernel(const PcgArgs a) {
       st_vec(a.r + row, bi - ax);
       v[0] = fma(bi, bi, v[0]);
     }
-    if (!grid_allreduce<1>(v, a.part, a.res, a.gs, a.budget, sm, flag, bar++)) return;
+    if (!grid_allreduce<1>(v, a.part, a.gs, a.budget, sm, flag, bar++)) return;
     bb = v[0];
   }
   const double bnorm = sqrt(bb);
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(256, 4) pcg_kernel(const PcgArgs a) {
           v[1] = fma(rv[s], rv[s], v[1]);
         }
       }
-      if (!grid_allreduce<2>(v, a.part, a.res, a.gs, a.budget, sm, flag, bar++)) return;
+      if (!grid_allreduce<2>(v, a.part, a.gs, a.budget, sm, flag, bar++)) return;
       rho = v[0];
       rr = v[1];
     }
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(256, 4) pcg_kernel(const PcgArgs a) {
           st_vec(a.q + row, qi);
           v[0] = fma(ld_vec(a.p + row), qi, v[0]);
         }
-        if (!grid_allreduce<1>(v, a.part, a.res, a.gs, a.budget, sm, flag, bar++)) return;
+        if (!grid_allreduce<1>(v, a.part, a.gs, a.budget, sm, flag, bar++)) return;
         pq = v[0];
       }
       if (!(pq > 0.0) || !isfinite(pq)) {
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(256, 4) pcg_kernel(const PcgArgs a) {
             v[1] = fma(rv[s], rv[s], v[1]);
           }
         }
-        if (!grid_allreduce<2>(v, a.part, a.res, a.gs, a.budget, sm, flag, bar++)) return;
+        if (!grid_allreduce<2>(v, a.part, a.gs, a.budget, sm, flag, bar++)) return;
         rz = v[0];
         rr = v[1];
       }
@@ -159,19 +159,32 @@ __global__ void __launch_bounds__(256, 4) pcg_kernel(const PcgArgs a) {
       if (sqrt(rr) <= tol * bnorm) {
         for (int64_t row = row0 + tid; row < row1; row += blockDim.x)
           st_vec(a.x + row, fma(alpha, ld_vec(a.p + row), ld_vec(a.x + row)));
-        if (!grid_allreduce<0>(nullptr, a.part, a.res, a.gs, a.budget, sm, flag, bar++)) return;
+        if (!grid_allreduce<0>(nullptr, a.part, a.gs, a.budget, sm, flag, bar++)) return;
         conv = true;
         break;
       }
       const double beta = rz / rho;
       rho = rz;
-      // ---- C: x += alpha p; p = z + beta p
-      for (int64_t row = row0 + tid; row < row1; row += blockDim.x) {
-        const double pi = ld_vec(a.p + row);
-        st_vec(a.x + row, fma(alpha, pi, ld_vec(a.x + row)));
-        st_vec(a.p + row, fma(beta, pi, ld_vec(a.z + row)));
+      // ---- C: x += alpha p; p = z + beta p  (4 rows per thread in flight)
+      for (int64_t base = row0 + tid; base < row1; base += 4 * (int64_t)blockDim.x) {
+        double pv[4], xv[4], zv[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int64_t row = min(base + t * (int64_t)blockDim.x, row1 - 1);
+          pv[t] = ld_vec(a.p + row);
+          xv[t] = ld_vec(a.x + row);
+          zv[t] = ld_vec(a.z + row);
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int64_t row = base + t * (int64_t)blockDim.x;
+          if (row < row1) {
+            st_vec(a.x + row, fma(alpha, pv[t], xv[t]));
+            st_vec(a.p + row, fma(beta, pv[t], zv[t]));
+          }
+        }
       }
-      if (!grid_allreduce<0>(nullptr, a.part, a.res, a.gs, a.budget, sm, flag, bar++)) return;
+      if (!grid_allreduce<0>(nullptr, a.part, a.gs, a.budget, sm, flag, bar++)) return;
     }
     // ---- true residual r = b - A x
     {
@@ -181,7 +194,7 @@ __global__ void __launch_bounds__(256, 4) pcg_kernel(const PcgArgs a) {
         st_vec(a.r + row, ri);
         v[0] = fma(ri, ri, v[0]);
       }
-      if (!grid_allreduce<1>(v, a.part, a.res, a.gs, a.budget, sm, flag, bar++)) return;
+      if (!grid_allreduce<1>(v, a.part, a.gs, a.budget, sm, flag, bar++)) return;
       tt = v[0];
     }
     if (!conv) break;                         // breakdown / no convergence: report and stop

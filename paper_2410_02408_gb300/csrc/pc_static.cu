@@ -91,7 +91,7 @@ extern "C" pc_status pcg_solve_noalloc(const pc_csr* A, int32_t block_size, cons
   const size_t sz_linv = round256(es * (size_t)(L.n_units * pc::unit_elems_linv(L)));
   const size_t sz_fail = 256;
   const size_t sz_vec = round256(sizeof(double) * 4 * n);
-  const size_t sz_part = round256(sizeof(double) * 2 * (size_t)grid);
+  const size_t sz_part = round256(sizeof(double) * 4 * (size_t)grid);
   const size_t sz_res = 256;
   const size_t sz_split = round256(sizeof(int64_t) * (size_t)(grid + 1));
   const size_t sz_ctl = round256(sizeof(pc::GridSync) + sizeof(pc::PcgOut));
