@@ -255,6 +255,23 @@ void pc_set_wait_budget(int64_t cycles);
 /* Number of CTAs per SM used by the persistent CG kernel (0 = occupancy maximum). */
 void pc_set_ctas_per_sm(int32_t ctas);
 
+/* CG engine of pcg_solve / pcg_solve_h: 0 = CUDA-graph loop (a device-driven `while`
+ * conditional node over three full-occupancy kernels per iteration; the default),
+ * 1 = one persistent cooperative kernel with grid-wide barriers.  Both compute the same
+ * recurrences; reductions are fixed-order in each.  Any other value restores the default
+ * (or the PC_CG_ENGINE environment variable: "graph" / "persistent"). */
+void pc_set_cg_engine(int32_t engine);
+
+/* Phase trace of the last pcg_solve_h on h, when the environment variable
+ * PC_TRACE_BARRIERS=N (N > 0) was set for that solve: out[0] is the device globaltimer (ns)
+ * at kernel start and out[k] the time after the k-th grid-wide synchronisation (entries
+ * never reached are 0).  Copies at most max_entries values to the HOST array out and
+ * returns how many were copied (0 if tracing was off).  Synchronous.
+ * With the graph engine and PC_CG_PROFILE=1 (the loop body kernels are then launched one by
+ * one from the host, with events around each) it returns 3 entries instead: the mean
+ * nanoseconds per iteration of the SpMV, preconditioner and vector-update kernels. */
+int32_t pc_get_trace(const pc_handle *h, int64_t *out, int32_t max_entries);
+
 /* Static description of a status code. */
 const char *pc_status_string(int32_t status);
 

@@ -14,7 +14,7 @@ from dataclasses import dataclass
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libpc.so")
+LIB_PATH = os.environ.get("PC_LIB_PATH") or os.path.join(HERE, "libpc.so")
 
 PC_OK, PC_ERR_INVALID_ARG, PC_ERR_NOT_SPD, PC_ERR_BREAKDOWN = 0, 1, 2, 3
 PC_ERR_NO_CONVERGENCE, PC_ERR_TIMEOUT, PC_ERR_CUDA, PC_ERR_OOM = 4, 5, 6, 7
@@ -95,8 +95,10 @@ def lib():
         "pc_grad_val": (_I32, [ctypes.POINTER(pc_csr), _P, _P, _P, _P]),
         "pcg_solve_batched": (_I32, [ctypes.POINTER(pc_batch), _P, _P, _D, _I32, _I32, _P, _P, _P,
                                      ctypes.POINTER(pc_solve_info), _P]),
+        "pc_get_trace": (_I32, [_P, _P, _I32]),
         "pc_set_wait_budget": (None, [_I64]),
         "pc_set_ctas_per_sm": (None, [_I32]),
+        "pc_set_cg_engine": (None, [_I32]),
         "pc_status_string": (ctypes.c_char_p, [_I32]),
         "pc_version": (_I32, []),
     }
@@ -236,6 +238,12 @@ class Handle:
     def kappa(self, v0, max_steps: int = 200, tol: float = 1e-12, reorth: bool = True):
         return _kappa(self._h, self.A, v0, max_steps, tol, reorth)
 
+    def trace(self, max_entries: int = 4096) -> np.ndarray:
+        """Barrier timestamps (ns) of the last solve when PC_TRACE_BARRIERS was set."""
+        out = np.zeros(max_entries, dtype=np.int64)
+        k = lib().pc_get_trace(self._h, out.ctypes.data, max_entries)
+        return out[:k]
+
 
 def setup(A, block_size: int, tol: float = 0.0, prec: str = "fp64") -> Handle:
     return Handle(A, block_size, tol, prec)
@@ -339,3 +347,8 @@ def set_wait_budget(cycles: int):
 
 def set_ctas_per_sm(ctas: int):
     lib().pc_set_ctas_per_sm(int(ctas))
+
+
+def set_cg_engine(engine: str):
+    """"graph" (default): CUDA-graph loop over three kernels; "persistent": one cooperative kernel."""
+    lib().pc_set_cg_engine({"graph": 0, "persistent": 1}.get(engine, -1))

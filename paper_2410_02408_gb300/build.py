@@ -38,10 +38,15 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list | None = None) -> str:
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, extra: list | None = None, out: str | None = None,
+          objdir: str | None = None) -> str:
+    """Compile (when stale) and link libpc.so; `extra` adds nvcc flags, `out`/`objdir` redirect
+    the library and objects (used to build tuning variants side by side)."""
+    target = out or OUT
+    bdir = objdir or BUILD
+    if not force and out is None and not _stale():
         return OUT
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
     flags += list(extra or [])
@@ -49,7 +54,7 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
         flags += ["-Xptxas", "-v"]
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(bdir, os.path.basename(src) + ".o")
         cmd = [nvcc] + flags + ["-c", src, "-o", obj]
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:
@@ -61,13 +66,13 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
     if verbose:
         for _, err in results:
             print(err)
-    tmp = OUT + f".tmp{os.getpid()}"
+    tmp = target + f".tmp{os.getpid()}"
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results]
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError(f"link failed:\n{p.stderr}")
-    os.replace(tmp, OUT)
-    return OUT
+    os.replace(tmp, target)
+    return target
 
 
 if __name__ == "__main__":

@@ -33,12 +33,29 @@ struct pc_handle {
   unsigned char* ctl;    // GridSync + PcgOut
   int grid;
   int block;
+  unsigned long long* trace_d;   // optional barrier trace (PC_TRACE_BARRIERS)
+  int trace_len;
+  // graph engine
+  void* graph;           // instantiated loop graph (pc::cg_graph_create)
+  double* gbx;           // copies of b and x: 2 n
+  double* gpart;         // per-CTA partials
+  void* gscal;           // CG scalars
+  int64_t prof_ns[3];    // graph engine, profiling mode: mean ns per iteration of the 3 kernels
+  int prof_valid;
 };
 
 namespace {
 
 long long g_budget = 0;          // 0 = default
 int g_ctas_per_sm = 0;           // 0 = occupancy maximum
+int g_engine = -1;               // -1: from PC_CG_ENGINE (default graph); 0 graph; 1 persistent
+
+int cg_engine() {
+  if (g_engine >= 0) return g_engine;
+  const char* e = getenv("PC_CG_ENGINE");
+  if (e && strcmp(e, "persistent") == 0) return 1;
+  return 0;
+}
 const long long kDefaultBudget = 4000000000LL;
 
 long long wait_budget() {
@@ -109,6 +126,8 @@ void pc_set_wait_budget(int64_t cycles) { g_budget = cycles > 0 ? (long long)cyc
 
 void pc_set_ctas_per_sm(int32_t ctas) { g_ctas_per_sm = ctas > 0 ? ctas : 0; }
 
+void pc_set_cg_engine(int32_t engine) { g_engine = (engine == 0 || engine == 1) ? engine : -1; }
+
 const char* pc_status_string(int32_t s) {
   switch (s) {
     case PC_OK: return "ok";
@@ -134,8 +153,29 @@ pc_status pc_destroy(pc_handle* h) {
   dfree(h->res);
   dfree(h->split);
   dfree(h->ctl);
+  dfree(h->trace_d);
+  if (h->graph) pc::cg_graph_destroy(h->graph);
+  dfree(h->gbx);
+  dfree(h->gpart);
+  dfree(h->gscal);
   delete h;
   return PC_OK;
+}
+
+int32_t pc_get_trace(const pc_handle* h, int64_t* out, int32_t max_entries) {
+  if (!h || !out || max_entries <= 0) return 0;
+  if (h->prof_valid) {
+    const int n = max_entries < 3 ? max_entries : 3;
+    for (int i = 0; i < n; ++i) out[i] = h->prof_ns[i];
+    return n;
+  }
+  if (!h->trace_d) return 0;
+  const int n = max_entries < h->trace_len ? max_entries : h->trace_len;
+  if (cudaMemcpy(out, h->trace_d, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
 int64_t pc_handle_failed_block(const pc_handle* h) { return h ? h->failed_block : -1; }
@@ -257,9 +297,12 @@ pc_status pc_grad_val(const pc_csr* A, const double* lambda, const double* x, do
 
 // ------------------------------------------------------------------ PCG
 static pc_status ensure_cg_workspace(pc_handle* h, cudaStream_t st) {
-  const int block = 256;
+  const int block = pc::PCG_BLOCK;
   int per_sm = 0;
-  PC_TRY(pc::pcg_occupancy(h->L, h->val_f32, h->fac_f32, block, &per_sm));
+  pc::PcgArgs plan;
+  plan.lay = h->L;
+  pc::pcg_plan(plan, h->A.nnz, h->val_f32, h->fac_f32);
+  PC_TRY(pc::pcg_occupancy(h->L, h->val_f32, h->fac_f32, block, plan.sp.total, &per_sm));
   if (per_sm < 1) return PC_ERR_CUDA;
   if (g_ctas_per_sm > 0 && g_ctas_per_sm < per_sm) per_sm = g_ctas_per_sm;
   int grid = per_sm * sm_count();
@@ -271,7 +314,7 @@ static pc_status ensure_cg_workspace(pc_handle* h, cudaStream_t st) {
   h->part = nullptr;
   h->split = nullptr;
   pc_status s = PC_OK;
-  if (!h->cg) s = dalloc(&h->cg, sizeof(double) * 4 * (size_t)h->A.n);
+  if (!h->cg) s = dalloc(&h->cg, sizeof(double) * (4 * (size_t)h->A.n + 64));
   if (s == PC_OK && !h->res) s = dalloc(&h->res, sizeof(double) * 4);
   if (s == PC_OK && !h->ctl) s = dalloc(&h->ctl, sizeof(pc::GridSync) + sizeof(pc::PcgOut));
   if (s == PC_OK) s = dalloc(&h->part, sizeof(double) * 4 * (size_t)grid);   // 2 buffers x 2 values
@@ -283,6 +326,55 @@ static pc_status ensure_cg_workspace(pc_handle* h, cudaStream_t st) {
   return PC_OK;
 }
 
+// Graph engine: the CG loop is a CUDA graph `while` node over three kernels (pc_cg_graph.cu).
+static pc_status pcg_solve_graph(pc_handle* h, const double* b, double* x, double tol, int32_t max_iter,
+                                 pc_solve_info* info, cudaStream_t st) {
+  const int64_t n = h->A.n;
+  pc_status s = PC_OK;
+  if (!h->cg) s = dalloc(&h->cg, sizeof(double) * (4 * (size_t)n + 64));   // padded: bulk copies round up
+  if (s == PC_OK && !h->gbx) s = dalloc(&h->gbx, sizeof(double) * 2 * (size_t)n);
+  if (s == PC_OK && !h->gpart) s = dalloc(&h->gpart, sizeof(double) * (size_t)pc::cg_graph_partials());
+  if (s == PC_OK && !h->gscal) s = dalloc(&h->gscal, pc::cg_scalars_bytes());
+  if (s != PC_OK) return s;
+  if (!h->graph) {
+    PC_TRY(pc::cg_graph_create(&h->graph, h->L, h->A.row_ptr, h->A.col_idx, h->A.val, h->val_f32, h->minv,
+                               h->fac_f32, h->gbx, h->gbx + n, h->cg, h->cg + n, h->cg + 2 * n, h->cg + 3 * n,
+                               h->gpart, h->gscal, st));
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  PC_TRY(cudaEventCreate(&e0));
+  cudaError_t e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->gbx, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->gbx + n, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  pc::CgResult res;
+  memset(&res, 0, sizeof(res));
+  if (e == cudaSuccess) e = pc::cg_graph_solve(h->graph, tol, max_iter, 3, h->val_f32, h->fac_f32, st, &res);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(x, h->gbx + n, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return from_cuda(e);
+  const pc_status status = (pc_status)res.status;
+  h->prof_valid = res.kernel_us[0] > 0.0 ? 1 : 0;
+  for (int i = 0; i < 3; ++i) h->prof_ns[i] = (int64_t)(1000.0 * res.kernel_us[i]);
+  if (info) {
+    info->status = status;
+    info->iterations = res.iterations;
+    info->restarts = res.restarts;
+    info->rel_residual = res.rel_residual;
+    info->true_rel_residual = res.true_rel_residual;
+    info->solve_ms = ms;
+    info->grid_ctas = 0;
+    info->block_size = h->bs;
+    info->prec = h->prec;
+  }
+  return status;
+}
+
 pc_status pcg_solve_h(pc_handle* h, const double* b, double* x, double tol, int32_t max_iter, pc_solve_info* info,
                       void* stream) {
   if (info) {
@@ -291,11 +383,13 @@ pc_status pcg_solve_h(pc_handle* h, const double* b, double* x, double tol, int3
   }
   if (!h || !b || !x || !(tol >= 0.0) || max_iter < 0) return PC_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
+  if (cg_engine() == 0) return pcg_solve_graph(h, b, x, tol, max_iter, info, st);
   pc_status s = ensure_cg_workspace(h, st);
   if (s != PC_OK) return s;
   const int64_t n = h->A.n;
   pc::PcgArgs a;
   a.lay = h->L;
+  pc::pcg_plan(a, h->A.nnz, h->val_f32, h->fac_f32);
   a.rp = h->A.row_ptr;
   a.ci = h->A.col_idx;
   a.va = h->A.val;
@@ -315,6 +409,25 @@ pc_status pcg_solve_h(pc_handle* h, const double* b, double* x, double tol, int3
   a.max_iter = max_iter;
   a.max_restarts = 3;
   a.budget = wait_budget();
+  a.trace = nullptr;
+  a.trace_len = 0;
+  {
+    const char* tv = getenv("PC_TRACE_BARRIERS");
+    const int want = tv ? atoi(tv) : 0;
+    if (want > 0) {
+      if (!h->trace_d || h->trace_len != want) {
+        dfree(h->trace_d);
+        h->trace_d = nullptr;
+        h->trace_len = 0;
+        if (dalloc(&h->trace_d, sizeof(unsigned long long) * (size_t)want) == PC_OK) h->trace_len = want;
+      }
+      if (h->trace_d) {
+        PC_TRY(cudaMemsetAsync(h->trace_d, 0, sizeof(unsigned long long) * (size_t)h->trace_len, st));
+        a.trace = h->trace_d;
+        a.trace_len = h->trace_len;
+      }
+    }
+  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   PC_TRY(cudaEventCreate(&e0));
   cudaError_t e = cudaEventCreate(&e1);

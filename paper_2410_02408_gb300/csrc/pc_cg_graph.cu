@@ -1,0 +1,775 @@
+// Graph-driven block-Jacobi PCG: three full-occupancy kernels per iteration inside a CUDA
+// graph `while` conditional node, so the iteration never returns to the host.
+//
+//   before the loop   I1  r = b - A x, ||b||^2          I2  z = M^{-1} r, p = z, rho, ||r||^2
+//   loop body         A   q = A p, p.q  -> alpha       B   r -= alpha q, z = M^{-1} r, r.z, ||r||^2
+//                     C   x += alpha p, p = z + beta p
+//   after the loop    T   r = b - A x, ||b - A x||^2 (true residual)
+//
+// Each kernel reduces its per-CTA partial sums in its last CTA, in CTA order (fixed order:
+// bit-reproducible), and that CTA updates the CG scalars and the loop condition
+// (cudaGraphSetConditional).  The scalar recurrences and stopping rules are those of
+// Hestenes-Stiefel PCG: alpha = rho / p.q, beta = rho'/rho, stop when ||r|| <= tol ||b||,
+// with max_iter and breakdown checks in the order the iteration meets them.  The host
+// restarts from x (at most 3 times) when the true residual is above tol.
+//
+// Kernels are separate launches so each runs at full occupancy with its own register budget:
+// the SpMV streams the CSR with ordinary L1-allocating loads (neighbouring rows share the
+// cache lines of the column/value arrays) and keeps 8 gathers in flight per row.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <stdlib.h>
+
+#include <algorithm>
+#include <type_traits>
+
+#include "pc_kernels.cuh"
+#include "pc_tma.cuh"
+
+namespace pc {
+
+struct CgScalars {
+  double bb, rho, alpha, beta, rr, tt;
+  double tol;
+  int32_t it, max_iter;
+  int32_t status;   // ST_* of the solve
+  int32_t done;     // 1: stop all further work of this round
+  int32_t xupd;     // 1: x += alpha p due in kernel C
+  int32_t pupd;     // 1: p = z + beta p due in kernel C
+  int32_t cont;     // loop condition
+  int32_t pad;
+  unsigned int cnt[4];   // last-CTA counters of I/A, B, T
+};
+
+// Last-CTA fixed-order reduction of NV values; returns true in the last CTA, whose v[] then
+// holds the totals.  part: gridDim.x * NV doubles.
+template <int NV>
+__device__ __forceinline__ bool cg_last_cta(double* v, double* part, unsigned* counter, double* sm, int* is_last) {
+  block_sum<NV>(v, sm);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) __stcg(part + (size_t)blockIdx.x * NV + i, v[i]);
+    __threadfence();
+    const unsigned old = atomicAdd(counter, 1u);
+    *is_last = (old == gridDim.x - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!*is_last) return false;
+  __threadfence();
+  double acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+  for (int c = threadIdx.x; c < (int)gridDim.x; c += blockDim.x) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] += __ldcg(part + (size_t)c * NV + i);
+  }
+  block_sum<NV>(acc, sm);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = acc[i];
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
+// SpMV row with 8 loads in flight, L1-allocating CSR loads (x may have been written by the
+// previous kernel: kernel boundaries make it visible).  Called by full warps (rows past n
+// have an empty range): the entry count is made warp-uniform so a product slot is issued
+// only if some lane needs it (a fully masked FP64 instruction still costs FP64-pipe time),
+// and float values are widened on the integer pipe.
+template <typename VT>
+__device__ __forceinline__ double cg_row(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                         const VT* __restrict__ va, const double* __restrict__ x, int64_t row,
+                                         bool valid) {
+  const int32_t s = valid ? __ldg(rp + row) : 0;
+  const int32_t e = valid ? __ldg(rp + row + 1) : 0;
+  const int32_t cnt = e - s;
+  const int32_t wmax = __reduce_max_sync(FULL, cnt);
+  double acc = 0.0;
+  for (int32_t k0 = 0; k0 < wmax; k0 += 8) {
+    int32_t c[8];
+    VT v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int32_t k = s + min(k0 + t, max(cnt, 1) - 1);
+      c[t] = __ldg(ci + k);
+      v[t] = __ldg(va + k);
+    }
+    double xv[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) xv[t] = __ldg(x + c[t]);
+    const int rem = wmax - k0;   // warp-uniform
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      if (t < rem) {
+        const double pr = fma(from_ft(v[t]), xv[t], acc);
+        acc = (k0 + t < cnt) ? pr : acc;
+      }
+    }
+  }
+  return acc;
+}
+
+struct CgArgs {
+  Layout lay;
+  const int32_t* rp;
+  const int32_t* ci;
+  const void* va;
+  const void* minv;
+  const double* b;
+  double* x;
+  double *r, *z, *p, *q;
+  double* part;
+  CgScalars* s;
+  cudaGraphConditionalHandle cond;
+  int32_t in_graph;    // 0 when the body kernels are launched one by one (profiling mode)
+};
+
+// MODE 0 (I1): r = b - A x, sum b^2.  MODE 1 (A): q = A p, sum p q.  MODE 2 (T): r = b - A x, sum r^2.
+template <typename VT, int MODE>
+__global__ void __launch_bounds__(256) cg_spmv_kernel(const CgArgs a) {
+  __shared__ double sm[32];
+  __shared__ int is_last;
+  CgScalars* S = a.s;
+  if (MODE == 1 && *(volatile int*)&S->done) return;
+  const VT* va = reinterpret_cast<const VT*>(a.va);
+  const int64_t n = a.lay.n;
+  double acc = 0.0;
+  // warp-uniform trip count: every lane runs every iteration (rows past n are masked)
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = base + threadIdx.x;
+    const bool valid = row < n;
+    if (MODE == 1) {
+      const double qi = cg_row<VT>(a.rp, a.ci, va, a.p, row, valid);
+      if (valid) {
+        a.q[row] = qi;
+        acc = fma(__ldg(a.p + row), qi, acc);
+      }
+    } else {
+      const double ax = cg_row<VT>(a.rp, a.ci, va, a.x, row, valid);
+      if (valid) {
+        const double bi = __ldg(a.b + row);
+        const double ri = bi - ax;
+        a.r[row] = ri;
+        acc = MODE == 0 ? fma(bi, bi, acc) : fma(ri, ri, acc);
+      }
+    }
+  }
+  double v[1] = {acc};
+  if (!cg_last_cta<1>(v, a.part, &S->cnt[MODE == 2 ? 2 : 0], sm, &is_last)) return;
+  if (threadIdx.x != 0) return;
+  if (MODE == 0) {
+    S->bb = v[0];
+  } else if (MODE == 2) {
+    S->tt = v[0];
+  } else {
+    const double pq = v[0];
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      S->status = ST_BREAKDOWN;
+      S->done = 1;
+      S->xupd = 0;
+      S->pupd = 0;
+      S->cont = 0;
+      if (a.in_graph) cudaGraphSetConditional(a.cond, 0u);
+    } else {
+      S->alpha = S->rho / pq;
+      S->xupd = 1;
+    }
+  }
+}
+
+// RESTART (I2): z = M^{-1} r, p = z, rho, rr.  Otherwise (B): r -= alpha q, z = M^{-1} r.
+template <typename FT, int BS, bool RESTART>
+__global__ void __launch_bounds__(256) cg_precond_kernel(const CgArgs a) {
+  __shared__ double sm[64];
+  __shared__ int is_last;
+  CgScalars* S = a.s;
+  if (*(volatile int*)&S->done) return;
+  const Layout& L = a.lay;
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t tw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t uM = unit_elems_minv(L);
+  const FT* Mf = reinterpret_cast<const FT*>(a.minv);
+  const double alpha = RESTART ? 0.0 : S->alpha;
+  const bool zero_b = RESTART && S->bb == 0.0;
+  constexpr int NSLOT = (BS > 0 && BS <= 32) ? 1 : 2;
+  const int nslot = NSLOT == 1 ? 1 : L.S;
+  double v0 = 0.0, v1 = 0.0;
+  for (int64_t u = gw; u < L.n_units; u += tw) {
+    double rv[2] = {0.0, 0.0}, zv[2];
+    int64_t rows[2];
+    bool ok[2] = {false, false};
+#pragma unroll
+    for (int t = 0; t < NSLOT; ++t) {
+      if (t >= nslot) break;
+      bool vld;
+      const int rh = unit_row(L, lane, t, vld);
+      rows[t] = u * L.U + rh;
+      ok[t] = vld && rows[t] < L.n;
+      if (ok[t]) rv[t] = RESTART ? a.r[rows[t]] : fma(-alpha, a.q[rows[t]], a.r[rows[t]]);
+    }
+    unit_apply_inv<FT, BS, false>(L, Mf + u * uM, lane, rv, zv);
+#pragma unroll
+    for (int t = 0; t < NSLOT; ++t) {
+      if (t >= nslot) break;
+      if (!ok[t]) continue;
+      if (zero_b) {
+        a.x[rows[t]] = 0.0;
+        continue;
+      }
+      if (!RESTART) a.r[rows[t]] = rv[t];
+      a.z[rows[t]] = zv[t];
+      if (RESTART) a.p[rows[t]] = zv[t];
+      v0 = fma(rv[t], zv[t], v0);
+      v1 = fma(rv[t], rv[t], v1);
+    }
+  }
+  double v[2] = {v0, v1};
+  if (!cg_last_cta<2>(v, a.part, &S->cnt[1], sm, &is_last)) return;
+  if (threadIdx.x != 0) return;
+  const double bnorm = sqrt(S->bb);
+  const double rz = v[0];
+  S->rr = v[1];
+  if (zero_b) {
+    S->status = ST_OK;
+    S->done = 1;
+    S->cont = 0;
+    S->rr = 0.0;
+    return;
+  }
+  const bool conv = sqrt(v[1]) <= S->tol * bnorm;
+  int cont = 0;
+  if (RESTART) {
+    S->rho = rz;
+    S->xupd = 0;
+    S->pupd = 0;
+  } else {
+    S->it += 1;
+    S->beta = conv ? 0.0 : rz / S->rho;
+    if (!conv) S->rho = rz;
+  }
+  if (conv) {
+    S->pupd = 0;
+  } else if (S->it >= S->max_iter) {
+    S->status = ST_NO_CONV;
+    S->pupd = 0;
+  } else if (!(S->rho > 0.0) || !isfinite(S->rho)) {
+    S->status = ST_BREAKDOWN;
+    S->pupd = 0;
+  } else {
+    S->pupd = RESTART ? 0 : 1;
+    cont = 1;
+  }
+  S->cont = cont;
+  if (!RESTART && a.in_graph) cudaGraphSetConditional(a.cond, (unsigned)cont);
+}
+
+// Shared epilogue of the preconditioner kernels (last CTA, thread 0): update the scalars and
+// the loop condition from rz = r.z and rr = r.r.
+template <bool RESTART>
+__device__ __forceinline__ void cg_precond_epilogue(const CgArgs& a, double rz, double rr, bool zero_b) {
+  CgScalars* S = a.s;
+  const double bnorm = sqrt(S->bb);
+  S->rr = rr;
+  if (zero_b) {
+    S->status = ST_OK;
+    S->done = 1;
+    S->cont = 0;
+    S->rr = 0.0;
+    return;
+  }
+  const bool conv = sqrt(rr) <= S->tol * bnorm;
+  int cont = 0;
+  if (RESTART) {
+    S->rho = rz;
+    S->xupd = 0;
+    S->pupd = 0;
+  } else {
+    S->it += 1;
+    S->beta = conv ? 0.0 : rz / S->rho;
+    if (!conv) S->rho = rz;
+  }
+  if (conv) {
+    S->pupd = 0;
+  } else if (S->it >= S->max_iter) {
+    S->status = ST_NO_CONV;
+    S->pupd = 0;
+  } else if (!(S->rho > 0.0) || !isfinite(S->rho)) {
+    S->status = ST_BREAKDOWN;
+    S->pupd = 0;
+  } else {
+    S->pupd = RESTART ? 0 : 1;
+    cont = 1;
+  }
+  S->cont = cont;
+  if (!RESTART && a.in_graph) cudaGraphSetConditional(a.cond, (unsigned)cont);
+}
+
+// Staged preconditioner kernel: a CTA walks tiles of TU warp units; thread 0 streams each
+// tile's M^{-1} blocks and its r (and q) rows into shared memory with bulk asynchronous copies,
+// NST tiles ahead, and the warps apply M^{-1} from shared memory.  All operands were written
+// before this kernel started, so the bulk copies need no cross-proxy ordering.
+constexpr int CGP_NST = 3;
+struct CgPrecondPlan {
+  int tu;          // warp units per tile
+  int stage;       // bytes per stage
+  int off_r;       // r rows within a stage
+  int off_q;       // q rows within a stage
+  int smem;        // dynamic shared memory
+  int64_t tiles;   // tiles in the matrix
+};
+
+template <typename FT, int BS, bool RESTART>
+__global__ void __launch_bounds__(256) cg_precond_tma_kernel(const CgArgs a, const CgPrecondPlan pl) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  __shared__ double sm[64];
+  __shared__ int is_last;
+  __shared__ int okflag;
+  CgScalars* S = a.s;
+  if (*(volatile int*)&S->done) return;
+  const Layout& L = a.lay;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int64_t uM = unit_elems_minv(L);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(dsm);
+  unsigned char* stages = dsm + 128;
+  const double alpha = RESTART ? 0.0 : S->alpha;
+  const bool zero_b = RESTART && S->bb == 0.0;
+  constexpr int NSLOT = (BS > 0 && BS <= 32) ? 1 : 2;
+  const int nslot = NSLOT == 1 ? 1 : L.S;
+  const int64_t G = gridDim.x;
+  const int64_t nj = pl.tiles > (int64_t)blockIdx.x ? (pl.tiles - blockIdx.x + G - 1) / G : 0;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < CGP_NST; ++s) mbar_init(&mbar[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](int64_t j) {
+    const int s = (int)(j % CGP_NST);
+    const int64_t tile = blockIdx.x + j * G;
+    const int64_t u0 = tile * pl.tu;
+    const int64_t nu = min((int64_t)pl.tu, L.n_units - u0);
+    const int64_t row0 = u0 * L.U;
+    const int64_t rows = min(nu * L.U, L.n - row0);
+    const uint32_t fb = (uint32_t)(nu * uM * (int64_t)sizeof(FT));
+    const uint32_t vb = (uint32_t)(((rows * 8) + 15) & ~(int64_t)15);   // vectors are padded by the caller
+    unsigned char* st = stages + (size_t)s * pl.stage;
+    mbar_arrive_expect_tx(&mbar[s], fb + vb * (RESTART ? 1u : 2u));
+    bulk_g2s(st, reinterpret_cast<const FT*>(a.minv) + u0 * uM, fb, &mbar[s]);
+    bulk_g2s(st + pl.off_r, a.r + row0, vb, &mbar[s]);
+    if (!RESTART) bulk_g2s(st + pl.off_q, a.q + row0, vb, &mbar[s]);
+  };
+  if (threadIdx.x == 0)
+    for (int64_t j = 0; j < nj && j < CGP_NST; ++j) issue(j);
+  uint32_t parity = 0u;
+  double v0 = 0.0, v1 = 0.0;
+  for (int64_t j = 0; j < nj; ++j) {
+    const int s = (int)(j % CGP_NST);
+    if (threadIdx.x == 0) okflag = mbar_wait_bounded(&mbar[s], (parity >> s) & 1u, 4000000000LL) ? 1 : 0;
+    __syncthreads();
+    parity ^= 1u << s;
+    if (!okflag) {
+      if (threadIdx.x == 0) {
+        atomicCAS(&S->status, ST_OK, ST_TIMEOUT);
+        for (int64_t t = j + 1; t < nj && t < j + CGP_NST; ++t) {
+          const int s2 = (int)(t % CGP_NST);
+          mbar_wait_bounded(&mbar[s2], (parity >> s2) & 1u, 4000000000LL);
+        }
+      }
+      break;   // leaves this CTA's partials at zero; the status reports the failure
+    }
+    const int64_t tile = blockIdx.x + j * G;
+    const int64_t u = tile * pl.tu + warp;
+    const unsigned char* st = stages + (size_t)s * pl.stage;
+    if (warp < pl.tu && u < L.n_units) {
+      const double* sr = reinterpret_cast<const double*>(st + pl.off_r);
+      const double* sq = reinterpret_cast<const double*>(st + pl.off_q);
+      double rv[2] = {0.0, 0.0}, zv[2];
+      int64_t rows[2];
+      bool ok[2] = {false, false};
+#pragma unroll
+      for (int t = 0; t < NSLOT; ++t) {
+        if (t >= nslot) break;
+        bool vld;
+        const int rh = unit_row(L, lane, t, vld);
+        rows[t] = u * L.U + rh;
+        ok[t] = vld && rows[t] < L.n;
+        const int li = warp * L.U + rh;
+        if (ok[t]) rv[t] = RESTART ? sr[li] : fma(-alpha, sq[li], sr[li]);
+      }
+      unit_apply_inv<FT, BS, true>(L, reinterpret_cast<const FT*>(st) + (int64_t)warp * uM, lane, rv, zv);
+#pragma unroll
+      for (int t = 0; t < NSLOT; ++t) {
+        if (t >= nslot) break;
+        if (!ok[t]) continue;
+        if (zero_b) {
+          a.x[rows[t]] = 0.0;
+          continue;
+        }
+        if (!RESTART) a.r[rows[t]] = rv[t];
+        a.z[rows[t]] = zv[t];
+        if (RESTART) a.p[rows[t]] = zv[t];
+        v0 = fma(rv[t], zv[t], v0);
+        v1 = fma(rv[t], rv[t], v1);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && j + CGP_NST < nj) issue(j + CGP_NST);
+  }
+  double v[2] = {v0, v1};
+  if (!cg_last_cta<2>(v, a.part, &S->cnt[1], sm, &is_last)) return;
+  if (threadIdx.x != 0) return;
+  cg_precond_epilogue<RESTART>(a, v[0], v[1], zero_b);
+}
+
+// C: x += alpha p (if due); p = z + beta p (if due).
+__global__ void __launch_bounds__(256) cg_update_kernel(const CgArgs a) {
+  const CgScalars* S = a.s;
+  const int xupd = *(volatile const int*)&S->xupd;
+  const int pupd = *(volatile const int*)&S->pupd;
+  if (!xupd && !pupd) return;
+  const double alpha = S->alpha, beta = S->beta;
+  const int64_t n = a.lay.n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; base < n; base += 4 * stride) {
+    double pv[4], xv[4], zv[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int64_t row = min(base + t * stride, n - 1);
+      pv[t] = a.p[row];
+      xv[t] = a.x[row];
+      zv[t] = pupd ? a.z[row] : 0.0;
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int64_t row = base + t * stride;
+      if (row < n) {
+        if (xupd) a.x[row] = fma(alpha, pv[t], xv[t]);
+        if (pupd) a.p[row] = fma(beta, pv[t], zv[t]);
+      }
+    }
+  }
+}
+
+// Resets the per-round flags and arms the loop condition from I2's decision.
+__global__ void cg_arm_kernel(const CgArgs a) {
+  cudaGraphSetConditional(a.cond, (unsigned)a.s->cont);
+}
+
+// ------------------------------------------------------------------ host side
+struct CgGraph {
+  cudaGraphExec_t exec;
+  cudaGraph_t graph;
+  CgArgs args;
+  int g_spmv, g_prec, g_upd;
+  bool tma;              // staged preconditioner kernel usable
+  CgPrecondPlan pl;
+};
+
+// Tile plan of the staged preconditioner kernel (about 24 KB per stage, 8 units per tile).
+static CgPrecondPlan precond_plan(const Layout& L, bool fac_f32, bool* usable) {
+  CgPrecondPlan pl;
+  const int64_t unit_bytes = unit_elems_minv(L) * (fac_f32 ? 4 : 8);
+  const int64_t vec_unit = (int64_t)L.U * 8;
+  const int64_t budget = 24 * 1024;
+  int64_t tu = budget / (unit_bytes + 2 * vec_unit);
+  if (tu > 8) tu = 8;
+  if (tu < 1) tu = 1;
+  // the first row of every tile must be 16-byte aligned: an even tile when U is odd
+  bool ok = true;
+  if ((L.U & 1) && (tu & 1)) {
+    if (tu > 1) tu -= 1;
+    else ok = false;
+  }
+  auto up = [](int64_t v, int64_t m) { return (v + m - 1) / m * m; };
+  pl.tu = (int)tu;
+  pl.off_r = (int)up(tu * unit_bytes, 128);
+  pl.off_q = (int)(pl.off_r + up(tu * vec_unit + 16, 128));
+  pl.stage = (int)(pl.off_q + up(tu * vec_unit + 16, 128));
+  pl.smem = 128 + CGP_NST * pl.stage;
+  pl.tiles = (L.n_units + tu - 1) / tu;
+  if (pl.smem > 200 * 1024) ok = false;
+  if (tu < 4) ok = false;   // too few warps busy per tile: the unstaged kernel is faster
+  *usable = ok;
+  return pl;
+}
+
+template <typename FT, int BS, bool RESTART>
+static cudaError_t launch_precond(cudaStream_t cs, const CgGraph* g) {
+  if (g->tma) {
+    cudaError_t e = cudaFuncSetAttribute(cg_precond_tma_kernel<FT, BS, RESTART>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, g->pl.smem);
+    if (e != cudaSuccess) return e;
+    cg_precond_tma_kernel<FT, BS, RESTART><<<g->g_prec, 256, g->pl.smem, cs>>>(g->args, g->pl);
+  } else {
+    cg_precond_kernel<FT, BS, RESTART><<<g->g_prec, 256, 0, cs>>>(g->args);
+  }
+  return cudaGetLastError();
+}
+
+template <typename VT, typename FT, int BS>
+static cudaError_t capture_body(cudaStream_t cs, const CgGraph* g) {
+  cg_spmv_kernel<VT, 1><<<g->g_spmv, 256, 0, cs>>>(g->args);
+  cudaError_t e = launch_precond<FT, BS, false>(cs, g);
+  if (e != cudaSuccess) return e;
+  cg_update_kernel<<<g->g_upd, 256, 0, cs>>>(g->args);
+  return cudaGetLastError();
+}
+
+template <typename VT, typename FT>
+static cudaError_t capture_body_bs(cudaStream_t cs, const CgGraph* g) {
+  switch (g->args.lay.bs) {
+    case 8: return capture_body<VT, FT, 8>(cs, g);
+    case 16: return capture_body<VT, FT, 16>(cs, g);
+    case 32: return capture_body<VT, FT, 32>(cs, g);
+    case 64: return capture_body<VT, FT, 64>(cs, g);
+    default: return capture_body<VT, FT, 0>(cs, g);
+  }
+}
+
+template <typename VT, typename FT, int BS>
+static cudaError_t launch_pre(cudaStream_t st, const CgGraph* g) {
+  cg_spmv_kernel<VT, 0><<<g->g_spmv, 256, 0, st>>>(g->args);
+  return launch_precond<FT, BS, true>(st, g);
+}
+
+template <typename VT, typename FT>
+static cudaError_t launch_pre_bs(cudaStream_t st, const CgGraph* g) {
+  switch (g->args.lay.bs) {
+    case 8: return launch_pre<VT, FT, 8>(st, g);
+    case 16: return launch_pre<VT, FT, 16>(st, g);
+    case 32: return launch_pre<VT, FT, 32>(st, g);
+    case 64: return launch_pre<VT, FT, 64>(st, g);
+    default: return launch_pre<VT, FT, 0>(st, g);
+  }
+}
+
+static int sms_now() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+int cg_graph_partials() { return sms_now() * 16 * 2 + 64; }
+
+size_t cg_scalars_bytes() { return sizeof(CgScalars); }
+
+// Builds and instantiates the loop graph for the given buffers.  ws_part must hold
+// cg_graph_partials() doubles; scal points to cg_scalars_bytes() of device memory.
+cudaError_t cg_graph_create(void** out, const Layout& L, const int32_t* rp, const int32_t* ci, const void* va,
+                            bool val_f32, const void* minv, bool fac_f32, const double* b, double* x, double* r,
+                            double* z, double* p, double* q, double* part, void* scal, cudaStream_t st) {
+  CgGraph* g = new CgGraph();
+  memset(g, 0, sizeof(*g));
+  const int sms = sms_now();
+  const int64_t n = L.n;
+  g->g_spmv = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
+  g->pl = precond_plan(L, fac_f32, &g->tma);
+  if (g->tma) g->g_prec = (int)std::min<int64_t>(g->pl.tiles, (int64_t)sms * std::max(1, (200 * 1024) / g->pl.smem));
+  else g->g_prec = (int)std::min<int64_t>((L.n_units + 7) / 8, (int64_t)sms * 8);
+  g->g_upd = (int)std::min<int64_t>((n + 1023) / 1024, (int64_t)sms * 8);
+  if (g->g_spmv < 1) g->g_spmv = 1;
+  if (g->g_prec < 1) g->g_prec = 1;
+  if (g->g_upd < 1) g->g_upd = 1;
+  CgArgs& a = g->args;
+  a.lay = L;
+  a.rp = rp;
+  a.ci = ci;
+  a.va = va;
+  a.minv = minv;
+  a.b = b;
+  a.x = x;
+  a.r = r;
+  a.z = z;
+  a.p = p;
+  a.q = q;
+  a.part = part;
+  a.s = reinterpret_cast<CgScalars*>(scal);
+  a.in_graph = 1;
+  cudaError_t e = cudaGraphCreate(&g->graph, 0);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&a.cond, g->graph, 0, 0);
+  cudaGraphNode_t arm = nullptr, loop = nullptr;
+  if (e == cudaSuccess) {
+    cudaKernelNodeParams kp;
+    memset(&kp, 0, sizeof(kp));
+    void* kargs[] = {&a};
+    kp.func = (void*)cg_arm_kernel;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1);
+    kp.kernelParams = kargs;
+    e = cudaGraphAddKernelNode(&arm, g->graph, nullptr, 0, &kp);
+  }
+  cudaGraph_t body = nullptr;
+  if (e == cudaSuccess) {
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+    memset(raw, 0, sizeof(raw));
+    cudaGraphNodeParams* np = reinterpret_cast<cudaGraphNodeParams*>(raw);
+    np->type = cudaGraphNodeTypeConditional;
+    np->conditional.handle = a.cond;
+    np->conditional.type = cudaGraphCondTypeWhile;
+    np->conditional.size = 1;
+    e = cudaGraphAddNode(&loop, g->graph, &arm, nullptr, 1, np);
+    if (e == cudaSuccess) body = np->conditional.phGraph_out[0];
+  }
+  if (e == cudaSuccess) {
+    cudaStream_t cs;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+      e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+      if (e == cudaSuccess) {
+        cudaError_t ce;
+        if (!val_f32 && !fac_f32) ce = capture_body_bs<double, double>(cs, g);
+        else if (!val_f32 && fac_f32) ce = capture_body_bs<double, float>(cs, g);
+        else if (val_f32 && fac_f32) ce = capture_body_bs<float, float>(cs, g);
+        else ce = capture_body_bs<float, double>(cs, g);
+        cudaGraph_t captured = nullptr;
+        e = cudaStreamEndCapture(cs, &captured);
+        if (e == cudaSuccess) e = ce;
+      }
+      cudaStreamDestroy(cs);
+    }
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+  if (e != cudaSuccess) {
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    cudaGetLastError();
+    return e;
+  }
+  (void)st;
+  *out = g;
+  return cudaSuccess;
+}
+
+void cg_graph_destroy(void* h) {
+  CgGraph* g = static_cast<CgGraph*>(h);
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+}
+
+// One round: I1, I2 (stream launches), the loop graph, T.  Scalars must hold it/max_iter/tol
+// and status/done cleared by the caller before the first round.
+cudaError_t cg_graph_round(void* h, bool val_f32, bool fac_f32, cudaStream_t st) {
+  CgGraph* g = static_cast<CgGraph*>(h);
+  const CgArgs& a = g->args;
+  cudaError_t e;
+  if (!val_f32 && !fac_f32) e = launch_pre_bs<double, double>(st, g);
+  else if (!val_f32 && fac_f32) e = launch_pre_bs<double, float>(st, g);
+  else if (val_f32 && fac_f32) e = launch_pre_bs<float, float>(st, g);
+  else e = launch_pre_bs<float, double>(st, g);
+  if (e != cudaSuccess) return e;
+  e = cudaGraphLaunch(g->exec, st);
+  if (e != cudaSuccess) return e;
+  if (val_f32) cg_spmv_kernel<float, 2><<<g->g_spmv, 256, 0, st>>>(a);
+  else cg_spmv_kernel<double, 2><<<g->g_spmv, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// Profiling round: the loop body kernels are launched one by one from the host with CUDA
+// events around each (per-kernel times accumulate into ms[3]); same kernels and results.
+template <typename VT, typename FT, int BS>
+static cudaError_t eager_round_t(CgGraph* g, cudaStream_t st, double* ms, int* iters) {
+  CgGraph eg = *g;
+  eg.args.in_graph = 0;
+  cudaError_t e = launch_pre<VT, FT, BS>(st, &eg);
+  cudaEvent_t ev[4];
+  for (int i = 0; i < 4; ++i) cudaEventCreate(&ev[i]);
+  int cont = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&cont, &eg.args.s->cont, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  while (e == cudaSuccess && cont) {
+    cudaEventRecord(ev[0], st);
+    cg_spmv_kernel<VT, 1><<<eg.g_spmv, 256, 0, st>>>(eg.args);
+    cudaEventRecord(ev[1], st);
+    e = launch_precond<FT, BS, false>(st, &eg);
+    cudaEventRecord(ev[2], st);
+    cg_update_kernel<<<eg.g_upd, 256, 0, st>>>(eg.args);
+    cudaEventRecord(ev[3], st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&cont, &eg.args.s->cont, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    float t;
+    for (int i = 0; i < 3; ++i) {
+      cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+      ms[i] += t;
+    }
+    ++*iters;
+  }
+  for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+  if (e != cudaSuccess) return e;
+  if (std::is_same<VT, float>::value) cg_spmv_kernel<float, 2><<<eg.g_spmv, 256, 0, st>>>(eg.args);
+  else cg_spmv_kernel<double, 2><<<eg.g_spmv, 256, 0, st>>>(eg.args);
+  return cudaGetLastError();
+}
+
+template <typename VT, typename FT>
+static cudaError_t eager_round_bs(CgGraph* g, cudaStream_t st, double* ms, int* iters) {
+  switch (g->args.lay.bs) {
+    case 8: return eager_round_t<VT, FT, 8>(g, st, ms, iters);
+    case 16: return eager_round_t<VT, FT, 16>(g, st, ms, iters);
+    case 32: return eager_round_t<VT, FT, 32>(g, st, ms, iters);
+    case 64: return eager_round_t<VT, FT, 64>(g, st, ms, iters);
+    default: return eager_round_t<VT, FT, 0>(g, st, ms, iters);
+  }
+}
+
+// Full solve: rounds of (I1, I2, loop, T) with at most max_restarts restarts from x when the
+// true residual is above tol.  Synchronises the stream.
+cudaError_t cg_graph_solve(void* h, double tol, int max_iter, int max_restarts, bool val_f32, bool fac_f32,
+                           cudaStream_t st, CgResult* res) {
+  CgGraph* g = static_cast<CgGraph*>(h);
+  CgScalars init;
+  memset(&init, 0, sizeof(init));
+  init.tol = tol;
+  init.max_iter = max_iter;
+  cudaError_t e = cudaMemcpyAsync(g->args.s, &init, sizeof(init), cudaMemcpyHostToDevice, st);
+  int restarts = 0;
+  CgScalars hs;
+  memset(&hs, 0, sizeof(hs));
+  const char* prof = getenv("PC_CG_PROFILE");
+  const bool eager = prof && prof[0] == '1';
+  double ms[3] = {0.0, 0.0, 0.0};
+  int eager_iters = 0;
+  for (;;) {
+    if (e == cudaSuccess) {
+      if (!eager) e = cg_graph_round(h, val_f32, fac_f32, st);
+      else if (!val_f32 && !fac_f32) e = eager_round_bs<double, double>(g, st, ms, &eager_iters);
+      else if (!val_f32 && fac_f32) e = eager_round_bs<double, float>(g, st, ms, &eager_iters);
+      else if (val_f32 && fac_f32) e = eager_round_bs<float, float>(g, st, ms, &eager_iters);
+      else e = eager_round_bs<float, double>(g, st, ms, &eager_iters);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, g->args.s, sizeof(hs), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    const double bnorm = sqrt(hs.bb);
+    if (hs.status != ST_OK || hs.bb == 0.0) break;
+    if (hs.cont != 0) break;   // should not happen: the loop ended with the condition set
+    if (sqrt(hs.tt) <= tol * bnorm) break;
+    if (restarts >= max_restarts) {
+      hs.status = ST_NO_CONV;
+      break;
+    }
+    ++restarts;
+    // next round: keep the iteration count, clear the round flags
+    CgScalars nxt = hs;
+    nxt.done = 0;
+    nxt.xupd = 0;
+    nxt.pupd = 0;
+    nxt.cont = 0;
+    nxt.cnt[0] = nxt.cnt[1] = nxt.cnt[2] = nxt.cnt[3] = 0u;
+    e = cudaMemcpyAsync(g->args.s, &nxt, sizeof(nxt), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // the host copy source is on the stack
+    if (e != cudaSuccess) return e;
+  }
+  res->status = hs.status;
+  res->iterations = hs.it;
+  res->restarts = restarts;
+  res->rel_residual = hs.bb > 0.0 ? sqrt(hs.rr) / sqrt(hs.bb) : 0.0;
+  res->true_rel_residual = hs.bb > 0.0 ? sqrt(hs.tt) / sqrt(hs.bb) : 0.0;
+  for (int i = 0; i < 3; ++i) res->kernel_us[i] = eager_iters ? 1000.0 * ms[i] / eager_iters : 0.0;
+  return cudaSuccess;
+}
+
+}  // namespace pc

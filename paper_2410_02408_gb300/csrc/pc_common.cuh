@@ -102,8 +102,48 @@ __device__ __forceinline__ double ld_x(const double* p) {
   else return __ldg(p);
 }
 
+// float <-> double conversions on the integer pipe.  On this GPU the hardware conversion
+// instructions share the (narrow) FP64 pipe with DFMA, so the hot loops convert by
+// rewriting the IEEE-754 fields: float -> double is exact; double -> float rounds to
+// nearest-even.  Values whose float image is zero, subnormal, infinite or NaN take the
+// hardware conversion (rare in the solver's data).
+// The hardware fallback sits behind a warp-uniform branch: a predicated-off conversion
+// would still occupy the FP64 pipe.  Both helpers must be called by full warps.
+__device__ __forceinline__ double f2d(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t ex = (u >> 23) & 0xffu;
+  const bool special = ex == 0u || ex == 0xffu;
+  const uint64_t d = ((uint64_t)(u & 0x80000000u) << 32) | ((uint64_t)(ex + 896u) << 52) |
+                     ((uint64_t)(u & 0x7fffffu) << 29);
+  double r = __longlong_as_double((long long)d);
+  if (__any_sync(FULL, special)) {
+    if (special) r = (double)f;
+  }
+  return r;
+}
+__device__ __forceinline__ float d2f(double x) {
+  const uint64_t u = (uint64_t)__double_as_longlong(x);
+  const uint32_t hi = (uint32_t)(u >> 32);
+  const int ex = (int)((hi >> 20) & 0x7ffu) - 896;   // biased float exponent
+  const bool special = ex <= 0 || ex >= 255;
+  const uint32_t m23 = (uint32_t)((u >> 29) & 0x7fffffull);
+  const uint32_t rest = (uint32_t)(u & 0x1fffffffull);   // 29 discarded bits
+  uint32_t f = (hi & 0x80000000u) | ((uint32_t)(ex & 0xff) << 23) | m23;
+  if (rest > 0x10000000u || (rest == 0x10000000u && (m23 & 1u))) f += 1u;   // carry may bump the exponent
+  float r = __uint_as_float(f);
+  if (__any_sync(FULL, special)) {
+    if (special) r = __double2float_rn(x);
+  }
+  return r;
+}
 template <typename T>
-__device__ __forceinline__ T to(double v) { return (T)v; }
+__device__ __forceinline__ T to_ft(double v);
+template <>
+__device__ __forceinline__ double to_ft<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float to_ft<float>(double v) { return d2f(v); }
+__device__ __forceinline__ double from_ft(double v) { return v; }
+__device__ __forceinline__ double from_ft(float v) { return f2d(v); }
 
 // ------------------------------------------------------------------ SpMV row
 // acc = sum_e val[e] * x[col[e]] over the row, in storage order (FMA chain).
@@ -129,7 +169,7 @@ __device__ __forceinline__ double spmv_row(const int32_t* __restrict__ rp, const
 #pragma unroll
     for (int t = 0; t < 8; ++t) xv[t] = ld_x<COHERENT>(x + c[t]);
 #pragma unroll
-    for (int t = 0; t < 8; ++t)
+    for (int t = 0; t < 8; ++t)   // per-lane conversion: callers may be divergent here
       if (k0 + t < e) acc = fma((double)v[t], xv[t], acc);
   }
   return acc;
@@ -143,19 +183,26 @@ __device__ __forceinline__ int unit_row(const Layout& L, int lane, int s, bool& 
   return rho;
 }
 
+// Factor element load: from global (read-only stream) or from a shared-memory copy.
+template <bool SMEM, typename FT>
+__device__ __forceinline__ FT ldf(const FT* p) {
+  if constexpr (SMEM) return *p;
+  else return ld_stream(p);
+}
+
 // ------------------------------------------------------------------ block apply, S = 1
 // z_i = sum_j M(i, j) r_j within each block of the unit (bs <= 32).
-template <typename FT, int BS>
+template <typename FT, int BS, bool SMEM = false>
 __device__ __forceinline__ FT apply_inv_s1(const FT* __restrict__ Mu, int bs_rt, int lane, FT r) {
   const int bs = BS > 0 ? BS : bs_rt;
   const int i = lane % bs;
   const int base = lane - i;
   const int K = bs / 2;
-  FT z = ld_stream(Mu + lane) * r;
+  FT z = ldf<SMEM>(Mu + lane) * r;
   if constexpr (BS > 0) {
 #pragma unroll
     for (int k = 1; k <= BS / 2; ++k) {
-      const FT a = ld_stream(Mu + k * 32 + lane);
+      const FT a = ldf<SMEM>(Mu + k * 32 + lane);
       int jf = i + k;
       if (jf >= bs) jf -= bs;
       const FT rf = __shfl_sync(FULL, r, base + jf);
@@ -168,7 +215,7 @@ __device__ __forceinline__ FT apply_inv_s1(const FT* __restrict__ Mu, int bs_rt,
     }
   } else {
     for (int k = 1; k <= K; ++k) {
-      const FT a = ld_stream(Mu + k * 32 + lane);
+      const FT a = ldf<SMEM>(Mu + k * 32 + lane);
       int jf = i + k;
       if (jf >= bs) jf -= bs;
       const FT rf = __shfl_sync(FULL, r, (base + jf) & 31);
@@ -185,17 +232,17 @@ __device__ __forceinline__ FT apply_inv_s1(const FT* __restrict__ Mu, int bs_rt,
 
 // ------------------------------------------------------------------ block apply, S = 2
 // One block of 33..64 rows per warp; lane owns rows lane and lane+32.
-template <typename FT, int BS>
+template <typename FT, int BS, bool SMEM = false>
 __device__ __forceinline__ void apply_inv_s2(const FT* __restrict__ Mu, int bs_rt, int lane, FT r0, FT r1,
                                              FT& z0, FT& z1) {
   const int bs = BS > 0 ? BS : bs_rt;
   const int K = bs / 2;
-  z0 = ld_stream(Mu + lane) * r0;
-  z1 = ld_stream(Mu + 32 + lane) * r1;
+  z0 = ldf<SMEM>(Mu + lane) * r0;
+  z1 = ldf<SMEM>(Mu + 32 + lane) * r1;
 #pragma unroll 4
   for (int k = 1; k <= K; ++k) {
-    const FT a0 = ld_stream(Mu + (2 * k) * 32 + lane);
-    const FT a1 = ld_stream(Mu + (2 * k + 1) * 32 + lane);
+    const FT a0 = ldf<SMEM>(Mu + (2 * k) * 32 + lane);
+    const FT a1 = ldf<SMEM>(Mu + (2 * k + 1) * 32 + lane);
     int j0 = lane + k;
     if (j0 >= bs) j0 -= bs;
     int j1 = lane + 32 + k;
@@ -227,17 +274,17 @@ __device__ __forceinline__ void apply_inv_s2(const FT* __restrict__ Mu, int bs_r
 
 // Unit-level M^{-1} apply: r/z are per-slot doubles of the rows the lane owns (0 for
 // rows beyond n or idle lanes).  Arithmetic in FT.
-template <typename FT, int BS>
+template <typename FT, int BS, bool SMEM = false>
 __device__ __forceinline__ void unit_apply_inv(const Layout& L, const FT* __restrict__ Mu, int lane,
                                                const double (&r)[2], double (&z)[2]) {
   if ((BS > 0 && BS <= 32) || (BS == 0 && L.S == 1)) {
-    z[0] = (double)apply_inv_s1<FT, (BS <= 32 ? BS : 0)>(Mu, L.bs, lane, (FT)r[0]);
+    z[0] = from_ft(apply_inv_s1<FT, (BS <= 32 ? BS : 0), SMEM>(Mu, L.bs, lane, to_ft<FT>(r[0])));
     z[1] = 0.0;
   } else {
     FT z0, z1;
-    apply_inv_s2<FT, (BS > 32 ? BS : 0)>(Mu, L.bs, lane, (FT)r[0], (FT)r[1], z0, z1);
-    z[0] = (double)z0;
-    z[1] = (double)z1;
+    apply_inv_s2<FT, (BS > 32 ? BS : 0), SMEM>(Mu, L.bs, lane, to_ft<FT>(r[0]), to_ft<FT>(r[1]), z0, z1);
+    z[0] = from_ft(z0);
+    z[1] = from_ft(z1);
   }
 }
 

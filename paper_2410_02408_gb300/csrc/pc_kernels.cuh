@@ -29,8 +29,42 @@ struct PcgOut {
   double true_rel_residual;
 };
 
+// Shared-memory plan of the persistent CG kernel (identical on host and device).
+constexpr int PCG_BLOCK = 256;    // threads per CTA
+constexpr int PCG_NW = PCG_BLOCK / 32;
+constexpr int PCG_NSTW = 2;       // pipeline stages per warp
+constexpr int PCG_TCAP = 512;     // SpMV chunk table capacity (entries)
+constexpr int PCG_WSTAGE = 3328;  // bytes per warp stage
+constexpr int PCG_CHUNK = 32;     // rows per SpMV chunk (one row per lane)
+
+struct PcgSmem {
+  int wstage;      // bytes per warp stage
+  int off_col;     // column window offset in an SpMV stage (after the row-pointer window)
+  int off_val;     // value window offset
+  int tnnz;        // entries an SpMV stage holds
+  int fac_smem;    // 1 if one warp unit of M^{-1} fits a stage
+  int total;       // dynamic shared memory bytes
+};
+
+__host__ __device__ inline PcgSmem pcg_smem_plan(int val_bytes, int64_t unit_bytes) {
+  PcgSmem p;
+  p.wstage = PCG_WSTAGE;
+  p.off_col = 176;                                  // row-pointer window: <= 33*4 + 32 bytes
+  int t = (PCG_WSTAGE - p.off_col - 32 - 32 - 16) / (4 + val_bytes);
+  t &= ~7;
+  p.tnnz = t;                                        // col window <= 4t+32, value window <= vb*t+32
+  p.off_val = (p.off_col + t * 4 + 32 + 15) & ~15;
+  p.fac_smem = unit_bytes <= PCG_WSTAGE ? 1 : 0;
+  p.total = 256 + PCG_TCAP * 4 + PCG_NW * PCG_NSTW * PCG_WSTAGE;
+  return p;
+}
+
 struct PcgArgs {
   Layout lay;
+  int64_t nnz;
+  int32_t tr;            // rows per SpMV tile
+  int32_t pad0;
+  PcgSmem sp;
   const int32_t* rp;
   const int32_t* ci;
   const void* va;
@@ -50,7 +84,16 @@ struct PcgArgs {
   int32_t max_iter;
   int32_t max_restarts;
   long long budget;
+  unsigned long long* trace;   // optional: globaltimer (ns) at kernel start and after each grid barrier
+  int32_t trace_len;           // entries available in trace
+  int32_t pad1;
 };
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 // pc_setup.cu
 cudaError_t launch_setup(const SetupArgs& a, bool val_f32, bool fac_f32, cudaStream_t st);
@@ -93,7 +136,25 @@ cudaError_t launch_grad_val(int64_t n, const int32_t* rp, const int32_t* ci, con
 
 // pc_pcg_*.cu
 cudaError_t launch_pcg(const PcgArgs& a, bool val_f32, bool fac_f32, int grid, int block, cudaStream_t st);
-cudaError_t pcg_occupancy(const Layout& L, bool val_f32, bool fac_f32, int block, int* ctas_per_sm);
+cudaError_t pcg_occupancy(const Layout& L, bool val_f32, bool fac_f32, int block, int smem, int* ctas_per_sm);
+// Fill the launch plan fields of a (nnz, tr, sp) for this matrix and factor precision.
+void pcg_plan(PcgArgs& a, int64_t nnz, bool val_f32, bool fac_f32);
+
+// pc_cg_graph.cu
+struct CgResult {
+  int32_t status, iterations, restarts, pad;
+  double rel_residual, true_rel_residual;
+  double kernel_us[3];   // profiling mode: mean time of the SpMV, preconditioner and update kernels
+};
+int cg_graph_partials();
+size_t cg_scalars_bytes();
+cudaError_t cg_graph_create(void** out, const Layout& L, const int32_t* rp, const int32_t* ci, const void* va,
+                            bool val_f32, const void* minv, bool fac_f32, const double* b, double* x, double* r,
+                            double* z, double* p, double* q, double* part, void* scal, cudaStream_t st);
+void cg_graph_destroy(void* g);
+cudaError_t cg_graph_round(void* g, bool val_f32, bool fac_f32, cudaStream_t st);
+cudaError_t cg_graph_solve(void* g, double tol, int max_iter, int max_restarts, bool val_f32, bool fac_f32,
+                           cudaStream_t st, CgResult* res);
 
 // pc_lanczos.cu
 struct LanczosState {

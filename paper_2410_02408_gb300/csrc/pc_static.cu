@@ -74,9 +74,12 @@ extern "C" pc_status pcg_solve_noalloc(const pc_csr* A, int32_t block_size, cons
   const size_t es = fac_f32 ? 4 : 8;
 
   // persistent grid, as in pcg_solve
-  const int block = 256;
+  const int block = pc::PCG_BLOCK;
   int per_sm = 0, dev = 0, sms = 0;
-  cudaError_t e = pc::pcg_occupancy(L, val_f32, fac_f32, block, &per_sm);
+  pc::PcgArgs a;
+  a.lay = L;
+  pc::pcg_plan(a, A->nnz, val_f32, fac_f32);
+  cudaError_t e = pc::pcg_occupancy(L, val_f32, fac_f32, block, a.sp.total, &per_sm);
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return to_status(e);
@@ -145,8 +148,6 @@ extern "C" pc_status pcg_solve_noalloc(const pc_csr* A, int32_t block_size, cons
   // solve: barrier words and outputs must start at zero
   e = pc::launch_split(A->n, A->nnz, A->row_ptr, grid, split, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, sizeof(pc::GridSync) + sizeof(pc::PcgOut), st);
-  pc::PcgArgs a;
-  a.lay = L;
   a.rp = A->row_ptr;
   a.ci = A->col_idx;
   a.va = A->val;
@@ -166,6 +167,8 @@ extern "C" pc_status pcg_solve_noalloc(const pc_csr* A, int32_t block_size, cons
   a.max_iter = max_iter;
   a.max_restarts = 3;
   a.budget = 4000000000LL;
+  a.trace = nullptr;
+  a.trace_len = 0;
   if (e == cudaSuccess) e = pc::launch_pcg(a, val_f32, fac_f32, grid, block, st);
   unsigned char hostctl[sizeof(pc::GridSync) + sizeof(pc::PcgOut)];
   if (e == cudaSuccess) e = cudaMemcpyAsync(hostctl, ctl, sizeof(hostctl), cudaMemcpyDeviceToHost, st);

@@ -201,8 +201,15 @@ def test_kappa_without_reorth_runs(pc):
 
 
 # ---------------------------------------------------------------- a8 PCG
+@pytest.fixture(params=["graph", "persistent"])
+def engine(pc, request):
+    pc.set_cg_engine(request.param)
+    yield request.param
+    pc.set_cg_engine("default")
+
+
 @pytest.mark.parametrize("bs", [1, 16, 64])
-def test_pcg_poisson2d_matches_oracle(pc, bs):
+def test_pcg_poisson2d_matches_oracle(pc, engine, bs):
     A = CASES["poisson2d_64"]
     b = W.rhs(A.n, 0)
     x, info = pc.pcg(A, b, bs, tol=1e-10)
@@ -214,7 +221,7 @@ def test_pcg_poisson2d_matches_oracle(pc, bs):
 
 
 @pytest.mark.parametrize("bs", [8, 10, 16, 32, 64])
-def test_pcg_diffusion_fp64_matches_oracle(pc, bs):
+def test_pcg_diffusion_fp64_matches_oracle(pc, engine, bs):
     A = W.diffusion3d(24, 2.0)
     b = W.rhs(A.n, 0)
     x, info = pc.pcg(A, b, bs, tol=1e-10, prec="fp64")
@@ -227,7 +234,7 @@ def test_pcg_diffusion_fp64_matches_oracle(pc, bs):
 
 
 @pytest.mark.parametrize("bs", [8, 16, 32, 64])
-def test_pcg_diffusion_mixed_reaches_tolerance(pc, bs):
+def test_pcg_diffusion_mixed_reaches_tolerance(pc, engine, bs):
     A = W.diffusion3d(24, 2.0)
     b = W.rhs(A.n, 0)
     x, info = pc.pcg(A, b, bs, tol=1e-10, prec="fp32")
@@ -239,7 +246,7 @@ def test_pcg_diffusion_mixed_reaches_tolerance(pc, bs):
           f"err vs oracle {rel(x.cpu().numpy(), o['x']):.2e}")
 
 
-def test_pcg_float32_values(pc):
+def test_pcg_float32_values(pc, engine):
     A = W.powerlaw_spd(n=20000, seed=5, w_max=500, cap=400)
     b = W.rhs(A.n, 0)
     A64 = W.CSR(A.row_ptr, A.col, A.val.astype(np.float64))
@@ -252,7 +259,7 @@ def test_pcg_float32_values(pc):
     assert rel(x2.cpu().numpy(), o["x"]) <= 1e-10
 
 
-def test_pcg_is_bit_reproducible(pc):
+def test_pcg_is_bit_reproducible(pc, engine):
     A = W.diffusion3d(16, 2.0)
     b = W.rhs(A.n, 0)
     x1, i1 = pc.pcg(A, b, 16)
@@ -261,7 +268,7 @@ def test_pcg_is_bit_reproducible(pc):
     assert torch.equal(x1, x2)
 
 
-def test_pcg_status_codes(pc):
+def test_pcg_status_codes(pc, engine):
     A = W.poisson2d(16)
     b = W.rhs(A.n, 0)
     x, info = pc.pcg(A, b, 4, max_iter=1, check=False)
@@ -279,6 +286,8 @@ def test_pcg_status_codes(pc):
 
 
 def test_pcg_bounded_wait_times_out_and_recovers(pc):
+    # the grid barrier of the persistent engine is the bounded device-side wait
+    pc.set_cg_engine("persistent")
     A = W.poisson2d(64)
     b = W.rhs(A.n, 0)
     pc.set_wait_budget(1)
@@ -288,10 +297,11 @@ def test_pcg_bounded_wait_times_out_and_recovers(pc):
         pc.set_wait_budget(0)
     assert info["status"] == 5
     x, info = pc.pcg(A, b, 16)
+    pc.set_cg_engine("default")
     assert info["status"] == 0
 
 
-def test_pcg_handle_reuse_and_warm_restart(pc):
+def test_pcg_handle_reuse_and_warm_restart(pc, engine):
     A = W.diffusion3d(12, 1.0)
     b = W.rhs(A.n, 0)
     h = pc.setup(A, 16)
