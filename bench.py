@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=128, help="grid points per axis")
     ap.add_argument("--sigma", type=float, default=2.0)
-    ap.add_argument("--bs", type=int, default=32)
+    ap.add_argument("--bs", type=int, default=16)
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "tf32"])
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--maxit", type=int, default=200000)
@@ -191,9 +191,9 @@ def kernel_source_hash():
 
 
 def profiled_traffic(bs, prec):
-    """DRAM bytes per CG iteration of the persistent kernel from the committed ncu summary,
-    or None if absent or if the kernel sources changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", "pcg_kernel_diffusion3d_128.md")
+    """DRAM bytes per launch of the SpMV kernel from the committed ncu summary, or None if
+    absent or if the kernel sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "cg_spmv_kernel_diffusion3d_128.md")
     try:
         txt = open(path).read()
     except OSError:
@@ -201,7 +201,7 @@ def profiled_traffic(bs, prec):
     m = re.search(r"kernel_source_hash:\s*(\w+)", txt)
     if not m or m.group(1) != kernel_source_hash():
         return None
-    m = re.search(rf"dram_bytes_per_iteration\[bs={bs},prec={prec}\]:\s*([0-9.eE+]+)", txt)
+    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     return float(m.group(1)) if m else None
 
 
@@ -325,16 +325,39 @@ def run_ours(args):
         sb, b_it, kb = step_bytes(n, nnz, args.bs, args.prec, inf["iterations"])
         total_bytes += sb
     value = total_bytes * ws / (ms_total / 1e3) / 1e9
-    # dominant kernel: the persistent CG kernel (one launch per step), CUDA-event timed
-    kern_ms = statistics.mean(i["solve_ms"] for i in infos)
-    _, b_it, kern_bytes = step_bytes(n, nnz, args.bs, args.prec, iters)
+    solve_ms = statistics.mean(i["solve_ms"] for i in infos)
     peak, peak_kind = measured_hbm()
-    achieved = kern_bytes / (kern_ms / 1e3) / 1e9
-    traffic_it = profiled_traffic(args.bs, args.prec)
+    _, b_it, _ = step_bytes(n, nnz, args.bs, args.prec, iters)
+    # Per-kernel times: one extra (untimed) solve in profiling mode, where the loop-body
+    # kernels are launched one by one with CUDA events around each on the current stream.
+    os.environ["PC_CG_PROFILE"] = "1"
+    hp = pc.setup(Ad, args.bs, prec=args.prec)
+    hp.pcg(bd, tol=args.tol, max_iter=args.maxit)
+    kt = hp.trace(8)
+    hp.destroy()
+    del os.environ["PC_CG_PROFILE"]
+    spmv_us, prec_us, upd_us = (float(kt[0]) / 1e3, float(kt[1]) / 1e3, float(kt[2]) / 1e3) if len(kt) >= 3 else (0.0, 0.0, 0.0)
+    fb = 4 if args.prec != "fp64" else 8
+    spmv_bytes = csr_bytes(n, nnz, 8) + 2 * 8 * n                       # CSR, p (read once), q
+    prec_bytes = factor_bytes(n, args.bs, fb)[0] + 4 * 8 * n              # M^{-1}, r, q in; r, z out
+    upd_bytes = 5 * 8 * n                                                 # x, p, z in; x, p out
+    # dominant kernel (largest share of the iteration): the SpMV q = A p with the p.q reduction
+    achieved = spmv_bytes / (spmv_us * 1e-6) / 1e9 if spmv_us > 0 else 0.0
+    traffic = profiled_traffic(args.bs, args.prec)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": (traffic_it * iters if traffic_it is not None else None),
-                "peak_kind": peak_kind, "kernel": "pcg_kernel (persistent, one launch per solve)",
-                "algorithmic_bytes_per_iteration": b_it}
+                "traffic": traffic, "peak_kind": peak_kind,
+                "kernel": "cg_spmv_kernel (q = A p and p.q; one launch per CG iteration)",
+                "algorithmic_bytes_per_launch": spmv_bytes, "avg_launch_us": spmv_us}
+    kernels = {
+        "spmv": {"us": spmv_us, "GBs": achieved, "bytes": spmv_bytes},
+        "precond": {"us": prec_us, "GBs": prec_bytes / (prec_us * 1e-6) / 1e9 if prec_us > 0 else 0.0,
+                    "bytes": prec_bytes},
+        "update": {"us": upd_us, "GBs": upd_bytes / (upd_us * 1e-6) / 1e9 if upd_us > 0 else 0.0,
+                   "bytes": upd_bytes},
+        "note": "profiling-mode launches (events around each kernel), includes per-launch overhead",
+    }
+    # launches of this library's kernels per step: setup; per round I1, I2, arm, T; 3 per iteration
+    launches = sum(1 + 4 * (i["restarts"] + 1) + 3 * i["iterations"] for i in infos)
     xr = x.cpu().numpy()
     true_res = float(np.linalg.norm(b - A.to_scipy() @ xr) / np.linalg.norm(b))   # report only
 
@@ -347,10 +370,12 @@ def run_ours(args):
                    "tol": args.tol, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (CSR %.0f MB + factor)" % (csr_bytes(n, nnz, 8) / 1e6)},
         "iterations": iters, "true_rel_residual": true_res,
-        "setup_ms": statistics.mean(i["setup_ms"] for i in infos), "solve_ms": kern_ms,
+        "setup_ms": statistics.mean(i["setup_ms"] for i in infos), "solve_ms": solve_ms,
+        "us_per_iteration": 1000.0 * solve_ms / max(iters, 1), "algorithmic_bytes_per_iteration": b_it,
         "frac_of_hbm_peak": value / peak,
         "roofline": roofline,
-        "gpu_launches": 3 * args.steps,
+        "kernels": kernels,
+        "gpu_launches": launches,
     }
     line["clocks"] = clk.summary()
 
