@@ -107,8 +107,14 @@ __device__ __forceinline__ double ld_x(const double* p) {
 // rewriting the IEEE-754 fields: float -> double is exact; double -> float rounds to
 // nearest-even.  Values whose float image is zero, subnormal, infinite or NaN take the
 // hardware conversion (rare in the solver's data).
-// The hardware fallback sits behind a warp-uniform branch: a predicated-off conversion
-// would still occupy the FP64 pipe.  Both helpers must be called by full warps.
+// The hardware fallback sits behind a warp-uniform branch into an out-of-line function: a
+// predicated-off conversion would still occupy the FP64 pipe, and keeping the fallback out of
+// line stops the compiler from if-converting the branch into exactly that.  Both helpers must
+// be called by full warps.
+static __device__ __noinline__ double f2d_special(float f, double r, bool special) { return special ? (double)f : r; }
+static __device__ __noinline__ float d2f_special(double x, float r, bool special) {
+  return special ? __double2float_rn(x) : r;
+}
 __device__ __forceinline__ double f2d(float f) {
   const uint32_t u = __float_as_uint(f);
   const uint32_t ex = (u >> 23) & 0xffu;
@@ -116,9 +122,7 @@ __device__ __forceinline__ double f2d(float f) {
   const uint64_t d = ((uint64_t)(u & 0x80000000u) << 32) | ((uint64_t)(ex + 896u) << 52) |
                      ((uint64_t)(u & 0x7fffffu) << 29);
   double r = __longlong_as_double((long long)d);
-  if (__any_sync(FULL, special)) {
-    if (special) r = (double)f;
-  }
+  if (__any_sync(FULL, special)) r = f2d_special(f, r, special);
   return r;
 }
 __device__ __forceinline__ float d2f(double x) {
@@ -131,9 +135,7 @@ __device__ __forceinline__ float d2f(double x) {
   uint32_t f = (hi & 0x80000000u) | ((uint32_t)(ex & 0xff) << 23) | m23;
   if (rest > 0x10000000u || (rest == 0x10000000u && (m23 & 1u))) f += 1u;   // carry may bump the exponent
   float r = __uint_as_float(f);
-  if (__any_sync(FULL, special)) {
-    if (special) r = __double2float_rn(x);
-  }
+  if (__any_sync(FULL, special)) r = d2f_special(x, r, special);
   return r;
 }
 template <typename T>
