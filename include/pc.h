@@ -216,6 +216,19 @@ pc_status pcg_solve_noalloc(const pc_csr *A, int32_t block_size, const double *b
 pc_status pc_grad_val(const pc_csr *A, const double *lambda, const double *x, double *grad_val,
                       void *stream);
 
+/* pc_grad_edges - the same adjoint for a matrix assembled from edge coefficients,
+ * A(c) = sum_e c_e (e_p - e_q)(e_p - e_q)^T + sum_f c_f e_p e_p^T (graph Laplacians and the
+ * variable-coefficient diffusion stencils: an interior face couples cells p and q, a
+ * Dirichlet boundary face touches cell p only and is marked q < 0).  dA/dc_e is that
+ * rank-one term, so
+ *     grad_c[e] = -(lambda[p[e]] - lambda[q[e]]) * (x[p[e]] - x[q[e]])   (q[e] >= 0)
+ *     grad_c[e] = -lambda[p[e]] * x[p[e]]                                 (q[e] <  0)
+ * Device arrays: p, q int32 [n_edges]; lambda, x [n]; grad_c [n_edges] (written).  Edges
+ * whose indices fall outside 0..n-1 get NaN.  Enqueued on stream; PC_ERR_INVALID_ARG for
+ * null pointers, negative sizes or n > INT32_MAX. */
+pc_status pc_grad_edges(int64_t n_edges, const int32_t *p, const int32_t *q, const double *lambda,
+                        const double *x, int64_t n, double *grad_c, void *stream);
+
 /* ---------------------------------------------------------------------------------
  * Batched mode: many independent SPD systems of uneven size, each with its own block
  * size, set up and solved in ONE persistent launch (each system is owned by one

@@ -80,6 +80,8 @@ def _declare(L):
     L.or_pcg.argtypes = [_i64, _p, _p, _p, _i32, _p, _p, _p, _dbl, _i32, _i32, _p, _p, _p]
     L.or_grad_val.restype = None
     L.or_grad_val.argtypes = [_i64, _p, _p, _p, _p, _p]
+    L.or_grad_edges.restype = None
+    L.or_grad_edges.argtypes = [_i64, _p, _p, _p, _p, _p]
 
 
 def _ptr(a: np.ndarray):
@@ -263,4 +265,16 @@ def grad_val(A, lam: np.ndarray, x: np.ndarray) -> np.ndarray:
     x = np.ascontiguousarray(x, dtype=np.float64)
     g = np.zeros(M.col.shape[0])
     lib().or_grad_val(M.n, _ptr(M.row_ptr), _ptr(M.col), _ptr(lam), _ptr(x), _ptr(g))
+    return g
+
+
+def grad_edges(p: np.ndarray, q: np.ndarray, lam: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """dL/dc_e = -(lam_p - lam_q)(x_p - x_q) per edge (p, q); q < 0 marks a boundary face
+    whose gradient is -lam_p x_p."""
+    p = np.ascontiguousarray(p, dtype=np.int32)
+    q = np.ascontiguousarray(q, dtype=np.int32)
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    g = np.zeros(p.shape[0])
+    lib().or_grad_edges(p.shape[0], _ptr(p), _ptr(q), _ptr(lam), _ptr(x), _ptr(g))
     return g

@@ -23,6 +23,8 @@
  *   or_pcg             - Hestenes-Stiefel preconditioned CG with the relative residual
  *                        ||b - A x|| / ||b|| of Sec. 3.7 as the stopping test
  *   or_grad_val        - adjoint gradient dL/dA_ij = -lambda_i x_j on the pattern
+ *   or_grad_edges      - the same adjoint for a matrix assembled from edge coefficients,
+ *                        A = sum_e c_e (e_p - e_q)(e_p - e_q)^T + sum_f c_f e_p e_p^T
  *
  * Condition number (Sec. 3.1): for the SPD operators here kappa = lambda_max/lambda_min.
  *
@@ -407,4 +409,18 @@ void or_grad_val(int64_t n, const int32_t *row_ptr, const int32_t *col, const do
                  const double *x, double *gval) {
   for (int64_t i = 0; i < n; ++i)
     for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) gval[e] = -lambda[i] * x[col[e]];
+}
+
+/* Adjoint with respect to edge coefficients.  For A(c) = sum_e c_e (e_p - e_q)(e_p - e_q)^T
+ * + sum_f c_f e_p e_p^T (a Dirichlet boundary face f touches one node p, marked q < 0),
+ * dA/dc_e is that rank-one term, so dL/dc_e = -lambda^T (dA/dc_e) x
+ * = -(lambda_p - lambda_q)(x_p - x_q), and -lambda_p x_p for a boundary face. */
+void or_grad_edges(int64_t n_edges, const int32_t *p, const int32_t *q, const double *lambda,
+                   const double *x, double *gc) {
+  for (int64_t e = 0; e < n_edges; ++e) {
+    if (q[e] < 0)
+      gc[e] = -lambda[p[e]] * x[p[e]];
+    else
+      gc[e] = -(lambda[p[e]] - lambda[q[e]]) * (x[p[e]] - x[q[e]]);
+  }
 }

@@ -93,6 +93,7 @@ def lib():
                              ctypes.POINTER(pc_solve_info), _P]),
         "pcg_solve_h": (_I32, [_P, _P, _P, _D, _I32, ctypes.POINTER(pc_solve_info), _P]),
         "pc_grad_val": (_I32, [ctypes.POINTER(pc_csr), _P, _P, _P, _P]),
+        "pc_grad_edges": (_I32, [_I64, _P, _P, _P, _P, _I64, _P, _P]),
         "pcg_solve_batched": (_I32, [ctypes.POINTER(pc_batch), _P, _P, _D, _I32, _I32, _P, _P, _P,
                                      ctypes.POINTER(pc_solve_info), _P]),
         "pc_get_trace": (_I32, [_P, _P, _I32]),
@@ -338,6 +339,20 @@ def grad_val(A, lam, x):
     out = torch.empty(A.nnz, dtype=torch.float64, device="cuda")
     d = A.desc()
     _check(lib().pc_grad_val(ctypes.byref(d), _ptr(lam), _ptr(x), _ptr(out), _stream()), "pc_grad_val")
+    return out
+
+
+def grad_edges(p, q, lam, x):
+    """dL/dc_e = -(lam_p - lam_q)(x_p - x_q) for every edge (p, q); q < 0 marks a boundary
+    face (-lam_p x_p).  p, q: int32 index tensors; lam, x: FP64 vectors."""
+    torch = _torch()
+    p = _dev(p, torch.int32)
+    q = _dev(q, torch.int32)
+    lam = _dev(lam, torch.float64)
+    x = _dev(x, torch.float64)
+    out = torch.empty(p.numel(), dtype=torch.float64, device="cuda")
+    _check(lib().pc_grad_edges(int(p.numel()), _ptr(p), _ptr(q), _ptr(lam), _ptr(x), int(x.numel()), _ptr(out),
+                               _stream()), "pc_grad_edges")
     return out
 
 

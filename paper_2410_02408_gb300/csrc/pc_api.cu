@@ -295,6 +295,14 @@ pc_status pc_grad_val(const pc_csr* A, const double* lambda, const double* x, do
   return from_cuda(pc::launch_grad_val(A->n, A->row_ptr, A->col_idx, lambda, x, grad_val, (cudaStream_t)stream));
 }
 
+pc_status pc_grad_edges(int64_t n_edges, const int32_t* p, const int32_t* q, const double* lambda, const double* x,
+                        int64_t n, double* grad_c, void* stream) {
+  if (n_edges < 0 || n < 0) return PC_ERR_INVALID_ARG;
+  if (n_edges == 0) return PC_OK;
+  if (!p || !q || !lambda || !x || !grad_c || n == 0 || n > INT32_MAX) return PC_ERR_INVALID_ARG;
+  return from_cuda(pc::launch_grad_edges(n_edges, p, q, lambda, x, n, grad_c, (cudaStream_t)stream));
+}
+
 // ------------------------------------------------------------------ PCG
 static pc_status ensure_cg_workspace(pc_handle* h, cudaStream_t st) {
   const int block = pc::PCG_BLOCK;

@@ -133,6 +133,8 @@ cudaError_t launch_sym_phase2(const SymPhase2Args& a, bool val_f32, bool fac_f32
 cudaError_t launch_split(int64_t n, int64_t nnz, const int32_t* rp, int parts, int64_t* split, cudaStream_t st);
 cudaError_t launch_grad_val(int64_t n, const int32_t* rp, const int32_t* ci, const double* lam, const double* x,
                             double* g, cudaStream_t st);
+cudaError_t launch_grad_edges(int64_t n_edges, const int32_t* ep, const int32_t* eq, const double* lam,
+                              const double* x, int64_t n, double* g, cudaStream_t st);
 
 // pc_pcg_*.cu
 cudaError_t launch_pcg(const PcgArgs& a, bool val_f32, bool fac_f32, int grid, int block, cudaStream_t st);

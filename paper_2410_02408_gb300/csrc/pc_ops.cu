@@ -120,6 +120,31 @@ __global__ void grad_val_kernel(int64_t n, const int32_t* __restrict__ rp, const
   }
 }
 
+// dL/dc_e for A = sum_e c_e (e_p - e_q)(e_p - e_q)^T + sum_f c_f e_p e_p^T: the rank-one
+// dA/dc_e turns -lambda^T (dA/dc_e) x into -(lambda_p - lambda_q)(x_p - x_q), or -lambda_p x_p
+// for a boundary face (q < 0).  An edge whose node index is out of range gets NaN and no
+// vector is read for it.
+__global__ void grad_edges_kernel(int64_t n_edges, const int32_t* __restrict__ ep, const int32_t* __restrict__ eq,
+                                  const double* __restrict__ lam, const double* __restrict__ x, int64_t n,
+                                  double* __restrict__ g) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_edges; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t p = __ldg(ep + e);
+    const int32_t q = __ldg(eq + e);
+    if (p < 0 || p >= n || q >= n) {
+      g[e] = __longlong_as_double(0x7ff8000000000000ll);
+      continue;
+    }
+    const double lp = __ldg(lam + p), xp = __ldg(x + p);
+    if (q < 0) {
+      g[e] = -(lp * xp);
+    } else {
+      const double dl = lp - __ldg(lam + q);
+      const double dx = xp - __ldg(x + q);
+      g[e] = -(dl * dx);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ launchers
 static unsigned grid_for(int64_t work, int per) {
   int64_t g = (work + per - 1) / per;
@@ -173,6 +198,13 @@ cudaError_t launch_split(int64_t n, int64_t nnz, const int32_t* rp, int parts, i
 cudaError_t launch_grad_val(int64_t n, const int32_t* rp, const int32_t* ci, const double* lam, const double* x,
                             double* g, cudaStream_t st) {
   grad_val_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, rp, ci, lam, x, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_edges(int64_t n_edges, const int32_t* ep, const int32_t* eq, const double* lam,
+                              const double* x, int64_t n, double* g, cudaStream_t st) {
+  if (n_edges == 0) return cudaSuccess;
+  grad_edges_kernel<<<grid_for(n_edges, 256), 256, 0, st>>>(n_edges, ep, eq, lam, x, n, g);
   return cudaGetLastError();
 }
 

@@ -146,39 +146,32 @@ def diffusion3d(n: int, sigma: float, seed: int = 1) -> CSR:
     return A
 
 
-def diffusion3d_face_grad(n: int, grad_val_fn) -> tuple:
-    """Chain rule of ``diffusion3d_from_faces``: given a function g(p, q) that returns
-    dL/dA_pq for arrays of (row, col) index pairs, return dL/dc for every face
-    (cx, cy, cz shapes).  Interior face between p and q: g(p,p)+g(q,q)-g(p,q)-g(q,p);
-    boundary face of p: g(p,p)."""
-    N = n ** 3
-    p = np.arange(N, dtype=np.int64).reshape(n, n, n)   # [k, j, i]
-    out = []
-    for axis, stride in ((2, 1), (1, n), (0, n * n)):
+def diffusion3d_face_edges(n: int) -> tuple:
+    """The node pair of every face coefficient of ``diffusion3d_faces``, in the order
+    cx.ravel(), cy.ravel(), cz.ravel(): int32 arrays (p, q) with q = -1 for a Dirichlet
+    boundary face (it touches only cell p).  Face f along an axis lies between cells f-1
+    and f of that axis; faces 0 and n are the boundary faces of cells 0 and n-1."""
+    k, j, i = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    ps, qs = [], []
+    for axis in (2, 1, 0):          # x faces (cx), y faces (cy), z faces (cz)
         shape = [n, n, n]
         shape[axis] += 1
-        g = np.zeros(shape)
-        # interior faces
-        sl_hi = [slice(None)] * 3
-        sl_lo = [slice(None)] * 3
-        sl_hi[axis] = slice(1, n)
-        sl_lo[axis] = slice(0, n - 1)
-        q_hi = p[tuple(sl_hi)].ravel()   # cell on the + side of the face
-        q_lo = p[tuple(sl_lo)].ravel()   # cell on the - side
-        gi = grad_val_fn(q_hi, q_hi) + grad_val_fn(q_lo, q_lo) - grad_val_fn(q_hi, q_lo) - grad_val_fn(q_lo, q_hi)
-        face_int = [slice(None)] * 3
-        face_int[axis] = slice(1, n)
-        g[tuple(face_int)] = gi.reshape(p[tuple(sl_hi)].shape)
-        # boundary faces (index 0 belongs to the first cell, index n to the last cell)
-        for fidx, cidx in ((0, 0), (n, n - 1)):
-            fsl = [slice(None)] * 3
-            fsl[axis] = slice(fidx, fidx + 1)
-            csl = [slice(None)] * 3
-            csl[axis] = slice(cidx, cidx + 1)
-            q = p[tuple(csl)].ravel()
-            g[tuple(fsl)] = grad_val_fn(q, q).reshape(p[tuple(csl)].shape)
-        out.append(g)
-    return tuple(out)
+        f = np.indices(shape)       # [k, j, i] indices of every face
+        lo = f.copy()
+        lo[axis] -= 1               # cell on the - side
+        hi = f                      # cell on the + side
+        def cell(c):
+            return c[0] * n * n + c[1] * n + c[2]
+        lo_ok = lo[axis] >= 0
+        hi_ok = hi[axis] <= n - 1
+        hi_c = np.where(hi_ok, cell(np.minimum(hi, n - 1)), -1)
+        lo_c = np.where(lo_ok, cell(np.maximum(lo, 0)), -1)
+        p = np.where(lo_ok, lo_c, hi_c)
+        q = np.where(lo_ok & hi_ok, hi_c, -1)
+        ps.append(p.ravel())
+        qs.append(q.ravel())
+    del k, j, i
+    return np.concatenate(ps).astype(np.int32), np.concatenate(qs).astype(np.int32)
 
 
 # ---------------------------------------------------------------------------

@@ -29,7 +29,7 @@ def libpc():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("pc_setup", "pc_apply", "kappa_estimate", "pcg_solve", "pc_destroy", "pc_status_string",
-                     "pcg_solve_batched", "pc_grad_val"):
+                     "pcg_solve_batched", "pc_grad_val", "pc_grad_edges"):
         assert required in names
 
 

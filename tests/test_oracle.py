@@ -327,6 +327,35 @@ def test_pcg_warm_start_from_solution():
 
 
 # ---------------------------------------------------------------- adjoint
+def _face_grad_chain(n, gfn):
+    """Chain rule of the 7-point assembly: dL/dc for every face (cx, cy, cz shapes) from
+    g(p, q) = dL/dA_pq.  Interior face between p and q: g(p,p)+g(q,q)-g(p,q)-g(q,p);
+    boundary face of p: g(p,p)."""
+    p = np.arange(n ** 3, dtype=np.int64).reshape(n, n, n)   # [k, j, i]
+    out = []
+    for axis in (2, 1, 0):
+        shape = [n, n, n]
+        shape[axis] += 1
+        g = np.zeros(shape)
+        sl_hi = [slice(None)] * 3
+        sl_lo = [slice(None)] * 3
+        sl_hi[axis] = slice(1, n)
+        sl_lo[axis] = slice(0, n - 1)
+        q_hi = p[tuple(sl_hi)].ravel()
+        q_lo = p[tuple(sl_lo)].ravel()
+        gi = gfn(q_hi, q_hi) + gfn(q_lo, q_lo) - gfn(q_hi, q_lo) - gfn(q_lo, q_hi)
+        g[tuple(sl_hi)] = gi.reshape(p[tuple(sl_hi)].shape)
+        for fidx, cidx in ((0, 0), (n, n - 1)):
+            fsl = [slice(None)] * 3
+            fsl[axis] = slice(fidx, fidx + 1)
+            csl = [slice(None)] * 3
+            csl[axis] = slice(cidx, cidx + 1)
+            q = p[tuple(csl)].ravel()
+            g[tuple(fsl)] = gfn(q, q).reshape(p[tuple(csl)].shape)
+        out.append(g)
+    return tuple(out)
+
+
 def test_grad_val_matches_finite_differences_dense():
     n = 4
     cx, cy, cz = W.diffusion3d_faces(n, 1.0, seed=2)
@@ -358,7 +387,7 @@ def test_grad_val_matches_finite_differences_dense():
     for e_, (i, j) in enumerate(zip(rows, A.col)):
         lookup[(int(i), int(j))] = gval[e_]
     gfn = lambda p, q: np.array([lookup[(int(a), int(c))] for a, c in zip(p, q)])
-    gc = W.diffusion3d_face_grad(n, gfn)
+    gc = _face_grad_chain(n, gfn)
     for axis in range(3):
         for idx in [(0, 0, 0), (1, 2, 3), (3, 3, 3)]:
             idx = tuple(min(v, s - 1) for v, s in zip(idx, gc[axis].shape))
@@ -369,3 +398,73 @@ def test_grad_val_matches_finite_differences_dense():
             lm = loss(c3)
             fd = (lp - lm) / (2 * h)
             assert gc[axis][idx] == pytest.approx(fd, rel=1e-5, abs=1e-8)
+
+
+def _edge_problem(n=4, sigma=1.0):
+    cx, cy, cz = W.diffusion3d_faces(n, sigma, seed=2)
+    A = W.diffusion3d_from_faces(n, cx, cy, cz)
+    b = W.rhs(A.n, 0)
+    xs = np.random.default_rng(9).standard_normal(A.n)
+    c = np.concatenate([cx.ravel(), cy.ravel(), cz.ravel()])
+    return (cx, cy, cz), c, A, b, xs
+
+
+def test_grad_edges_matches_finite_differences_dense():
+    """dL/dc_e from the edge formula vs central differences of L = ||x - x*||^2 with dense
+    library solves, on interior and boundary faces of every axis."""
+    n = 4
+    c3, c, A, b, xs = _edge_problem(n)
+    p, q = W.diffusion3d_face_edges(n)
+    Ad = A.to_dense()
+    x = np.linalg.solve(Ad, b)
+    lam = np.linalg.solve(Ad.T, 2 * (x - xs))
+    g = oracle.grad_edges(p, q, lam, x)
+    sizes = [a.size for a in c3]
+    offs = np.cumsum([0] + sizes)
+
+    def loss(cv):
+        parts = [cv[offs[a]:offs[a + 1]].reshape(c3[a].shape) for a in range(3)]
+        xx = np.linalg.solve(W.diffusion3d_from_faces(n, *parts).to_dense(), b)
+        return float(((xx - xs) ** 2).sum())
+
+    h = 1e-6
+    picks = [e for e in range(len(c)) if q[e] < 0][:6] + [e for e in range(len(c)) if q[e] >= 0][::37]
+    assert any(q[e] < 0 for e in picks) and any(q[e] >= 0 for e in picks)
+    for e in picks:
+        cp = c.copy()
+        cp[e] += h
+        cm = c.copy()
+        cm[e] -= h
+        fd = (loss(cp) - loss(cm)) / (2 * h)
+        assert g[e] == pytest.approx(fd, rel=1e-5, abs=1e-8)
+
+
+def test_grad_edges_homogeneity():
+    """A(c) is linear and homogeneous in c, so sum_e c_e dL/dc_e = -lambda^T A x = -lambda^T b."""
+    n = 5
+    _, c, A, b, xs = _edge_problem(n, sigma=2.0)
+    p, q = W.diffusion3d_face_edges(n)
+    Ad = A.to_dense()
+    x = np.linalg.solve(Ad, b)
+    lam = np.linalg.solve(Ad, 2 * (x - xs))
+    g = oracle.grad_edges(p, q, lam, x)
+    assert float(c @ g) == pytest.approx(-float(lam @ b), rel=1e-10)
+
+
+def test_grad_edges_agrees_with_entry_gradient_chain():
+    """Edge formula == chain rule of the assembly applied to dL/dA_ij = -lambda_i x_j."""
+    n = 4
+    c3, c, A, b, xs = _edge_problem(n)
+    p, q = W.diffusion3d_face_edges(n)
+    Ad = A.to_dense()
+    x = np.linalg.solve(Ad, b)
+    lam = np.linalg.solve(Ad, 2 * (x - xs))
+    gval = oracle.grad_val(A, lam, x)
+    lookup = {}
+    rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
+    for e_, (i, j) in enumerate(zip(rows, A.col)):
+        lookup[(int(i), int(j))] = gval[e_]
+    gfn = lambda pp, qq: np.array([lookup[(int(a), int(d))] for a, d in zip(pp, qq)])
+    chain = np.concatenate([a.ravel() for a in _face_grad_chain(n, gfn)])
+    g = oracle.grad_edges(p, q, lam, x)
+    np.testing.assert_allclose(g, chain, rtol=1e-9, atol=1e-12 * np.abs(chain).max())
