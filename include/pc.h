@@ -231,17 +231,26 @@ pc_status pc_grad_edges(int64_t n_edges, const int32_t *p, const int32_t *q, con
 
 /* ---------------------------------------------------------------------------------
  * Batched mode: many independent SPD systems of uneven size, each with its own block
- * size, set up and solved in ONE persistent launch (each system is owned by one
- * thread-block cluster; cluster barriers replace grid barriers).
- *   n_sys          number of systems.
+ * size.  Block-Jacobi setup (Sec. 3.2-3.3) and PCG to ||b_s - A_s x_s|| <= tol ||b_s||
+ * (Sec. 3.7) for every system run inside ONE persistent cooperative kernel launch, which
+ * pc_batch_solve captures in a CUDA graph (a counter reset plus that launch) and replays.
+ *
+ * Each system is handled by a team of co-resident CTAs sized by its estimated work (a
+ * power of two up to the team limit); teams take queue slots in order of decreasing
+ * work and synchronise through their own bounded release/acquire barriers.  Reductions
+ * are fixed-order, so results are bit-reproducible for a given schedule.
+ *
+ *   n_sys          number of systems (>= 1).
  *   sys_row        device int64 [n_sys+1]: system s owns rows [sys_row[s], sys_row[s+1])
- *                  of the concatenated CSR; row_ptr holds global nnz offsets.
- *   col_idx        LOCAL column indices (0 .. N_s - 1) of each system.
- *   block_size     device int32 [n_sys], each 1..64.
- *   b, x           device [total rows]; x is overwritten (x0 = 0).
- *   iters, status  device int32 [n_sys] outputs; relres device double [n_sys] outputs
- *                  (true relative residual per system).
- * Returns PC_OK if every system converged, else the first non-OK status. */
+ *                  of the concatenated CSR (sys_row[0] = 0, sys_row[n_sys] = n_rows);
+ *                  row_ptr holds global nnz offsets (row_ptr[0] = 0, row_ptr[n_rows] = nnz).
+ *   col_idx        LOCAL column indices (0 .. N_s - 1) of each system, sorted per row,
+ *                  with the diagonal stored.  A system with rows must store entries.
+ *   val            FP64 values.
+ *   block_size     device int32 [n_sys], each 1..max_block_size (<= 64).
+ *   b, x           device [n_rows]; x is overwritten (x0 = 0).
+ * All arrays are caller-owned device memory and must stay valid while a handle that was
+ * created from them is used.  A system with zero rows is reported converged. */
 typedef struct {
   int32_t n_sys;
   int64_t n_rows;           /* total rows */
@@ -254,6 +263,61 @@ typedef struct {
   int32_t max_block_size;   /* host: max over block_size (<= 64) */
 } pc_batch;
 
+typedef struct pc_batch_handle pc_batch_handle;
+
+/* pc_batch_create - validate the batch (an O(nnz) device pass: row pointers
+ * non-decreasing, local columns inside their system), schedule the teams and allocate the
+ * library-owned workspace (4 FP64 vectors of n_rows, the M^{-1} factors, team counters).
+ * prec: PC_PREC_FP64, or PC_PREC_FP32 / PC_PREC_TF32 (FP32 factors applied in FP32, FP64
+ * CG).  pivot_tol: a Cholesky pivot <= pivot_tol * (largest diagonal entry of its block)
+ * marks the system not SPD.  Synchronises the stream.  Errors: PC_ERR_INVALID_ARG
+ * (arguments or CSR structure), PC_ERR_OOM, PC_ERR_CUDA. */
+pc_status pc_batch_create(const pc_batch *B, int32_t prec, double pivot_tol, void *stream,
+                          pc_batch_handle **out);
+
+/* pc_batch_solve - setup + PCG for every system in one launch (graph replay when b, x,
+ * tol and max_iter match the previous call, else a new capture).  max_iter bounds each
+ * system's CG iterations; up to 3 restarts from the true residual.
+ * Outputs (device arrays, each may be NULL): iters, status (pc_status values) int32
+ * [n_sys]; relres double [n_sys] = ||b_s - A_s x_s|| / ||b_s|| (0 for b_s = 0, -1 when
+ * not computed).  info (host, may be NULL): status = first non-OK system status (or
+ * PC_ERR_TIMEOUT), failed_block = the index of that SYSTEM, iterations = max over
+ * systems, true_rel_residual = worst system, solve_ms = device time of the launch,
+ * grid_ctas = persistent grid size, reserved = 1 if the launch went through the graph.
+ * Synchronises the stream. */
+pc_status pc_batch_solve(pc_batch_handle *h, const double *b, double *x, double tol,
+                         int32_t max_iter, int32_t *iters, int32_t *status, double *relres,
+                         pc_solve_info *info, void *stream);
+
+pc_status pc_batch_destroy(pc_batch_handle *h);
+
+/* Launch shape of a handle, host out[]: grid CTAs, CTAs per SM, queue slots, team limit,
+ * dynamic shared memory, setup warps per CTA, graph captured (1/0).  Returns the count
+ * written (<= max_entries). */
+int32_t pc_batch_info(const pc_batch_handle *h, int32_t *out, int32_t max_entries);
+
+/* Team size and first queue slot of every system (host arrays [n_sys], may be NULL).
+ * Returns n_sys. */
+int32_t pc_batch_teams(const pc_batch_handle *h, int32_t *team, int32_t *slot0);
+
+/* The scheduler, host only (no GPU): team sizes, first slots and slot order for systems
+ * of n_rows[s] rows, nnz[s] entries and block size block_size[s] on a grid of n_ctas
+ * CTAs.  A system's cost is its bytes per CG iteration times N^(1/3) (the growth of the
+ * PCG iteration count with kappa ~ N^(2/3) on 3D meshes and geometric graphs); a team
+ * doubles while it stays within team_max and n_ctas, keeps >= 4 warp units per member
+ * and each member keeps >= total / (slots_per_cta * n_ctas) of the cost.  Slots go to
+ * larger teams first, then to longer slots.  Host arrays [n_sys]: team, slot0, order
+ * (systems in slot order).  Returns the number of slots, or -1 on invalid input. */
+int32_t pc_batch_schedule(int32_t n_sys, const int64_t *n_rows, const int64_t *nnz,
+                          const int32_t *block_size, int32_t n_ctas, int32_t team_max,
+                          double slots_per_cta, int32_t *team, int32_t *slot0, int32_t *order);
+
+/* Tuning of handles created afterwards: CTAs per SM of the persistent grid (0 =
+ * occupancy maximum), team limit (0 = 32) and slots per CTA of the scheduler (0 = 2).
+ * Process-wide. */
+void pc_batch_set_tuning(int32_t ctas_per_sm, int32_t team_max, double slots_per_cta);
+
+/* One-shot form: pc_batch_create (pivot_tol 0) + pc_batch_solve + pc_batch_destroy. */
 pc_status pcg_solve_batched(const pc_batch *B, const double *b, double *x, double tol,
                             int32_t max_iter, int32_t prec, int32_t *iters, int32_t *status,
                             double *relres, pc_solve_info *info, void *stream);

@@ -96,6 +96,13 @@ def lib():
         "pc_grad_edges": (_I32, [_I64, _P, _P, _P, _P, _I64, _P, _P]),
         "pcg_solve_batched": (_I32, [ctypes.POINTER(pc_batch), _P, _P, _D, _I32, _I32, _P, _P, _P,
                                      ctypes.POINTER(pc_solve_info), _P]),
+        "pc_batch_create": (_I32, [ctypes.POINTER(pc_batch), _I32, _D, _P, ctypes.POINTER(_P)]),
+        "pc_batch_solve": (_I32, [_P, _P, _P, _D, _I32, _P, _P, _P, ctypes.POINTER(pc_solve_info), _P]),
+        "pc_batch_destroy": (_I32, [_P]),
+        "pc_batch_info": (_I32, [_P, _P, _I32]),
+        "pc_batch_teams": (_I32, [_P, _P, _P]),
+        "pc_batch_schedule": (_I32, [_I32, _P, _P, _P, _I32, _I32, _D, _P, _P, _P]),
+        "pc_batch_set_tuning": (None, [_I32, _I32, _D]),
         "pc_get_trace": (_I32, [_P, _P, _I32]),
         "pc_set_wait_budget": (None, [_I64]),
         "pc_set_ctas_per_sm": (None, [_I32]),
@@ -354,6 +361,102 @@ def grad_edges(p, q, lam, x):
     _check(lib().pc_grad_edges(int(p.numel()), _ptr(p), _ptr(q), _ptr(lam), _ptr(x), int(x.numel()), _ptr(out),
                                _stream()), "pc_grad_edges")
     return out
+
+
+class Batch:
+    """A batch of independent SPD systems on the device (concatenated CSR, local columns)
+    with its pc_batch_create handle.  ``host`` is any object with row_ptr, col, val,
+    sys_row and bs arrays (``workloads.Batch``)."""
+
+    def __init__(self, host, prec: str = "fp64", pivot_tol: float = 0.0):
+        torch = _torch()
+        self.n_sys = int(len(host.bs))
+        self.sys_row = _dev(host.sys_row, torch.int64)
+        self.row_ptr = _dev(host.row_ptr, torch.int32)
+        self.col = _dev(host.col, torch.int32)
+        self.val = _dev(host.val, torch.float64)
+        self.bs = _dev(host.bs, torch.int32)
+        self.n_rows = int(self.row_ptr.numel() - 1)
+        self.prec = prec
+        self._d = pc_batch(self.n_sys, self.n_rows, int(self.col.numel()), self.sys_row.data_ptr(),
+                           self.row_ptr.data_ptr(), self.col.data_ptr(), self.val.data_ptr(), self.bs.data_ptr(),
+                           int(np.max(np.asarray(host.bs))) if self.n_sys else 1)
+        h = ctypes.c_void_p()
+        _check(lib().pc_batch_create(ctypes.byref(self._d), PREC[prec], float(pivot_tol), _stream(), ctypes.byref(h)),
+               "pc_batch_create")
+        self._h = h
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _torch().cuda.current_stream().synchronize()
+            lib().pc_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def solve(self, b, tol: float = 1e-10, max_iter: int = 100000, x=None, check: bool = True):
+        """Setup + PCG of every system in one launch.  Returns (x, per-system dict, info)."""
+        torch = _torch()
+        b = _dev(b, torch.float64)
+        x = torch.empty_like(b) if x is None else x
+        iters = torch.empty(self.n_sys, dtype=torch.int32, device="cuda")
+        status = torch.empty(self.n_sys, dtype=torch.int32, device="cuda")
+        relres = torch.empty(self.n_sys, dtype=torch.float64, device="cuda")
+        info = pc_solve_info()
+        st = lib().pc_batch_solve(self._h, _ptr(b), _ptr(x), float(tol), int(max_iter), _ptr(iters), _ptr(status),
+                                  _ptr(relres), ctypes.byref(info), _stream())
+        if check:
+            _check(st, "pc_batch_solve")
+        per = {"iterations": iters.cpu().numpy(), "status": status.cpu().numpy(), "relres": relres.cpu().numpy()}
+        d = info.to_dict()
+        d["graph"] = bool(info.reserved)
+        return x, per, d
+
+    def launch_info(self) -> dict:
+        out = (ctypes.c_int32 * 8)()
+        k = lib().pc_batch_info(self._h, ctypes.cast(out, ctypes.c_void_p), 8)
+        keys = ("grid", "ctas_per_sm", "slots", "team_max", "smem", "setup_warps", "graph")
+        return {keys[i]: int(out[i]) for i in range(min(k, len(keys)))}
+
+    def teams(self):
+        team = np.zeros(self.n_sys, dtype=np.int32)
+        slot0 = np.zeros(self.n_sys, dtype=np.int32)
+        lib().pc_batch_teams(self._h, team.ctypes.data, slot0.ctypes.data)
+        return team, slot0
+
+
+def pcg_batched(host, b, tol: float = 1e-10, max_iter: int = 100000, prec: str = "fp64", check: bool = True):
+    """One-shot batched solve (create + solve + destroy).  Returns (x, per-system dict, info)."""
+    B = Batch(host, prec)
+    try:
+        return B.solve(b, tol, max_iter, check=check)
+    finally:
+        B.destroy()
+
+
+def batch_schedule(n_rows, nnz, block_size, n_ctas: int, team_max: int = 32, slots_per_cta: float = 2.0):
+    """The library's team scheduler (host only).  Returns (team, slot0, order, n_slots)."""
+    n_rows = np.ascontiguousarray(n_rows, dtype=np.int64)
+    nnz = np.ascontiguousarray(nnz, dtype=np.int64)
+    block_size = np.ascontiguousarray(block_size, dtype=np.int32)
+    k = n_rows.shape[0]
+    team = np.zeros(k, dtype=np.int32)
+    slot0 = np.zeros(k, dtype=np.int32)
+    order = np.zeros(k, dtype=np.int32)
+    n = lib().pc_batch_schedule(k, n_rows.ctypes.data, nnz.ctypes.data, block_size.ctypes.data, int(n_ctas),
+                                int(team_max), float(slots_per_cta), team.ctypes.data, slot0.ctypes.data,
+                                order.ctypes.data)
+    if n < 0:
+        raise PcError(PC_ERR_INVALID_ARG, "pc_batch_schedule")
+    return team, slot0, order, n
+
+
+def batch_set_tuning(ctas_per_sm: int = 0, team_max: int = 0, slots_per_cta: float = 0.0):
+    lib().pc_batch_set_tuning(int(ctas_per_sm), int(team_max), float(slots_per_cta))
 
 
 def set_wait_budget(cycles: int):

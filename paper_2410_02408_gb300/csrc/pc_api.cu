@@ -619,14 +619,6 @@ pc_status kappa_estimate(const pc_csr* A, int32_t block_size, int32_t max_steps,
   return s;
 }
 
-// ------------------------------------------------------------------ batched (see pc_batched.cu)
-pc_status pc_batched_impl(const pc_batch* B, const double* b, double* x, double tol, int32_t max_iter, int32_t prec,
-                          int32_t* iters, int32_t* status, double* relres, pc_solve_info* info, void* stream);
-
-pc_status pcg_solve_batched(const pc_batch* B, const double* b, double* x, double tol, int32_t max_iter,
-                            int32_t prec, int32_t* iters, int32_t* status, double* relres, pc_solve_info* info,
-                            void* stream) {
-  return pc_batched_impl(B, b, x, tol, max_iter, prec, iters, status, relres, info, stream);
-}
+// Batched mode: pc_batched.cu.
 
 }  // extern "C"

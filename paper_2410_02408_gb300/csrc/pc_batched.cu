@@ -1,8 +1,922 @@
-// Batched mode placeholder: replaced by the cluster-per-system persistent kernel.
+// Batched block-Jacobi PCG: many independent SPD systems of uneven size, each with its own
+// block size, set up (Sec. 3.2-3.3) and solved (Hestenes-Stiefel PCG, Sec. 3.7 residual)
+// inside ONE persistent cooperative kernel launch that is captured in a CUDA graph.
+//
+// Work distribution.  The host scheduler gives every system a team of T co-resident CTAs
+// (T a power of two, sized by the system's estimated work) and lays the teams out as
+// consecutive "slots" in order of decreasing work per slot.  Each CTA of the persistent
+// grid takes the next slot from a device counter, runs its share of that system (a
+// contiguous range of warp units / rows) to completion and takes the next slot.  Teams
+// synchronise through their own release/acquire counter; because slots are handed out in
+// increasing order and every CTA is resident, the lowest unfinished team always has all of
+// its members, so the waits cannot deadlock.  Every wait has a cycle budget after which the
+// launch records PC_ERR_TIMEOUT and all waits give up.
+//
+// Reductions are fixed-order: warp xor tree, CTA sum, then each member adds the team's
+// partials in rank order, so every member holds the same bits and reaches the same
+// decisions (convergence, breakdown, restart) without a broadcast.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include "pc.h"
 #include "pc_kernels.cuh"
+#include "pc_setup_unit.cuh"
 
-extern "C" pc_status pc_batched_impl(const pc_batch*, const double*, double*, double, int32_t, int32_t, int32_t*,
-                                     int32_t*, double*, pc_solve_info*, void*) {
-  return PC_ERR_INVALID_ARG;
+namespace pc {
+namespace {
+
+constexpr int BT = 512;   // threads per CTA
+constexpr int BNW = BT / 32;
+
+struct BSys {
+  int64_t row0;   // first row in the concatenated arrays
+  int64_t fac0;   // first factor element of the system
+  int32_t n;      // rows
+  int32_t bs;     // block size
+  int32_t team;   // CTAs on this system
+  int32_t slot0;  // first queue slot of the team
+};
+
+struct BArgs {
+  const BSys* sys;
+  const int32_t* slot_sys;   // queue slot -> system
+  int32_t n_sys, n_slots;
+  const int32_t* rp;         // global row pointers (global nnz offsets)
+  const int32_t* ci;         // local column indices
+  const double* va;
+  const double* b;
+  double* x;
+  double *r, *z, *p, *q;     // workspace vectors, one entry per row
+  void* minv;                // M^{-1} of every system, unit layout, FT
+  double* part;              // [slot][2][4] team partial sums
+  unsigned* cnt;             // [n_sys] team barrier counters
+  unsigned long long* fail;  // [n_sys] smallest failing block (all ones: none)
+  unsigned* queue;           // next slot
+  int* err;                  // first launch-wide error (timeout)
+  int32_t* o_status;         // [n_sys]
+  int32_t* o_iters;          // [n_sys]
+  int32_t* o_restarts;       // [n_sys]
+  double* o_relres;          // [n_sys] true relative residual
+  double tol, pivot_tol;
+  int32_t max_iter, max_restarts;
+  long long budget;
+  int32_t setup_warps;       // warps per CTA with a shared-memory setup slot
+  int32_t slot_bytes;        // shared memory per setup slot
+};
+
+struct Team {
+  int s, rank, T, slot0;
+  unsigned phase;   // team barriers passed
+  unsigned nred;    // team reductions done (partial-buffer parity)
+};
+
+__device__ __forceinline__ double* part_at(const BArgs& a, int slot, unsigned parity) {
+  return a.part + ((size_t)slot * 2 + (parity & 1u)) * 4;
 }
+
+// All CTAs of the team arrive; false if the wait ran out of budget or another wait did.
+// The first wait of a team also covers its formation: a member may have to wait until the
+// last member's CTA has finished its previous system, so it gets a longer budget.
+__device__ bool team_sync(const BArgs& a, Team& t, int* flag) {
+  __syncthreads();
+  if (t.T == 1) return true;
+  if (threadIdx.x == 0) {
+    const unsigned target = (t.phase + 1u) * (unsigned)t.T;
+    red_release_add_u32(&a.cnt[t.s], 1u);
+    const long long t0 = clock64();
+    const long long limit = t.phase == 0 ? 16 * a.budget : a.budget;
+    int good = 1;
+    while ((int)(ld_acquire_u32(&a.cnt[t.s]) - target) < 0) {
+      if (ld_volatile_i32(a.err) != 0 || clock64() - t0 > limit) {
+        atomicCAS(a.err, 0, ST_TIMEOUT);
+        good = 0;
+        break;
+      }
+    }
+    *flag = good;
+  }
+  __syncthreads();
+  t.phase++;
+  return *flag != 0;
+}
+
+// Sum of NV values over the team, identical bits in every thread of every member.
+template <int NV>
+__device__ bool team_allreduce(const BArgs& a, Team& t, double* v, double* red, int* flag) {
+  block_sum<NV>(v, red);
+  if (t.T == 1) return true;
+  const unsigned par = t.nred++;
+  if (threadIdx.x == 0) {
+    double* mine = part_at(a, t.slot0 + t.rank, par);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) __stcg(mine + i, v[i]);
+  }
+  if (!team_sync(a, t, flag)) return false;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double acc = 0.0;
+    for (int m = 0; m < t.T; ++m) acc += __ldcg(part_at(a, t.slot0 + m, par) + i);
+    v[i] = acc;
+  }
+  return true;
+}
+
+// Row of the system's CSR: sum_e val[e] * x[col[e]] in storage order.  The trip count is
+// the warp's longest row (all lanes run every chunk; shorter rows are masked), so the
+// whole warp must call it.  x may have been written by other CTAs: loads bypass L1.
+__device__ __forceinline__ double brow(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                       const double* __restrict__ va, const double* x, int64_t row, bool valid,
+                                       int32_t s_idle) {
+  const int32_t s0 = valid ? __ldg(rp + row) : s_idle;
+  const int32_t e = valid ? __ldg(rp + row + 1) : s_idle;
+  const int32_t cnt = e - s0;
+  const int32_t s = cnt > 0 ? s0 : s_idle;   // an empty row loads (and ignores) a valid entry
+  const int32_t wmax = __reduce_max_sync(FULL, cnt);
+  double acc = 0.0;
+  for (int32_t k0 = 0; k0 < wmax; k0 += 8) {
+    int32_t c[8];
+    double v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int32_t k = s + min(k0 + t, max(cnt, 1) - 1);
+      c[t] = __ldg(ci + k);
+      v[t] = __ldg(va + k);
+    }
+    double xv[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) xv[t] = __ldcg(x + c[t]);
+    const int rem = wmax - k0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      if (t < rem) {
+        const double pr = fma(v[t], xv[t], acc);
+        acc = (k0 + t < cnt) ? pr : acc;
+      }
+    }
+  }
+  return acc;
+}
+
+enum { U_INIT = 0, U_ITER = 1, U_RESTART = 2 };
+
+// Warp-unit pass over the member's units: r update (U_ITER: r -= alpha q, x += alpha p),
+// z = M^{-1} r, p = z (U_INIT/U_RESTART), and the partial sums (r.z, r.r).
+template <typename FT, int BS, int MODE>
+__device__ __forceinline__ void unit_pass(const BArgs& a, const Layout& L, const FT* __restrict__ Mf, int64_t u0,
+                                          int64_t u1, const double* bs_, double* xs, double* rs, double* zs,
+                                          double* ps, const double* qs, double alpha, double& v0, double& v1) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int64_t uM = unit_elems_minv(L);
+  for (int64_t u = u0 + warp; u < u1; u += BNW) {
+    double rv[2] = {0.0, 0.0}, zv[2];
+    int64_t rows[2];
+    bool ok[2] = {false, false};
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      if (t >= L.S) break;
+      bool vld;
+      const int rh = unit_row(L, lane, t, vld);
+      rows[t] = u * L.U + rh;
+      ok[t] = vld && rows[t] < L.n;
+      if (ok[t]) {
+        if (MODE == U_INIT) rv[t] = __ldg(bs_ + rows[t]);
+        else if (MODE == U_RESTART) rv[t] = rs[rows[t]];
+        else rv[t] = fma(-alpha, qs[rows[t]], rs[rows[t]]);
+      }
+    }
+    unit_apply_inv<FT, BS, false>(L, Mf + u * uM, lane, rv, zv);
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      if (t >= L.S || !ok[t]) continue;
+      const int64_t row = rows[t];
+      if (MODE == U_INIT) {
+        xs[row] = 0.0;
+        rs[row] = rv[t];
+      } else if (MODE == U_ITER) {
+        xs[row] = fma(alpha, __ldcg(ps + row), xs[row]);
+        rs[row] = rv[t];
+      }
+      zs[row] = zv[t];
+      if (MODE != U_ITER) __stcg(ps + row, zv[t]);
+      v0 = fma(rv[t], zv[t], v0);
+      v1 = fma(rv[t], rv[t], v1);
+    }
+  }
+}
+
+// One member's share of one system: setup of its units, then PCG with true-residual
+// restarts.  Returns with every member having taken the same decisions.
+template <typename FT, int BS>
+__device__ __noinline__ void solve_system(const BArgs& a, const BSys& d, Team& t, unsigned char* dsm, double* red, int* flag) {
+  const Layout L = make_layout(d.n, d.bs);
+  const int64_t u0 = L.n_units * t.rank / t.T;
+  const int64_t u1 = L.n_units * (t.rank + 1) / t.T;
+  const int64_t rl = u0 * L.U < L.n ? u0 * L.U : L.n;
+  const int64_t rh = u1 * L.U < L.n ? u1 * L.U : L.n;
+  const int32_t* rp = a.rp + d.row0;
+  const double* bs_ = a.b + d.row0;
+  double* xs = a.x + d.row0;
+  double* rs = a.r + d.row0;
+  double* zs = a.z + d.row0;
+  double* ps = a.p + d.row0;
+  double* qs = a.q + d.row0;
+  FT* Mf = reinterpret_cast<FT*>(a.minv) + d.fac0;
+  const int32_t s_idle = __ldg(rp);   // a valid entry index of this system (used by idle lanes)
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  int status = ST_OK, it = 0, restarts = 0;
+  double tt = 0.0;
+  double relres = -1.0;   // -1: not computed (setup failure, timeout)
+
+  // ---- setup: extract + factor this member's units
+  if (warp < a.setup_warps) {
+    FT* As = reinterpret_cast<FT*>(dsm + (size_t)warp * a.slot_bytes);
+    FT* Xs = As + (size_t)L.U * (L.bs + 1);
+    const int64_t uM = unit_elems_minv(L);
+    for (int64_t u = u0 + warp; u < u1; u += a.setup_warps)
+      setup_unit<double, FT>(L, u, rp, a.ci, a.va, a.pivot_tol, Mf + u * uM, nullptr, As, Xs, lane, &a.fail[t.s]);
+  }
+  __syncthreads();
+
+  // ---- x0 = 0: r = b, z = M^{-1} r, p = z; ||b||^2, rho = r.z
+  double v[3] = {0.0, 0.0, 0.0};
+  {
+    double rz = 0.0, rr = 0.0;
+    unit_pass<FT, BS, U_INIT>(a, L, Mf, u0, u1, bs_, xs, rs, zs, ps, qs, 0.0, rz, rr);
+    v[0] = rr;
+    v[1] = rz;
+  }
+  if (!team_allreduce<2>(a, t, v, red, flag)) {
+    status = ST_TIMEOUT;
+    goto done;
+  }
+  {
+    const double bb = v[0];
+    const double bnorm = sqrt(bb);
+    double rho = v[1];
+    if (*(volatile unsigned long long*)&a.fail[t.s] != ~0ull) {
+      status = ST_NOT_SPD;
+      goto done;
+    }
+    if (bb == 0.0) {   // x = 0 is exact
+      relres = 0.0;
+      goto done;
+    }
+    double rr = bb;
+    for (;;) {
+      // ---- CG iterations until the recurrence residual meets the tolerance
+      while (!(sqrt(rr) <= a.tol * bnorm)) {
+        if (it >= a.max_iter) {
+          status = ST_NO_CONV;
+          break;
+        }
+        if (!(rho > 0.0) || !isfinite(rho)) {
+          status = ST_BREAKDOWN;
+          break;
+        }
+        // q = A p, p.q
+        double pq[1] = {0.0};
+        for (int64_t base = rl; base < rh; base += BT) {
+          const int64_t row = base + threadIdx.x;
+          const bool valid = row < rh;
+          const double qi = brow(rp, a.ci, a.va, ps, row, valid, s_idle);
+          if (valid) {
+            qs[row] = qi;
+            pq[0] = fma(__ldcg(ps + row), qi, pq[0]);
+          }
+        }
+        if (!team_allreduce<1>(a, t, pq, red, flag)) {
+          status = ST_TIMEOUT;
+          goto done;
+        }
+        if (!(pq[0] > 0.0) || !isfinite(pq[0])) {
+          status = ST_BREAKDOWN;
+          break;
+        }
+        const double alpha = rho / pq[0];
+        // x += alpha p, r -= alpha q, z = M^{-1} r, r.z, r.r
+        double w[2] = {0.0, 0.0};
+        unit_pass<FT, BS, U_ITER>(a, L, Mf, u0, u1, bs_, xs, rs, zs, ps, qs, alpha, w[0], w[1]);
+        if (!team_allreduce<2>(a, t, w, red, flag)) {
+          status = ST_TIMEOUT;
+          goto done;
+        }
+        ++it;
+        rr = w[1];
+        if (sqrt(rr) <= a.tol * bnorm) break;
+        const double beta = w[0] / rho;
+        rho = w[0];
+        // p = z + beta p
+        for (int64_t row = rl + threadIdx.x; row < rh; row += BT) __stcg(ps + row, fma(beta, __ldcg(ps + row), zs[row]));
+        if (!team_sync(a, t, flag)) {
+          status = ST_TIMEOUT;
+          goto done;
+        }
+      }
+      // ---- true residual t = b - A x (stored in r for a restart); also reported when the
+      // iteration stopped without convergence
+      double tv[1] = {0.0};
+      for (int64_t base = rl; base < rh; base += BT) {
+        const int64_t row = base + threadIdx.x;
+        const bool valid = row < rh;
+        const double ax = brow(rp, a.ci, a.va, xs, row, valid, s_idle);
+        if (valid) {
+          const double ti = bs_[row] - ax;
+          rs[row] = ti;
+          tv[0] = fma(ti, ti, tv[0]);
+        }
+      }
+      // x is written by every member during the iterations: the SpMV above gathers it
+      // across members, so the team must have finished its last x update first.  The
+      // reduction before the convergence break is that barrier: the last unit pass came
+      // before it.
+      if (!team_allreduce<1>(a, t, tv, red, flag)) {
+        status = ST_TIMEOUT;
+        goto done;
+      }
+      tt = tv[0];
+      relres = sqrt(tt) / bnorm;
+      if (status != ST_OK) break;
+      if (sqrt(tt) <= a.tol * bnorm) break;
+      if (restarts >= a.max_restarts) {
+        status = ST_NO_CONV;
+        break;
+      }
+      ++restarts;
+      // restart from x: r = t, z = M^{-1} r, p = z
+      __syncthreads();
+      double w[2] = {0.0, 0.0};
+      unit_pass<FT, BS, U_RESTART>(a, L, Mf, u0, u1, bs_, xs, rs, zs, ps, qs, 0.0, w[0], w[1]);
+      if (!team_allreduce<2>(a, t, w, red, flag)) {
+        status = ST_TIMEOUT;
+        goto done;
+      }
+      rho = w[0];
+      rr = w[1];
+    }
+  }
+done:
+  if (t.rank == 0 && threadIdx.x == 0) {
+    a.o_status[t.s] = status;
+    a.o_iters[t.s] = it;
+    a.o_restarts[t.s] = restarts;
+    a.o_relres[t.s] = relres;
+  }
+  __syncthreads();
+}
+
+template <typename FT>
+__global__ void __launch_bounds__(BT, 2) batched_kernel(const BArgs a) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ double red[2 * 32];
+  __shared__ int s_slot;
+  __shared__ int flag;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_slot = (int)atomicAdd(a.queue, 1u);
+    __syncthreads();
+    const int slot = s_slot;
+    if (slot >= a.n_slots) break;
+    const int s = __ldg(a.slot_sys + slot);
+    const BSys d = a.sys[s];
+    Team t;
+    t.s = s;
+    t.T = d.team;
+    t.slot0 = d.slot0;
+    t.rank = slot - d.slot0;
+    t.phase = 0;
+    t.nred = 0;
+    if (d.n == 0) {
+      if (t.rank == 0 && threadIdx.x == 0) {
+        a.o_status[s] = ST_OK;
+        a.o_iters[s] = 0;
+        a.o_restarts[s] = 0;
+        a.o_relres[s] = 0.0;
+      }
+      continue;
+    }
+    switch (d.bs) {
+      case 4: solve_system<FT, 4>(a, d, t, dsm, red, &flag); break;
+      case 8: solve_system<FT, 8>(a, d, t, dsm, red, &flag); break;
+      case 16: solve_system<FT, 16>(a, d, t, dsm, red, &flag); break;
+      case 32: solve_system<FT, 32>(a, d, t, dsm, red, &flag); break;
+      case 64: solve_system<FT, 64>(a, d, t, dsm, red, &flag); break;
+      default: solve_system<FT, 0>(a, d, t, dsm, red, &flag); break;
+    }
+  }
+}
+
+// Resets the launch's counters (part of the captured graph).
+__global__ void batched_reset(unsigned* queue, int* err, unsigned* cnt, unsigned long long* fail, int n_sys) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    *queue = 0u;
+    *err = 0;
+  }
+  for (int s = i; s < n_sys; s += gridDim.x * blockDim.x) {
+    cnt[s] = 0u;
+    fail[s] = ~0ull;
+  }
+}
+
+// CSR checks of the concatenated batch: row pointers non-decreasing and inside [0, nnz],
+// every local column index inside its system.  bad[0] counts violations.
+__global__ void batched_validate(const int64_t* __restrict__ sys_row, int n_sys, const int32_t* __restrict__ rp,
+                                 const int32_t* __restrict__ ci, int64_t nnz, unsigned* bad) {
+  const int s = blockIdx.x;
+  if (s >= n_sys) return;
+  const int64_t r0 = sys_row[s], r1 = sys_row[s + 1];
+  const int32_t n = (int32_t)(r1 - r0);
+  unsigned nbad = 0;
+  for (int64_t row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
+    const int32_t e0 = rp[row], e1 = rp[row + 1];
+    if (e0 < 0 || e1 < e0 || (int64_t)e1 > nnz) {
+      ++nbad;
+      continue;
+    }
+    for (int32_t e = e0; e < e1; ++e) {
+      const int32_t c = ci[e];
+      if (c < 0 || c >= n) ++nbad;
+    }
+  }
+  if (nbad) atomicAdd(bad, nbad);
+}
+
+}  // namespace
+}  // namespace pc
+
+// ------------------------------------------------------------------ host side
+using pc::BSys;
+
+struct pc_batch_handle {
+  int32_t n_sys = 0;
+  int64_t n_rows = 0, nnz = 0;
+  int32_t prec = 0;
+  bool fac_f32 = false;
+  int grid = 0, ctas_per_sm = 0, team_max = 0;
+  int n_slots = 0;
+  pc::BArgs args{};
+  int smem = 0;
+  // device memory (library-owned)
+  BSys* sys = nullptr;
+  int32_t* slot_sys = nullptr;
+  double* work = nullptr;   // r, z, p, q
+  void* minv = nullptr;
+  double* part = nullptr;
+  unsigned* cnt = nullptr;
+  unsigned long long* fail = nullptr;
+  unsigned* misc = nullptr;   // queue, err, bad
+  int32_t* o_restarts = nullptr;
+  int32_t* d_status = nullptr;
+  int32_t* d_iters = nullptr;
+  double* d_relres = nullptr;
+  // host copies
+  std::vector<BSys> hsys;
+  std::vector<int32_t> hslot;
+  // captured launch
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool graph_ok = false;
+  const double* g_b = nullptr;
+  double* g_x = nullptr;
+  double g_tol = -1.0;
+  int32_t g_max_iter = -1;
+};
+
+namespace {
+
+pc_status bfrom(cudaError_t e) {
+  if (e == cudaSuccess) return PC_OK;
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? PC_ERR_OOM : PC_ERR_CUDA;
+}
+
+#define PCB_TRY(expr)                          \
+  do {                                         \
+    cudaError_t _e = (expr);                   \
+    if (_e != cudaSuccess) return bfrom(_e);   \
+  } while (0)
+
+template <typename T>
+pc_status balloc(T** p, size_t bytes) {
+  *p = nullptr;
+  cudaError_t e = cudaMalloc((void**)p, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return bfrom(e);
+  }
+  return PC_OK;
+}
+
+long long batch_budget() {
+  const char* e = getenv("PC_WAIT_BUDGET");
+  if (e) {
+    const long long v = atoll(e);
+    if (v > 0) return v;
+  }
+  return 4000000000LL;
+}
+
+int g_batch_ctas_per_sm = 0;   // 0: occupancy maximum
+int g_batch_team_max = 0;      // 0: default
+double g_batch_split = 0.0;    // 0: default slots-per-CTA target
+
+}  // namespace
+
+extern "C" {
+
+void pc_batch_set_tuning(int32_t ctas_per_sm, int32_t team_max, double slots_per_cta) {
+  g_batch_ctas_per_sm = ctas_per_sm > 0 ? ctas_per_sm : 0;
+  g_batch_team_max = team_max > 0 ? team_max : 0;
+  g_batch_split = slots_per_cta > 0.0 ? slots_per_cta : 0.0;
+}
+
+int32_t pc_batch_schedule(int32_t n_sys, const int64_t* n_rows, const int64_t* nnz, const int32_t* block_size,
+                          int32_t n_ctas, int32_t team_max, double slots_per_cta, int32_t* team, int32_t* slot0,
+                          int32_t* order) {
+  if (n_sys < 1 || !n_rows || !nnz || !block_size || n_ctas < 1 || team_max < 1 || !team || !slot0 || !order)
+    return -1;
+  // Estimated cost of a system: bytes per CG iteration (CSR, factor, ~11 vector streams)
+  // times an iteration count that grows like N^(1/3) (PCG iterations ~ sqrt(kappa) and
+  // kappa ~ N^(2/3) for meshes and geometric graphs in 3D).
+  std::vector<double> w(n_sys);
+  double total = 0.0;
+  for (int s = 0; s < n_sys; ++s) {
+    if (n_rows[s] < 0 || nnz[s] < 0 || block_size[s] < 1 || block_size[s] > 64) return -1;
+    const double n = (double)n_rows[s];
+    const double fac = (double)(block_size[s] / 2 + 1) * 4.0;
+    w[s] = (12.0 * (double)nnz[s] + (88.0 + fac) * n) * std::cbrt(std::max(n, 1.0));
+    total += w[s];
+  }
+  const double target = total / (std::max(slots_per_cta, 0.25) * (double)n_ctas);
+  std::vector<double> per_slot(n_sys);
+  for (int s = 0; s < n_sys; ++s) {
+    const int bs = block_size[s];
+    const int64_t U = bs <= 32 ? (32 / bs) * bs : bs;
+    const int64_t units = (n_rows[s] + U - 1) / U;
+    int T = 1;
+    while (T * 2 <= team_max && T * 2 <= n_ctas && (double)(T * 2) * target <= w[s] && units >= (int64_t)T * 2 * 4)
+      T *= 2;
+    team[s] = T;
+    per_slot[s] = w[s] / T;
+  }
+  for (int s = 0; s < n_sys; ++s) order[s] = s;
+  // Larger teams first (they form while the grid is still free), then longest slot first.
+  std::stable_sort(order, order + n_sys, [&](int a, int b) {
+    if (team[a] != team[b]) return team[a] > team[b];
+    return per_slot[a] > per_slot[b];
+  });
+  int32_t k = 0;
+  for (int i = 0; i < n_sys; ++i) {
+    slot0[order[i]] = k;
+    k += team[order[i]];
+  }
+  return k;
+}
+
+pc_status pc_batch_destroy(pc_batch_handle* h) {
+  if (!h) return PC_OK;
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  void* ptrs[] = {h->sys, h->slot_sys, h->work, h->minv, h->part, h->cnt, h->fail, h->misc, h->o_restarts,
+                  h->d_status, h->d_iters, h->d_relres};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete h;
+  return PC_OK;
+}
+
+pc_status pc_batch_create(const pc_batch* B, int32_t prec, double pivot_tol, void* stream, pc_batch_handle** out) {
+  if (out) *out = nullptr;
+  if (!B || !out || B->n_sys < 1 || B->n_rows < 0 || B->nnz < 1 || B->nnz >= (int64_t)INT32_MAX || !B->sys_row ||
+      !B->row_ptr || !B->col_idx || !B->val || !B->block_size || B->max_block_size < 1 || B->max_block_size > 64 ||
+      (prec != PC_PREC_FP64 && prec != PC_PREC_FP32 && prec != PC_PREC_TF32) || !(pivot_tol >= 0.0))
+    return PC_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n_sys = B->n_sys;
+  std::vector<int64_t> srow(n_sys + 1);
+  std::vector<int32_t> hbs(n_sys);
+  std::vector<int32_t> hrp(n_sys + 1);
+  PCB_TRY(cudaMemcpyAsync(srow.data(), B->sys_row, sizeof(int64_t) * (n_sys + 1), cudaMemcpyDeviceToHost, st));
+  PCB_TRY(cudaMemcpyAsync(hbs.data(), B->block_size, sizeof(int32_t) * n_sys, cudaMemcpyDeviceToHost, st));
+  PCB_TRY(cudaStreamSynchronize(st));
+  if (srow[0] != 0 || srow[n_sys] != B->n_rows) return PC_ERR_INVALID_ARG;
+  for (int s = 0; s < n_sys; ++s) {
+    if (srow[s + 1] < srow[s] || srow[s + 1] - srow[s] >= (int64_t)INT32_MAX) return PC_ERR_INVALID_ARG;
+    if (hbs[s] < 1 || hbs[s] > B->max_block_size) return PC_ERR_INVALID_ARG;
+  }
+  for (int s = 0; s <= n_sys; ++s)
+    PCB_TRY(cudaMemcpyAsync(&hrp[s], B->row_ptr + srow[s], sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  PCB_TRY(cudaStreamSynchronize(st));
+  if (hrp[0] != 0 || (int64_t)hrp[n_sys] != B->nnz) return PC_ERR_INVALID_ARG;
+  for (int s = 0; s < n_sys; ++s)
+    if (hrp[s + 1] < hrp[s] || (srow[s + 1] > srow[s] && hrp[s + 1] == hrp[s])) return PC_ERR_INVALID_ARG;
+
+  pc_batch_handle* h = new pc_batch_handle();
+  h->n_sys = n_sys;
+  h->n_rows = B->n_rows;
+  h->nnz = B->nnz;
+  h->prec = prec;
+  h->fac_f32 = prec != PC_PREC_FP64;
+  const size_t fts = h->fac_f32 ? sizeof(float) : sizeof(double);
+  pc_status ps = PC_OK;
+#define PCB_CHECK(expr)            \
+  do {                             \
+    ps = (expr);                   \
+    if (ps != PC_OK) {             \
+      pc_batch_destroy(h);         \
+      return ps;                   \
+    }                              \
+  } while (0)
+#define PCB_CUDA(expr) PCB_CHECK(bfrom(expr))
+
+  // validation of the concatenated CSR on the device
+  PCB_CHECK(balloc(&h->misc, 4 * sizeof(unsigned)));
+  PCB_CUDA(cudaMemsetAsync(h->misc, 0, 4 * sizeof(unsigned), st));
+  pc::batched_validate<<<n_sys, 256, 0, st>>>(B->sys_row, n_sys, B->row_ptr, B->col_idx, B->nnz, h->misc + 2);
+  PCB_CUDA(cudaGetLastError());
+  unsigned bad = 0;
+  PCB_CUDA(cudaMemcpyAsync(&bad, h->misc + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  PCB_CUDA(cudaStreamSynchronize(st));
+  if (bad) PCB_CHECK(PC_ERR_INVALID_ARG);
+
+  // shared memory: setup slots large enough for every block size up to the maximum (the
+  // need is not monotone in bs: U = 32 rows for bs <= 32 only when bs divides 32), as
+  // many slots as fit in the budget
+  size_t need = 0;
+  for (int bsz = 1; bsz <= B->max_block_size; ++bsz)
+    need = std::max(need, pc::setup_unit_smem(pc::make_layout(64, bsz), fts));
+  const int slot_bytes = (int)((need + 15) & ~(size_t)15);
+  const int budget = 70 * 1024;
+  int setup_warps = std::max(1, std::min(pc::BNW, budget / slot_bytes));
+  h->smem = setup_warps * slot_bytes;
+  const void* fn = h->fac_f32 ? (const void*)pc::batched_kernel<float> : (const void*)pc::batched_kernel<double>;
+  PCB_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem));
+  int occ = 0;
+  PCB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, pc::BT, (size_t)h->smem));
+  if (occ < 1) PCB_CHECK(PC_ERR_CUDA);
+  if (g_batch_ctas_per_sm > 0 && g_batch_ctas_per_sm < occ) occ = g_batch_ctas_per_sm;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  h->ctas_per_sm = occ;
+  h->grid = occ * std::max(sms, 1);
+
+  // schedule
+  std::vector<int64_t> nr(n_sys), nz(n_sys);
+  for (int s = 0; s < n_sys; ++s) {
+    nr[s] = srow[s + 1] - srow[s];
+    nz[s] = (int64_t)hrp[s + 1] - hrp[s];
+  }
+  std::vector<int32_t> team(n_sys), slot0(n_sys), order(n_sys);
+  h->team_max = g_batch_team_max > 0 ? g_batch_team_max : 32;
+  const double split = g_batch_split > 0.0 ? g_batch_split : 2.0;
+  const int n_slots = pc_batch_schedule(n_sys, nr.data(), nz.data(), hbs.data(), h->grid, h->team_max, split,
+                                        team.data(), slot0.data(), order.data());
+  if (n_slots < 1) PCB_CHECK(PC_ERR_INVALID_ARG);
+  h->n_slots = n_slots;
+  h->hsys.resize(n_sys);
+  h->hslot.resize(n_slots);
+  int64_t fac = 0;
+  for (int s = 0; s < n_sys; ++s) {
+    const pc::Layout L = pc::make_layout(nr[s], hbs[s]);
+    BSys& d = h->hsys[s];
+    d.row0 = srow[s];
+    d.fac0 = fac;
+    d.n = (int32_t)nr[s];
+    d.bs = hbs[s];
+    d.team = team[s];
+    d.slot0 = slot0[s];
+    fac += L.n_units * pc::unit_elems_minv(L);
+    for (int m = 0; m < team[s]; ++m) h->hslot[slot0[s] + m] = s;
+  }
+
+  // device memory
+  PCB_CHECK(balloc(&h->sys, sizeof(BSys) * n_sys));
+  PCB_CHECK(balloc(&h->slot_sys, sizeof(int32_t) * n_slots));
+  PCB_CHECK(balloc(&h->work, sizeof(double) * 4 * (size_t)std::max<int64_t>(B->n_rows, 1)));
+  PCB_CHECK(balloc(&h->minv, fts * (size_t)std::max<int64_t>(fac, 1)));
+  PCB_CHECK(balloc(&h->part, sizeof(double) * 8 * (size_t)n_slots));
+  PCB_CHECK(balloc(&h->cnt, sizeof(unsigned) * n_sys));
+  PCB_CHECK(balloc(&h->fail, sizeof(unsigned long long) * n_sys));
+  PCB_CHECK(balloc(&h->o_restarts, sizeof(int32_t) * n_sys));
+  PCB_CHECK(balloc(&h->d_status, sizeof(int32_t) * n_sys));
+  PCB_CHECK(balloc(&h->d_iters, sizeof(int32_t) * n_sys));
+  PCB_CHECK(balloc(&h->d_relres, sizeof(double) * n_sys));
+  PCB_CUDA(cudaMemcpyAsync(h->sys, h->hsys.data(), sizeof(BSys) * n_sys, cudaMemcpyHostToDevice, st));
+  PCB_CUDA(cudaMemcpyAsync(h->slot_sys, h->hslot.data(), sizeof(int32_t) * n_slots, cudaMemcpyHostToDevice, st));
+  PCB_CUDA(cudaStreamSynchronize(st));   // host vectors are the copy sources
+
+  pc::BArgs& a = h->args;
+  memset(&a, 0, sizeof(a));
+  a.sys = h->sys;
+  a.slot_sys = h->slot_sys;
+  a.n_sys = n_sys;
+  a.n_slots = n_slots;
+  a.rp = B->row_ptr;
+  a.ci = B->col_idx;
+  a.va = B->val;
+  const int64_t nr_all = std::max<int64_t>(B->n_rows, 1);
+  a.r = h->work;
+  a.z = h->work + nr_all;
+  a.p = h->work + 2 * nr_all;
+  a.q = h->work + 3 * nr_all;
+  a.minv = h->minv;
+  a.part = h->part;
+  a.cnt = h->cnt;
+  a.fail = h->fail;
+  a.queue = h->misc;
+  a.err = reinterpret_cast<int*>(h->misc + 1);
+  a.o_status = h->d_status;
+  a.o_iters = h->d_iters;
+  a.o_restarts = h->o_restarts;
+  a.o_relres = h->d_relres;
+  a.pivot_tol = pivot_tol;
+  a.max_restarts = 3;
+  a.budget = batch_budget();
+  a.setup_warps = setup_warps;
+  a.slot_bytes = slot_bytes;
+  *out = h;
+  return PC_OK;
+#undef PCB_CUDA
+#undef PCB_CHECK
+}
+
+static cudaError_t batch_launch(pc_batch_handle* h, cudaStream_t st) {
+  pc::batched_reset<<<std::max(1, std::min(1024, (h->n_sys + 255) / 256)), 256, 0, st>>>(
+      h->misc, reinterpret_cast<int*>(h->misc + 1), h->cnt, h->fail, h->n_sys);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3((unsigned)h->grid);
+  cfg.blockDim = dim3(pc::BT);
+  cfg.dynamicSmemBytes = (size_t)h->smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (h->fac_f32) return cudaLaunchKernelEx(&cfg, pc::batched_kernel<float>, h->args);
+  return cudaLaunchKernelEx(&cfg, pc::batched_kernel<double>, h->args);
+}
+
+static cudaError_t batch_capture(pc_batch_handle* h, cudaStream_t st) {
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->exec = nullptr;
+  h->graph = nullptr;
+  cudaStream_t cs;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t le = batch_launch(h, cs);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cs, &g);
+    if (le != cudaSuccess) e = le;
+    if (e == cudaSuccess) {
+      h->graph = g;
+      e = cudaGraphInstantiate(&h->exec, g, 0);
+    } else if (g) {
+      cudaGraphDestroy(g);
+    }
+  }
+  cudaStreamDestroy(cs);
+  (void)st;
+  return e;
+}
+
+pc_status pc_batch_solve(pc_batch_handle* h, const double* b, double* x, double tol, int32_t max_iter,
+                         int32_t* iters, int32_t* status, double* relres, pc_solve_info* info, void* stream) {
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->failed_block = -1;
+  }
+  if (!h || (!b && h->n_rows > 0) || (!x && h->n_rows > 0) || !(tol >= 0.0) || max_iter < 0)
+    return PC_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->args.b = b;
+  h->args.x = x;
+  h->args.tol = tol;
+  h->args.max_iter = max_iter;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  PCB_TRY(cudaEventCreate(&e0));
+  PCB_TRY(cudaEventCreate(&e1));
+  cudaError_t e = cudaSuccess;
+  const bool same = h->exec && h->g_b == b && h->g_x == x && h->g_tol == tol && h->g_max_iter == max_iter;
+  if (!same) {
+    e = batch_capture(h, st);
+    h->graph_ok = e == cudaSuccess;
+    if (h->graph_ok) {
+      h->g_b = b;
+      h->g_x = x;
+      h->g_tol = tol;
+      h->g_max_iter = max_iter;
+    } else {
+      cudaGetLastError();
+      h->exec = nullptr;
+    }
+  }
+  cudaEventRecord(e0, st);
+  if (h->graph_ok) e = cudaGraphLaunch(h->exec, st);
+  else e = batch_launch(h, st);
+  cudaEventRecord(e1, st);
+  int err = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&err, h->misc + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
+  std::vector<int32_t> hs(h->n_sys), hi(h->n_sys), hr(h->n_sys);
+  std::vector<double> hrel(h->n_sys);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), h->d_status, sizeof(int32_t) * h->n_sys, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hi.data(), h->d_iters, sizeof(int32_t) * h->n_sys, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hr.data(), h->o_restarts, sizeof(int32_t) * h->n_sys, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hrel.data(), h->d_relres, sizeof(double) * h->n_sys, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && iters) e = cudaMemcpyAsync(iters, h->d_iters, sizeof(int32_t) * h->n_sys, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && status)
+    e = cudaMemcpyAsync(status, h->d_status, sizeof(int32_t) * h->n_sys, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && relres)
+    e = cudaMemcpyAsync(relres, h->d_relres, sizeof(double) * h->n_sys, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  float ms = 0.f;
+  if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return bfrom(e);
+  pc_status out = PC_OK;
+  int max_it = 0, max_rs = 0;
+  double worst = 0.0;
+  for (int s = 0; s < h->n_sys; ++s) {
+    max_it = std::max(max_it, hi[s]);
+    max_rs = std::max(max_rs, hr[s]);
+    worst = std::max(worst, hrel[s]);
+    if (out == PC_OK && hs[s] != pc::ST_OK) {
+      out = hs[s] == pc::ST_NOT_SPD   ? PC_ERR_NOT_SPD
+            : hs[s] == pc::ST_BREAKDOWN ? PC_ERR_BREAKDOWN
+            : hs[s] == pc::ST_NO_CONV   ? PC_ERR_NO_CONVERGENCE
+            : hs[s] == pc::ST_TIMEOUT   ? PC_ERR_TIMEOUT
+                                        : PC_ERR_CUDA;
+      if (info) info->failed_block = s;
+    }
+  }
+  if (err == pc::ST_TIMEOUT) out = PC_ERR_TIMEOUT;
+  if (info) {
+    info->status = out;
+    info->iterations = max_it;
+    info->restarts = max_rs;
+    info->rel_residual = worst;
+    info->true_rel_residual = worst;
+    info->setup_ms = 0.0;
+    info->solve_ms = ms;
+    info->grid_ctas = h->grid;
+    info->block_size = 0;
+    info->prec = h->prec;
+    info->reserved = h->graph_ok ? 1 : 0;
+  }
+  return out;
+}
+
+int32_t pc_batch_info(const pc_batch_handle* h, int32_t* out, int32_t max_entries) {
+  if (!h || !out || max_entries < 1) return 0;
+  const int32_t vals[] = {h->grid, h->ctas_per_sm, h->n_slots, h->team_max, h->smem, h->args.setup_warps,
+                          h->graph_ok ? 1 : 0};
+  const int32_t k = std::min<int32_t>(max_entries, (int32_t)(sizeof(vals) / sizeof(vals[0])));
+  for (int32_t i = 0; i < k; ++i) out[i] = vals[i];
+  return k;
+}
+
+int32_t pc_batch_teams(const pc_batch_handle* h, int32_t* team, int32_t* slot0) {
+  if (!h) return 0;
+  for (int s = 0; s < h->n_sys; ++s) {
+    if (team) team[s] = h->hsys[s].team;
+    if (slot0) slot0[s] = h->hsys[s].slot0;
+  }
+  return h->n_sys;
+}
+
+pc_status pcg_solve_batched(const pc_batch* B, const double* b, double* x, double tol, int32_t max_iter,
+                            int32_t prec, int32_t* iters, int32_t* status, double* relres, pc_solve_info* info,
+                            void* stream) {
+  pc_batch_handle* h = nullptr;
+  pc_status s = pc_batch_create(B, prec, 0.0, stream, &h);
+  if (s != PC_OK) {
+    if (info) {
+      memset(info, 0, sizeof(*info));
+      info->status = s;
+      info->failed_block = -1;
+    }
+    return s;
+  }
+  s = pc_batch_solve(h, b, x, tol, max_iter, iters, status, relres, info, stream);
+  pc_batch_destroy(h);
+  return s;
+}
+
+}  // extern "C"

@@ -1,13 +1,8 @@
-// Block-Jacobi setup (Sec. 3.2-3.3): extract each diagonal block A_kk from CSR and
-// factor it, A_kk = L_k L_k^T, then form L_k^{-1} and M_k^{-1} = L_k^{-T} L_k^{-1}.
-//
-// One warp owns one warp unit (whole blocks, see pc_common.cuh).  The unit's blocks sit
-// in shared memory as dense rows (row stride bs+1): lane l owns unit row l (and l+32 for
-// blocks of 33..64 rows).  Extraction, the right-looking Cholesky (lanes = rows, lockstep
-// over the pivot column), the triangular inverse (lanes = columns, independent) and the
-// products for M^{-1} all run from shared memory; the results are written straight into
-// the coalesced unit layouts used by the apply kernels.
+// Block-Jacobi setup (Sec. 3.2-3.3) for one matrix: every warp factors warp units with
+// setup_unit (extraction from CSR, block Cholesky, L^{-1}, M^{-1}); plus the dense
+// extraction and factor read-back used for inspection.
 #include "pc_kernels.cuh"
+#include "pc_setup_unit.cuh"
 
 namespace pc {
 
@@ -18,127 +13,15 @@ __global__ void __launch_bounds__(128) setup_kernel(SetupArgs a) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
-  const int bs = L.bs;
-  const int ld = bs + 1;
-  FT* As = reinterpret_cast<FT*>(smem_raw) + (size_t)warp * 2 * L.U * ld;
-  FT* Xs = As + (size_t)L.U * ld;
+  FT* As = reinterpret_cast<FT*>(smem_raw) + (size_t)warp * 2 * L.U * (L.bs + 1);
+  FT* Xs = As + (size_t)L.U * (L.bs + 1);
   const VT* va = reinterpret_cast<const VT*>(a.val);
   FT* Mo = reinterpret_cast<FT*>(a.minv);
   FT* Lo = reinterpret_cast<FT*>(a.linv);
   const int64_t uM = unit_elems_minv(L), uL = unit_elems_linv(L);
-
-  for (int64_t u = (int64_t)blockIdx.x * nw + warp; u < L.n_units; u += (int64_t)gridDim.x * nw) {
-    const int64_t urow0 = u * L.U;
-    // ---- zero, then extract (identity on rows past n)
-    for (int t = lane; t < L.U * ld; t += 32) {
-      As[t] = FT(0);
-      Xs[t] = FT(0);
-    }
-    __syncwarp();
-    for (int s = 0; s < L.S; ++s) {
-      const int rho = lane + 32 * s;
-      if (rho >= L.U) continue;
-      const int i = rho % bs;
-      const int64_t row = urow0 + rho;
-      if (row < L.n) {
-        const int64_t bstart = row - i;
-        const int32_t e0 = a.row_ptr[row], e1 = a.row_ptr[row + 1];
-        for (int32_t e = e0; e < e1; ++e) {
-          const int64_t c = a.col[e];
-          if (c >= bstart && c < bstart + bs) As[rho * ld + (int)(c - bstart)] = (FT)va[e];
-        }
-      } else {
-        As[rho * ld + i] = FT(1);
-      }
-    }
-    __syncwarp();
-    // ---- per-block pivot scale: max diagonal entry of the block
-    FT dmax[2] = {FT(0), FT(0)};
-    for (int s = 0; s < L.S; ++s) {
-      const int rho = lane + 32 * s;
-      if (rho >= L.U) continue;
-      const int gb = rho - rho % bs;
-      FT m = FT(0);
-      for (int t = 0; t < bs; ++t)
-        if (urow0 + gb + t < L.n) m = max(m, As[(gb + t) * ld + t]);
-      dmax[s] = m;
-    }
-    // ---- right-looking Cholesky, lanes = rows
-    for (int j = 0; j < bs; ++j) {
-      for (int s = 0; s < L.S; ++s) {
-        const int rho = lane + 32 * s;
-        if (rho >= L.U) continue;
-        if (rho % bs == j) {
-          FT d = As[rho * ld + j];
-          if (urow0 + rho < L.n && (!(d > FT(a.tol) * dmax[s]) || !isfinite((double)d))) {
-            const unsigned long long blk = (unsigned long long)((urow0 + rho) / bs);
-            atomicMin(a.failed, blk);
-            d = FT(1);
-          }
-          As[rho * ld + j] = sqrt(d);
-        }
-      }
-      __syncwarp();
-      for (int s = 0; s < L.S; ++s) {
-        const int rho = lane + 32 * s;
-        if (rho >= L.U) continue;
-        const int i = rho % bs;
-        if (i > j) {
-          const int gb = rho - i;
-          As[rho * ld + j] = As[rho * ld + j] / As[(gb + j) * ld + j];
-        }
-      }
-      __syncwarp();
-      for (int s = 0; s < L.S; ++s) {
-        const int rho = lane + 32 * s;
-        if (rho >= L.U) continue;
-        const int i = rho % bs;
-        if (i > j) {
-          const int gb = rho - i;
-          const FT lij = As[rho * ld + j];
-          for (int k = j + 1; k <= i; ++k) As[rho * ld + k] = fma(-lij, As[(gb + k) * ld + j], As[rho * ld + k]);
-        }
-      }
-      __syncwarp();
-    }
-    // ---- X = L^{-1}: lane owns column c = its row index in the block
-    for (int s = 0; s < L.S; ++s) {
-      const int rho = lane + 32 * s;
-      if (rho >= L.U) continue;
-      const int c = rho % bs;
-      const int gb = rho - c;
-      for (int i = c; i < bs; ++i) {
-        FT acc = (i == c) ? FT(1) : FT(0);
-        for (int k = c; k < i; ++k) acc = fma(-As[(gb + i) * ld + k], Xs[(gb + k) * ld + c], acc);
-        Xs[(gb + i) * ld + c] = acc / As[(gb + i) * ld + i];
-      }
-    }
-    __syncwarp();
-    // ---- M^{-1} (circulant rows) and L^{-1} (by diagonals), coalesced unit stores
-    FT* Mu = Mo + u * uM;
-    FT* Lu = Lo + u * uL;
-    for (int s = 0; s < L.S; ++s) {
-      const int rho = lane + 32 * s;
-      const bool valid = rho < L.U;
-      const int i = valid ? rho % bs : 0;
-      const int gb = valid ? rho - i : 0;
-      for (int k = 0; k <= L.K; ++k) {
-        FT acc = FT(0);
-        if (valid) {
-          int j = i + k;
-          if (j >= bs) j -= bs;
-          const int m0 = i > j ? i : j;
-          for (int m = m0; m < bs; ++m) acc = fma(Xs[(gb + m) * ld + i], Xs[(gb + m) * ld + j], acc);
-        }
-        Mu[(k * L.S + s) * 32 + lane] = acc;
-      }
-      for (int k = 0; k < bs; ++k) {
-        const FT v = (valid && i >= k) ? Xs[rho * ld + (i - k)] : FT(0);
-        Lu[(k * L.S + s) * 32 + lane] = v;
-      }
-    }
-    __syncwarp();
-  }
+  for (int64_t u = (int64_t)blockIdx.x * nw + warp; u < L.n_units; u += (int64_t)gridDim.x * nw)
+    setup_unit<VT, FT>(L, u, a.row_ptr, a.col, va, a.tol, Mo + u * uM, Lo ? Lo + u * uL : nullptr, As, Xs, lane,
+                       a.failed);
 }
 
 // Dense copy of the diagonal blocks (bit-exact value copy; rows past n are zero).
