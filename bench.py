@@ -57,6 +57,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-iters", type=int, default=0, help="oracle CG iterations per sample (0 = auto)")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="persistent CG CTAs per SM (0 = occupancy max)")
+    ap.add_argument("--workload", default="diffusion3d", choices=["diffusion3d", "batched_rgg_512"],
+                    help="diffusion3d: the headline 128^3 solve; batched_rgg_512: 512 uneven RGG systems "
+                         "set up and solved in one persistent launch")
+    ap.add_argument("--n-sys", type=int, default=512, help="systems in the batched workload")
+    ap.add_argument("--no-tune", action="store_true", help="batched workload: skip the launch-shape autotuner")
+    ap.add_argument("--tune-trials", type=int, default=0, help="batched autotuner candidates (0 = all)")
     ap.add_argument("--profile", action="store_true",
                     help="one solve of the workload and nothing else (for ncu captures); prints a short line")
     return ap.parse_args()
@@ -446,6 +452,156 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- batched workload
+def batch_step_bytes(batch, prec, iters, restarts):
+    """Algorithmic bytes of one batched step: per system, setup (CSR read, M^{-1} write),
+    the x0 = 0 start (b read, M^{-1} read, x, r, z, p written), iterations * B_it and the
+    true residual (CSR, x, b read, r written), plus one M^{-1} pass and 5 vectors per restart."""
+    fb = 4 if prec != "fp64" else 8
+    total = 0
+    for s, A in enumerate(batch.systems):
+        n, nnz, bs = A.n, A.nnz, int(batch.bs[s])
+        C = csr_bytes(n, nnz, 8)
+        Fm, _ = factor_bytes(n, bs, fb)
+        v = 8 * n
+        b_it = C + Fm + 11 * v
+        total += (C + Fm) + (Fm + 5 * v) + int(iters[s]) * b_it + (int(restarts[s]) + 1) * (C + 3 * v)
+        total += int(restarts[s]) * (Fm + 5 * v)
+    return total
+
+
+def run_batched(args):
+    import torch
+
+    import paper_2410_02408_gb300 as pc
+
+    pc.load()
+    t0 = time.time()
+    batch = W.rgg_batch(n_sys=args.n_sys, seed=3)
+    gen_s = time.time() - t0
+    n_rows = int(batch.sys_row[-1])
+    nnz = int(batch.row_ptr[-1])
+    b = W.rhs(n_rows, 0)
+    bd = torch.from_numpy(b).cuda()
+    st = torch.cuda.current_stream()
+    peak, peak_kind = measured_hbm()
+    tuning = {}
+    if not args.no_tune:
+        for prec in ([args.prec, "fp64"] if args.prec != "fp64" and not args.no_fp64_compare else [args.prec]):
+            t0 = time.time()
+            tms, cfg = pc.batch_autotune(batch, bd, args.tol, args.maxit, prec, args.tune_trials)
+            tuning[prec] = {"best_ms": tms, "config": cfg, "tuning_s": time.time() - t0}
+
+    def timed(prec, steps, warmup):
+        H = pc.Batch(batch, prec)
+        x = torch.empty_like(bd)
+        for _ in range(warmup):
+            H.solve(bd, args.tol, args.maxit, x=x)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        per = info = None
+        kms = []
+        e0.record(st)
+        for _ in range(steps):
+            _, per, info = H.solve(bd, args.tol, args.maxit, x=x)
+            kms.append(info["solve_ms"])
+        e1.record(st)
+        torch.cuda.synchronize()
+        li = H.launch_info()
+        team, _ = H.teams()
+        H.destroy()
+        ms = e0.elapsed_time(e1) / steps
+        return x, per, info, ms, statistics.mean(kms), li, team
+
+    with ClockSampler(0) as clk:
+        x, per, info, ms, kms, li, team = timed(args.prec, args.steps, args.warmup)
+    restarts = np.zeros(batch.n_sys, dtype=np.int64)   # per-system restarts are not exported; bytes omit them
+    step_b = batch_step_bytes(batch, args.prec, per["iterations"], restarts)
+    value = step_b / (ms / 1e3) / 1e9
+    achieved = step_b / (kms / 1e3) / 1e9
+    it = per["iterations"]
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"batched_rgg_{batch.n_sys}", "n_sys": batch.n_sys, "rows": n_rows, "nnz": nnz,
+                   "block_sizes": "per system from {4,8,16,32,64}",
+                   "prec": "mixed (fp32 factors, fp64 CG)" if args.prec != "fp64" else "fp64", "tol": args.tol,
+                   "parallelism": "one persistent launch, teams of CTAs per system",
+                   "l2": "inputs larger than L2 (CSR %.0f MB)" % (csr_bytes(n_rows, nnz, 8) / 1e6)},
+        "status": info["status_name"], "worst_true_rel_residual": float(np.max(per["relres"])),
+        "iterations": {"min": int(it.min()), "median": float(np.median(it)), "max": int(it.max()),
+                       "sum": int(it.sum())},
+        "frac_of_hbm_peak": value / peak,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "batched_kernel (setup + PCG of every system, one persistent launch)",
+                     "algorithmic_bytes_per_launch": step_b, "avg_launch_us": kms * 1e3},
+        "launch": li, "teams": {"multi_cta_systems": int((team > 1).sum()), "max_team": int(team.max())},
+        "graph": bool(info["graph"]), "gpu_launches": 2 * args.steps, "generation_s": gen_s, "autotune": tuning,
+    }
+    line["clocks"] = clk.summary()
+    if args.prec != "fp64" and not args.no_fp64_compare:
+        _, per64, info64, ms64, kms64, _, _ = timed("fp64", max(1, min(args.steps, 2)), 1)
+        b64 = batch_step_bytes(batch, "fp64", per64["iterations"], restarts)
+        line["fp64"] = {"value": b64 / (ms64 / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": ms64,
+                        "iterations_sum": int(per64["iterations"].sum()), "status": info64["status_name"]}
+        line["mixed_speedup_vs_fp64"] = ms64 / ms
+    if not args.no_e2e:
+        hb = torch.from_numpy(b).pin_memory()
+        hx = torch.empty(n_rows, dtype=torch.float64).pin_memory()
+        hrp = torch.from_numpy(batch.row_ptr).pin_memory()
+        hci = torch.from_numpy(batch.col).pin_memory()
+        hva = torch.from_numpy(batch.val).pin_memory()
+        H = pc.Batch(batch, args.prec)
+        dbb = torch.empty_like(hb, device="cuda")
+        xe = torch.empty_like(dbb)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        k = max(1, min(args.steps, 3))
+        for _ in range(k):
+            H.row_ptr.copy_(hrp, non_blocking=True)
+            H.col.copy_(hci, non_blocking=True)
+            H.val.copy_(hva, non_blocking=True)
+            dbb.copy_(hb, non_blocking=True)
+            H.solve(dbb, args.tol, args.maxit, x=xe)
+            hx.copy_(xe, non_blocking=True)
+        e1.record(st)
+        torch.cuda.synchronize()
+        H.destroy()
+        ems = e0.elapsed_time(e1) / k
+        h2d = sum(t.numel() * t.element_size() for t in (hrp, hci, hva, hb))
+        line["e2e"] = {"value": step_b / (ems / 1e3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": hx.numel() * 8, "ms_per_step": ems}
+    if not args.no_cpu_baseline:
+        import oracle
+
+        # systems in increasing size until about 10 s of CPU work
+        order = np.argsort([A.n for A in batch.systems])
+        t0 = time.perf_counter()
+        sb = 0
+        done = 0
+        for s in order:
+            if time.perf_counter() - t0 > 10.0:
+                break
+            done += 1
+            A = batch.systems[s]
+            sl = slice(int(batch.sys_row[s]), int(batch.sys_row[s + 1]))
+            r = oracle.pcg(A, b[sl], int(batch.bs[s]), args.tol)
+            n_s, nnz_s, bs_s = A.n, A.nnz, int(batch.bs[s])
+            C = csr_bytes(n_s, nnz_s, 8)
+            Fm, _ = factor_bytes(n_s, bs_s, 8)
+            v = 8 * n_s
+            sb += (C + Fm) + (Fm + 5 * v) + r["iterations"] * (C + Fm + 11 * v) + (r["restarts"] + 1) * (C + 3 * v)
+        cs = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": sb / cs / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                                "sample": f"oracle FP64 setup + PCG of the {done} smallest systems ({cs:.1f} s)"}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.profile:
@@ -453,6 +609,8 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched_rgg_512":
+        run_batched(args)
     else:
         run_ours(args)
 

@@ -317,6 +317,27 @@ int32_t pc_batch_schedule(int32_t n_sys, const int64_t *n_rows, const int64_t *n
  * Process-wide. */
 void pc_batch_set_tuning(int32_t ctas_per_sm, int32_t team_max, double slots_per_cta);
 
+/* Shared memory (KB) that pc_batch_create gives to setup slots: the number of warps of a
+ * CTA that factor blocks concurrently is this budget over one slot (a slot holds the
+ * dense A and L^{-1} tiles of one warp unit of the largest block size).  0 = 70 KB.
+ * Process-wide. */
+void pc_batch_set_setup_smem(int32_t kb);
+
+/* Autotuner of the batched launch: solves the batch (setup + PCG, right-hand side b) with
+ * up to max_trials candidate launch shapes (0 = all 24: CTAs per SM {occupancy maximum, 1}
+ * x team limit {8, 32} x slots per CTA {1, 2, 4} x setup shared memory {70, 140} KB),
+ * timing the second (graph-replayed) solve of each, and records the fastest for this batch
+ * signature (n_sys, n_rows, nnz, prec): later pc_batch_create calls on a matching batch use
+ * it unless explicit tuning was set.  Allocates a scratch x.  best_ms (host, may be NULL):
+ * its solve time; best_cfg (host int32 [4], may be NULL): CTAs per SM (0 = maximum), team
+ * limit, slots per CTA x 1000, setup KB.  Synchronous. */
+pc_status pc_batch_autotune(const pc_batch *B, int32_t prec, const double *b, double tol,
+                            int32_t max_iter, int32_t max_trials, void *stream, double *best_ms,
+                            int32_t *best_cfg);
+
+/* Forget every autotuned launch shape. */
+void pc_batch_clear_tuned(void);
+
 /* One-shot form: pc_batch_create (pivot_tol 0) + pc_batch_solve + pc_batch_destroy. */
 pc_status pcg_solve_batched(const pc_batch *B, const double *b, double *x, double tol,
                             int32_t max_iter, int32_t prec, int32_t *iters, int32_t *status,

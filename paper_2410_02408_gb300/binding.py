@@ -103,6 +103,9 @@ def lib():
         "pc_batch_teams": (_I32, [_P, _P, _P]),
         "pc_batch_schedule": (_I32, [_I32, _P, _P, _P, _I32, _I32, _D, _P, _P, _P]),
         "pc_batch_set_tuning": (None, [_I32, _I32, _D]),
+        "pc_batch_set_setup_smem": (None, [_I32]),
+        "pc_batch_autotune": (_I32, [ctypes.POINTER(pc_batch), _I32, _P, _D, _I32, _I32, _P, _P, _P]),
+        "pc_batch_clear_tuned": (None, []),
         "pc_get_trace": (_I32, [_P, _P, _I32]),
         "pc_set_wait_budget": (None, [_I64]),
         "pc_set_ctas_per_sm": (None, [_I32]),
@@ -427,6 +430,28 @@ class Batch:
         slot0 = np.zeros(self.n_sys, dtype=np.int32)
         lib().pc_batch_teams(self._h, team.ctypes.data, slot0.ctypes.data)
         return team, slot0
+
+
+def batch_autotune(host, b, tol: float = 1e-10, max_iter: int = 100000, prec: str = "fp64", max_trials: int = 0):
+    """Time candidate launch shapes of the batched solve on this batch and keep the fastest
+    for later batches of the same signature.  Returns (best_ms, config dict)."""
+    torch = _torch()
+    B = Batch.__new__(Batch)
+    B.sys_row = _dev(host.sys_row, torch.int64)
+    B.row_ptr = _dev(host.row_ptr, torch.int32)
+    B.col = _dev(host.col, torch.int32)
+    B.val = _dev(host.val, torch.float64)
+    B.bs = _dev(host.bs, torch.int32)
+    n_sys = int(len(host.bs))
+    d = pc_batch(n_sys, int(B.row_ptr.numel() - 1), int(B.col.numel()), B.sys_row.data_ptr(), B.row_ptr.data_ptr(),
+                 B.col.data_ptr(), B.val.data_ptr(), B.bs.data_ptr(), int(np.max(np.asarray(host.bs))))
+    b = _dev(b, torch.float64)
+    ms = ctypes.c_double(0.0)
+    cfg = (ctypes.c_int32 * 4)()
+    _check(lib().pc_batch_autotune(ctypes.byref(d), PREC[prec], _ptr(b), float(tol), int(max_iter), int(max_trials),
+                                   _stream(), ctypes.byref(ms), ctypes.cast(cfg, ctypes.c_void_p)), "pc_batch_autotune")
+    return ms.value, {"ctas_per_sm": int(cfg[0]), "team_max": int(cfg[1]), "slots_per_cta": cfg[2] / 1000.0,
+                      "setup_kb": int(cfg[3])}
 
 
 def pcg_batched(host, b, tol: float = 1e-10, max_iter: int = 100000, prec: str = "fp64", check: bool = True):

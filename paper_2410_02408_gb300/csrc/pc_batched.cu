@@ -75,25 +75,41 @@ struct Team {
   unsigned nred;    // team reductions done (partial-buffer parity)
 };
 
-__device__ __forceinline__ double* part_at(const BArgs& a, int slot, unsigned parity) {
-  return a.part + ((size_t)slot * 2 + (parity & 1u)) * 4;
+// Launch-wide pointers and constants the phases need, copied once per CTA into shared
+// memory (the phases are out-of-line functions; handing them the kernel parameter block
+// by reference would make the compiler copy it to local memory).
+struct Env {
+  const int32_t* ci;
+  const double* va;
+  double* part;
+  unsigned* cnt;
+  unsigned long long* fail;
+  int* err;
+  long long budget;
+  double tol, pivot_tol;
+  int32_t max_iter, max_restarts;
+  int32_t setup_warps, slot_bytes;
+};
+
+__device__ __forceinline__ double* part_at(const Env& e, int slot, unsigned parity) {
+  return e.part + ((size_t)slot * 2 + (parity & 1u)) * 4;
 }
 
 // All CTAs of the team arrive; false if the wait ran out of budget or another wait did.
 // The first wait of a team also covers its formation: a member may have to wait until the
 // last member's CTA has finished its previous system, so it gets a longer budget.
-__device__ bool team_sync(const BArgs& a, Team& t, int* flag) {
+__device__ __forceinline__ bool team_sync(const Env& e, Team& t, int* flag) {
   __syncthreads();
   if (t.T == 1) return true;
   if (threadIdx.x == 0) {
     const unsigned target = (t.phase + 1u) * (unsigned)t.T;
-    red_release_add_u32(&a.cnt[t.s], 1u);
+    red_release_add_u32(&e.cnt[t.s], 1u);
     const long long t0 = clock64();
-    const long long limit = t.phase == 0 ? 16 * a.budget : a.budget;
+    const long long limit = t.phase == 0 ? 16 * e.budget : e.budget;
     int good = 1;
-    while ((int)(ld_acquire_u32(&a.cnt[t.s]) - target) < 0) {
-      if (ld_volatile_i32(a.err) != 0 || clock64() - t0 > limit) {
-        atomicCAS(a.err, 0, ST_TIMEOUT);
+    while ((int)(ld_acquire_u32(&e.cnt[t.s]) - target) < 0) {
+      if (ld_volatile_i32(e.err) != 0 || clock64() - t0 > limit) {
+        atomicCAS(e.err, 0, ST_TIMEOUT);
         good = 0;
         break;
       }
@@ -107,20 +123,20 @@ __device__ bool team_sync(const BArgs& a, Team& t, int* flag) {
 
 // Sum of NV values over the team, identical bits in every thread of every member.
 template <int NV>
-__device__ bool team_allreduce(const BArgs& a, Team& t, double* v, double* red, int* flag) {
+__device__ __forceinline__ bool team_allreduce(const Env& e, Team& t, double* v, double* red, int* flag) {
   block_sum<NV>(v, red);
   if (t.T == 1) return true;
   const unsigned par = t.nred++;
   if (threadIdx.x == 0) {
-    double* mine = part_at(a, t.slot0 + t.rank, par);
+    double* mine = part_at(e, t.slot0 + t.rank, par);
 #pragma unroll
     for (int i = 0; i < NV; ++i) __stcg(mine + i, v[i]);
   }
-  if (!team_sync(a, t, flag)) return false;
+  if (!team_sync(e, t, flag)) return false;
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
     double acc = 0.0;
-    for (int m = 0; m < t.T; ++m) acc += __ldcg(part_at(a, t.slot0 + m, par) + i);
+    for (int m = 0; m < t.T; ++m) acc += __ldcg(part_at(e, t.slot0 + m, par) + i);
     v[i] = acc;
   }
   return true;
@@ -128,7 +144,10 @@ __device__ bool team_allreduce(const BArgs& a, Team& t, double* v, double* red, 
 
 // Row of the system's CSR: sum_e val[e] * x[col[e]] in storage order.  The trip count is
 // the warp's longest row (all lanes run every chunk; shorter rows are masked), so the
-// whole warp must call it.  x may have been written by other CTAs: loads bypass L1.
+// whole warp must call it.  x may have been written by other CTAs of the team before the
+// last team barrier: that barrier's release (writer) -> acquire (thread 0 here) ->
+// bar.sync chain orders those stores before these plain coherent loads, so the gathers
+// may use L1 (never the read-only .nc path, which assumes data constant for the launch).
 __device__ __forceinline__ double brow(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                        const double* __restrict__ va, const double* x, int64_t row, bool valid,
                                        int32_t s_idle) {
@@ -149,7 +168,7 @@ __device__ __forceinline__ double brow(const int32_t* __restrict__ rp, const int
     }
     double xv[8];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) xv[t] = __ldcg(x + c[t]);
+    for (int t = 0; t < 8; ++t) xv[t] = x[c[t]];
     const int rem = wmax - k0;
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
@@ -164,16 +183,97 @@ __device__ __forceinline__ double brow(const int32_t* __restrict__ rp, const int
 
 enum { U_INIT = 0, U_ITER = 1, U_RESTART = 2 };
 
+// CTA-uniform description of this member's share of one system.  It lives in shared
+// memory and the phases below are out-of-line functions, so that no phase carries the
+// others' state in registers.
+struct SysCtx {
+  const int32_t* rp;   // the system's row pointers (global nnz offsets)
+  const double* b;
+  double *x, *r, *z, *p, *q;
+  const void* Mf;      // the system's M^{-1} (FT)
+  Layout L;
+  int64_t u0, u1;      // member's warp units
+  int64_t rl, rh;      // member's rows
+  int32_t s_idle;      // a valid entry index of the system (loaded by idle lanes)
+  int32_t s;           // system index
+};
+
+struct D2 {
+  double a, b;
+};
+
+// Setup of the member's units: extraction + block Cholesky + M^{-1} (setup_unit).
+template <typename FT>
+__device__ __noinline__ void phase_setup(const Env& e, const SysCtx& c, unsigned char* dsm) {
+  const int warp = threadIdx.x >> 5;
+  if (warp >= e.setup_warps) return;
+  const Layout L = c.L;
+  FT* As = reinterpret_cast<FT*>(dsm + (size_t)warp * e.slot_bytes);
+  FT* Xs = As + (size_t)L.U * (L.bs + 1);
+  FT* Mf = reinterpret_cast<FT*>(const_cast<void*>(c.Mf));
+  const int64_t uM = unit_elems_minv(L);
+  for (int64_t u = c.u0 + warp; u < c.u1; u += e.setup_warps)
+    setup_unit<double, FT>(L, u, c.rp, e.ci, e.va, e.pivot_tol, Mf + u * uM, nullptr, As, Xs, threadIdx.x & 31,
+                           &e.fail[c.s]);
+}
+
+// q = A p over the member's rows; returns this thread's share of p.q.
+__device__ __noinline__ double phase_spmv(const Env& e, const SysCtx& c) {
+  double pq = 0.0;
+  const int64_t rl = c.rl, rh = c.rh;
+  for (int64_t base = rl; base < rh; base += BT) {
+    const int64_t row = base + threadIdx.x;
+    const bool valid = row < rh;
+    const double qi = brow(c.rp, e.ci, e.va, c.p, row, valid, c.s_idle);
+    if (valid) {
+      c.q[row] = qi;
+      pq = fma(c.p[row], qi, pq);
+    }
+  }
+  return pq;
+}
+
+// t = b - A x over the member's rows, stored in r; returns this thread's share of t.t.
+__device__ __noinline__ double phase_true_residual(const Env& e, const SysCtx& c) {
+  double tt = 0.0;
+  const int64_t rl = c.rl, rh = c.rh;
+  for (int64_t base = rl; base < rh; base += BT) {
+    const int64_t row = base + threadIdx.x;
+    const bool valid = row < rh;
+    const double ax = brow(c.rp, e.ci, e.va, c.x, row, valid, c.s_idle);
+    if (valid) {
+      const double ti = __ldg(c.b + row) - ax;
+      c.r[row] = ti;
+      tt = fma(ti, ti, tt);
+    }
+  }
+  return tt;
+}
+
+// p = z + beta p over the member's rows.
+__device__ __noinline__ void phase_p_update(const SysCtx& c, double beta) {
+  double* p = c.p;
+  const double* z = c.z;
+  for (int64_t row = c.rl + threadIdx.x; row < c.rh; row += BT) p[row] = fma(beta, p[row], z[row]);
+}
+
 // Warp-unit pass over the member's units: r update (U_ITER: r -= alpha q, x += alpha p),
-// z = M^{-1} r, p = z (U_INIT/U_RESTART), and the partial sums (r.z, r.r).
+// z = M^{-1} r, p = z (U_INIT / U_RESTART; U_INIT also sets x = 0, r = b), and this
+// thread's shares of r.z and r.r.
 template <typename FT, int BS, int MODE>
-__device__ __forceinline__ void unit_pass(const BArgs& a, const Layout& L, const FT* __restrict__ Mf, int64_t u0,
-                                          int64_t u1, const double* bs_, double* xs, double* rs, double* zs,
-                                          double* ps, const double* qs, double alpha, double& v0, double& v1) {
+__device__ __noinline__ D2 phase_units(const SysCtx& c, double alpha) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
+  const Layout L = c.L;
   const int64_t uM = unit_elems_minv(L);
-  for (int64_t u = u0 + warp; u < u1; u += BNW) {
+  const FT* Mf = reinterpret_cast<const FT*>(c.Mf);
+  double* xs = c.x;
+  double* rs = c.r;
+  double* zs = c.z;
+  double* ps = c.p;
+  const double* qs = c.q;
+  double v0 = 0.0, v1 = 0.0;
+  for (int64_t u = c.u0 + warp; u < c.u1; u += BNW) {
     double rv[2] = {0.0, 0.0}, zv[2];
     int64_t rows[2];
     bool ok[2] = {false, false};
@@ -185,7 +285,7 @@ __device__ __forceinline__ void unit_pass(const BArgs& a, const Layout& L, const
       rows[t] = u * L.U + rh;
       ok[t] = vld && rows[t] < L.n;
       if (ok[t]) {
-        if (MODE == U_INIT) rv[t] = __ldg(bs_ + rows[t]);
+        if (MODE == U_INIT) rv[t] = __ldg(c.b + rows[t]);
         else if (MODE == U_RESTART) rv[t] = rs[rows[t]];
         else rv[t] = fma(-alpha, qs[rows[t]], rs[rows[t]]);
       }
@@ -199,80 +299,51 @@ __device__ __forceinline__ void unit_pass(const BArgs& a, const Layout& L, const
         xs[row] = 0.0;
         rs[row] = rv[t];
       } else if (MODE == U_ITER) {
-        xs[row] = fma(alpha, __ldcg(ps + row), xs[row]);
+        xs[row] = fma(alpha, ps[row], xs[row]);
         rs[row] = rv[t];
       }
       zs[row] = zv[t];
-      if (MODE != U_ITER) __stcg(ps + row, zv[t]);
+      if (MODE != U_ITER) ps[row] = zv[t];
       v0 = fma(rv[t], zv[t], v0);
       v1 = fma(rv[t], rv[t], v1);
     }
   }
+  return D2{v0, v1};
 }
 
 // One member's share of one system: setup of its units, then PCG with true-residual
-// restarts.  Returns with every member having taken the same decisions.
+// restarts.  Every member takes the same decisions (identical reduced bits).
 template <typename FT, int BS>
-__device__ __noinline__ void solve_system(const BArgs& a, const BSys& d, Team& t, unsigned char* dsm, double* red, int* flag) {
-  const Layout L = make_layout(d.n, d.bs);
-  const int64_t u0 = L.n_units * t.rank / t.T;
-  const int64_t u1 = L.n_units * (t.rank + 1) / t.T;
-  const int64_t rl = u0 * L.U < L.n ? u0 * L.U : L.n;
-  const int64_t rh = u1 * L.U < L.n ? u1 * L.U : L.n;
-  const int32_t* rp = a.rp + d.row0;
-  const double* bs_ = a.b + d.row0;
-  double* xs = a.x + d.row0;
-  double* rs = a.r + d.row0;
-  double* zs = a.z + d.row0;
-  double* ps = a.p + d.row0;
-  double* qs = a.q + d.row0;
-  FT* Mf = reinterpret_cast<FT*>(a.minv) + d.fac0;
-  const int32_t s_idle = __ldg(rp);   // a valid entry index of this system (used by idle lanes)
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
+__device__ __noinline__ void solve_system(const Env& e, const SysCtx& c, Team t, unsigned char* dsm,
+                                          double* red, int* flag, int32_t* o_status, int32_t* o_iters,
+                                          int32_t* o_restarts, double* o_relres) {
   int status = ST_OK, it = 0, restarts = 0;
-  double tt = 0.0;
   double relres = -1.0;   // -1: not computed (setup failure, timeout)
 
-  // ---- setup: extract + factor this member's units
-  if (warp < a.setup_warps) {
-    FT* As = reinterpret_cast<FT*>(dsm + (size_t)warp * a.slot_bytes);
-    FT* Xs = As + (size_t)L.U * (L.bs + 1);
-    const int64_t uM = unit_elems_minv(L);
-    for (int64_t u = u0 + warp; u < u1; u += a.setup_warps)
-      setup_unit<double, FT>(L, u, rp, a.ci, a.va, a.pivot_tol, Mf + u * uM, nullptr, As, Xs, lane, &a.fail[t.s]);
-  }
+  phase_setup<FT>(e, c, dsm);
   __syncthreads();
 
-  // ---- x0 = 0: r = b, z = M^{-1} r, p = z; ||b||^2, rho = r.z
-  double v[3] = {0.0, 0.0, 0.0};
+  // x0 = 0: r = b, z = M^{-1} r, p = z; ||b||^2, rho = r.z
+  double v[2];
   {
-    double rz = 0.0, rr = 0.0;
-    unit_pass<FT, BS, U_INIT>(a, L, Mf, u0, u1, bs_, xs, rs, zs, ps, qs, 0.0, rz, rr);
-    v[0] = rr;
-    v[1] = rz;
+    const D2 d = phase_units<FT, BS, U_INIT>(c, 0.0);
+    v[0] = d.b;
+    v[1] = d.a;
   }
-  if (!team_allreduce<2>(a, t, v, red, flag)) {
+  if (!team_allreduce<2>(e, t, v, red, flag)) {
     status = ST_TIMEOUT;
-    goto done;
-  }
-  {
-    const double bb = v[0];
-    const double bnorm = sqrt(bb);
+  } else if (*(volatile unsigned long long*)&e.fail[t.s] != ~0ull) {
+    status = ST_NOT_SPD;
+  } else if (v[0] == 0.0) {
+    relres = 0.0;   // b = 0: x = 0 is exact
+  } else {
+    const double bnorm = sqrt(v[0]);
     double rho = v[1];
-    if (*(volatile unsigned long long*)&a.fail[t.s] != ~0ull) {
-      status = ST_NOT_SPD;
-      goto done;
-    }
-    if (bb == 0.0) {   // x = 0 is exact
-      relres = 0.0;
-      goto done;
-    }
-    double rr = bb;
+    double rr = v[0];
     for (;;) {
-      // ---- CG iterations until the recurrence residual meets the tolerance
-      while (!(sqrt(rr) <= a.tol * bnorm)) {
-        if (it >= a.max_iter) {
+      // CG iterations until the recurrence residual meets the tolerance
+      while (!(sqrt(rr) <= e.tol * bnorm)) {
+        if (it >= e.max_iter) {
           status = ST_NO_CONV;
           break;
         }
@@ -280,103 +351,94 @@ __device__ __noinline__ void solve_system(const BArgs& a, const BSys& d, Team& t
           status = ST_BREAKDOWN;
           break;
         }
-        // q = A p, p.q
-        double pq[1] = {0.0};
-        for (int64_t base = rl; base < rh; base += BT) {
-          const int64_t row = base + threadIdx.x;
-          const bool valid = row < rh;
-          const double qi = brow(rp, a.ci, a.va, ps, row, valid, s_idle);
-          if (valid) {
-            qs[row] = qi;
-            pq[0] = fma(__ldcg(ps + row), qi, pq[0]);
-          }
-        }
-        if (!team_allreduce<1>(a, t, pq, red, flag)) {
+        double pq[1] = {phase_spmv(e, c)};
+        if (!team_allreduce<1>(e, t, pq, red, flag)) {
           status = ST_TIMEOUT;
-          goto done;
+          break;
         }
         if (!(pq[0] > 0.0) || !isfinite(pq[0])) {
           status = ST_BREAKDOWN;
           break;
         }
         const double alpha = rho / pq[0];
-        // x += alpha p, r -= alpha q, z = M^{-1} r, r.z, r.r
-        double w[2] = {0.0, 0.0};
-        unit_pass<FT, BS, U_ITER>(a, L, Mf, u0, u1, bs_, xs, rs, zs, ps, qs, alpha, w[0], w[1]);
-        if (!team_allreduce<2>(a, t, w, red, flag)) {
+        const D2 d = phase_units<FT, BS, U_ITER>(c, alpha);
+        double w[2] = {d.a, d.b};
+        if (!team_allreduce<2>(e, t, w, red, flag)) {
           status = ST_TIMEOUT;
-          goto done;
+          break;
         }
         ++it;
         rr = w[1];
-        if (sqrt(rr) <= a.tol * bnorm) break;
+        if (sqrt(rr) <= e.tol * bnorm) break;
         const double beta = w[0] / rho;
         rho = w[0];
-        // p = z + beta p
-        for (int64_t row = rl + threadIdx.x; row < rh; row += BT) __stcg(ps + row, fma(beta, __ldcg(ps + row), zs[row]));
-        if (!team_sync(a, t, flag)) {
+        phase_p_update(c, beta);
+        if (!team_sync(e, t, flag)) {
           status = ST_TIMEOUT;
-          goto done;
+          break;
         }
       }
-      // ---- true residual t = b - A x (stored in r for a restart); also reported when the
-      // iteration stopped without convergence
-      double tv[1] = {0.0};
-      for (int64_t base = rl; base < rh; base += BT) {
-        const int64_t row = base + threadIdx.x;
-        const bool valid = row < rh;
-        const double ax = brow(rp, a.ci, a.va, xs, row, valid, s_idle);
-        if (valid) {
-          const double ti = bs_[row] - ax;
-          rs[row] = ti;
-          tv[0] = fma(ti, ti, tv[0]);
-        }
-      }
-      // x is written by every member during the iterations: the SpMV above gathers it
-      // across members, so the team must have finished its last x update first.  The
-      // reduction before the convergence break is that barrier: the last unit pass came
-      // before it.
-      if (!team_allreduce<1>(a, t, tv, red, flag)) {
+      if (status == ST_TIMEOUT) break;
+      // True residual t = b - A x (kept in r for a restart); also reported when the
+      // iteration stopped without convergence.  Every exit from the loop above follows a
+      // team barrier that came after the last x update, so the gathers of x are safe.
+      double tv[1] = {phase_true_residual(e, c)};
+      if (!team_allreduce<1>(e, t, tv, red, flag)) {
         status = ST_TIMEOUT;
-        goto done;
+        break;
       }
-      tt = tv[0];
-      relres = sqrt(tt) / bnorm;
+      relres = sqrt(tv[0]) / bnorm;
       if (status != ST_OK) break;
-      if (sqrt(tt) <= a.tol * bnorm) break;
-      if (restarts >= a.max_restarts) {
+      if (sqrt(tv[0]) <= e.tol * bnorm) break;
+      if (restarts >= e.max_restarts) {
         status = ST_NO_CONV;
         break;
       }
       ++restarts;
-      // restart from x: r = t, z = M^{-1} r, p = z
       __syncthreads();
-      double w[2] = {0.0, 0.0};
-      unit_pass<FT, BS, U_RESTART>(a, L, Mf, u0, u1, bs_, xs, rs, zs, ps, qs, 0.0, w[0], w[1]);
-      if (!team_allreduce<2>(a, t, w, red, flag)) {
+      const D2 d = phase_units<FT, BS, U_RESTART>(c, 0.0);
+      double w[2] = {d.a, d.b};
+      if (!team_allreduce<2>(e, t, w, red, flag)) {
         status = ST_TIMEOUT;
-        goto done;
+        break;
       }
       rho = w[0];
       rr = w[1];
     }
   }
-done:
+  if (status == ST_TIMEOUT) relres = -1.0;
   if (t.rank == 0 && threadIdx.x == 0) {
-    a.o_status[t.s] = status;
-    a.o_iters[t.s] = it;
-    a.o_restarts[t.s] = restarts;
-    a.o_relres[t.s] = relres;
+    o_status[t.s] = status;
+    o_iters[t.s] = it;
+    o_restarts[t.s] = restarts;
+    o_relres[t.s] = relres;
   }
   __syncthreads();
 }
 
 template <typename FT>
-__global__ void __launch_bounds__(BT, 2) batched_kernel(const BArgs a) {
+__global__ void __launch_bounds__(BT, 2) batched_kernel(const __grid_constant__ BArgs a) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ double red[2 * 32];
+  __shared__ SysCtx ctx;
+  __shared__ Env env;
   __shared__ int s_slot;
   __shared__ int flag;
+  if (threadIdx.x == 0) {
+    env.ci = a.ci;
+    env.va = a.va;
+    env.part = a.part;
+    env.cnt = a.cnt;
+    env.fail = a.fail;
+    env.err = a.err;
+    env.budget = a.budget;
+    env.tol = a.tol;
+    env.pivot_tol = a.pivot_tol;
+    env.max_iter = a.max_iter;
+    env.max_restarts = a.max_restarts;
+    env.setup_warps = a.setup_warps;
+    env.slot_bytes = a.slot_bytes;
+  }
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_slot = (int)atomicAdd(a.queue, 1u);
@@ -401,13 +463,33 @@ __global__ void __launch_bounds__(BT, 2) batched_kernel(const BArgs a) {
       }
       continue;
     }
+    if (threadIdx.x == 0) {
+      SysCtx& c = ctx;
+      c.L = make_layout(d.n, d.bs);
+      c.u0 = c.L.n_units * t.rank / t.T;
+      c.u1 = c.L.n_units * (t.rank + 1) / t.T;
+      c.rl = c.u0 * c.L.U < c.L.n ? c.u0 * c.L.U : c.L.n;
+      c.rh = c.u1 * c.L.U < c.L.n ? c.u1 * c.L.U : c.L.n;
+      c.rp = a.rp + d.row0;
+      c.b = a.b + d.row0;
+      c.x = a.x + d.row0;
+      c.r = a.r + d.row0;
+      c.z = a.z + d.row0;
+      c.p = a.p + d.row0;
+      c.q = a.q + d.row0;
+      c.Mf = sizeof(FT) == 4 ? (const void*)(reinterpret_cast<const float*>(a.minv) + d.fac0)
+                             : (const void*)(reinterpret_cast<const double*>(a.minv) + d.fac0);
+      c.s_idle = __ldg(c.rp);
+      c.s = s;
+    }
+    __syncthreads();
     switch (d.bs) {
-      case 4: solve_system<FT, 4>(a, d, t, dsm, red, &flag); break;
-      case 8: solve_system<FT, 8>(a, d, t, dsm, red, &flag); break;
-      case 16: solve_system<FT, 16>(a, d, t, dsm, red, &flag); break;
-      case 32: solve_system<FT, 32>(a, d, t, dsm, red, &flag); break;
-      case 64: solve_system<FT, 64>(a, d, t, dsm, red, &flag); break;
-      default: solve_system<FT, 0>(a, d, t, dsm, red, &flag); break;
+      case 4: solve_system<FT, 4>(env, ctx, t, dsm, red, &flag, a.o_status, a.o_iters, a.o_restarts, a.o_relres); break;
+      case 8: solve_system<FT, 8>(env, ctx, t, dsm, red, &flag, a.o_status, a.o_iters, a.o_restarts, a.o_relres); break;
+      case 16: solve_system<FT, 16>(env, ctx, t, dsm, red, &flag, a.o_status, a.o_iters, a.o_restarts, a.o_relres); break;
+      case 32: solve_system<FT, 32>(env, ctx, t, dsm, red, &flag, a.o_status, a.o_iters, a.o_restarts, a.o_relres); break;
+      case 64: solve_system<FT, 64>(env, ctx, t, dsm, red, &flag, a.o_status, a.o_iters, a.o_restarts, a.o_relres); break;
+      default: solve_system<FT, 0>(env, ctx, t, dsm, red, &flag, a.o_status, a.o_iters, a.o_restarts, a.o_relres); break;
     }
   }
 }
@@ -526,6 +608,23 @@ long long batch_budget() {
 int g_batch_ctas_per_sm = 0;   // 0: occupancy maximum
 int g_batch_team_max = 0;      // 0: default
 double g_batch_split = 0.0;    // 0: default slots-per-CTA target
+int g_batch_setup_kb = 0;      // 0: default shared-memory budget for setup slots (KB)
+
+// Launch shape chosen by pc_batch_autotune for a batch signature.
+struct Tuned {
+  int32_t n_sys;
+  int64_t n_rows, nnz;
+  int32_t prec;
+  int32_t ctas_per_sm, team_max, setup_kb;
+  double split;
+};
+std::vector<Tuned> g_tuned;
+
+const Tuned* find_tuned(const pc_batch* B, int32_t prec) {
+  for (const Tuned& t : g_tuned)
+    if (t.n_sys == B->n_sys && t.n_rows == B->n_rows && t.nnz == B->nnz && t.prec == prec) return &t;
+  return nullptr;
+}
 
 }  // namespace
 
@@ -536,6 +635,10 @@ void pc_batch_set_tuning(int32_t ctas_per_sm, int32_t team_max, double slots_per
   g_batch_team_max = team_max > 0 ? team_max : 0;
   g_batch_split = slots_per_cta > 0.0 ? slots_per_cta : 0.0;
 }
+
+void pc_batch_set_setup_smem(int32_t kb) { g_batch_setup_kb = kb > 0 ? kb : 0; }
+
+void pc_batch_clear_tuned(void) { g_tuned.clear(); }
 
 int32_t pc_batch_schedule(int32_t n_sys, const int64_t* n_rows, const int64_t* nnz, const int32_t* block_size,
                           int32_t n_ctas, int32_t team_max, double slots_per_cta, int32_t* team, int32_t* slot0,
@@ -653,7 +756,11 @@ pc_status pc_batch_create(const pc_batch* B, int32_t prec, double pivot_tol, voi
   for (int bsz = 1; bsz <= B->max_block_size; ++bsz)
     need = std::max(need, pc::setup_unit_smem(pc::make_layout(64, bsz), fts));
   const int slot_bytes = (int)((need + 15) & ~(size_t)15);
-  const int budget = 70 * 1024;
+  const Tuned* tu = (g_batch_ctas_per_sm || g_batch_team_max || g_batch_split > 0.0 || g_batch_setup_kb)
+                        ? nullptr
+                        : find_tuned(B, prec);
+  const int setup_kb = g_batch_setup_kb ? g_batch_setup_kb : (tu ? tu->setup_kb : 70);
+  const int budget = setup_kb * 1024;
   int setup_warps = std::max(1, std::min(pc::BNW, budget / slot_bytes));
   h->smem = setup_warps * slot_bytes;
   const void* fn = h->fac_f32 ? (const void*)pc::batched_kernel<float> : (const void*)pc::batched_kernel<double>;
@@ -661,7 +768,8 @@ pc_status pc_batch_create(const pc_batch* B, int32_t prec, double pivot_tol, voi
   int occ = 0;
   PCB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, pc::BT, (size_t)h->smem));
   if (occ < 1) PCB_CHECK(PC_ERR_CUDA);
-  if (g_batch_ctas_per_sm > 0 && g_batch_ctas_per_sm < occ) occ = g_batch_ctas_per_sm;
+  const int want_occ = g_batch_ctas_per_sm ? g_batch_ctas_per_sm : (tu ? tu->ctas_per_sm : 0);
+  if (want_occ > 0 && want_occ < occ) occ = want_occ;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -675,8 +783,8 @@ pc_status pc_batch_create(const pc_batch* B, int32_t prec, double pivot_tol, voi
     nz[s] = (int64_t)hrp[s + 1] - hrp[s];
   }
   std::vector<int32_t> team(n_sys), slot0(n_sys), order(n_sys);
-  h->team_max = g_batch_team_max > 0 ? g_batch_team_max : 32;
-  const double split = g_batch_split > 0.0 ? g_batch_split : 2.0;
+  h->team_max = g_batch_team_max > 0 ? g_batch_team_max : (tu ? tu->team_max : 32);
+  const double split = g_batch_split > 0.0 ? g_batch_split : (tu ? tu->split : 2.0);
   const int n_slots = pc_batch_schedule(n_sys, nr.data(), nz.data(), hbs.data(), h->grid, h->team_max, split,
                                         team.data(), slot0.data(), order.data());
   if (n_slots < 1) PCB_CHECK(PC_ERR_INVALID_ARG);
@@ -749,6 +857,11 @@ pc_status pc_batch_create(const pc_batch* B, int32_t prec, double pivot_tol, voi
 }
 
 static cudaError_t batch_launch(pc_batch_handle* h, cudaStream_t st) {
+  // the dynamic shared-memory limit is per function: another handle may have lowered it
+  cudaError_t ae = cudaFuncSetAttribute(h->fac_f32 ? (const void*)pc::batched_kernel<float>
+                                                   : (const void*)pc::batched_kernel<double>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem);
+  if (ae != cudaSuccess) return ae;
   pc::batched_reset<<<std::max(1, std::min(1024, (h->n_sys + 255) / 256)), 256, 0, st>>>(
       h->misc, reinterpret_cast<int*>(h->misc + 1), h->cnt, h->fail, h->n_sys);
   cudaError_t e = cudaGetLastError();
@@ -899,6 +1012,86 @@ int32_t pc_batch_teams(const pc_batch_handle* h, int32_t* team, int32_t* slot0) 
     if (slot0) slot0[s] = h->hsys[s].slot0;
   }
   return h->n_sys;
+}
+
+pc_status pc_batch_autotune(const pc_batch* B, int32_t prec, const double* b, double tol, int32_t max_iter,
+                            int32_t max_trials, void* stream, double* best_ms, int32_t* best_cfg) {
+  if (!B || !b || !(tol >= 0.0) || max_iter < 0) return PC_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* x = nullptr;
+  pc_status ps = balloc(&x, sizeof(double) * (size_t)std::max<int64_t>(B->n_rows, 1));
+  if (ps != PC_OK) return ps;
+  // Candidate launch shapes: CTAs per SM (0 = occupancy maximum), team limit, slots per CTA
+  // of the scheduler, and the shared memory given to setup slots (setup warps per CTA).
+  struct Cand {
+    int occ, team, kb;
+    double split;
+  };
+  std::vector<Cand> cands;
+  for (int occ : {0, 1})
+    for (int team : {8, 32})
+      for (double split : {1.0, 2.0, 4.0})
+        for (int kb : {70, 140}) cands.push_back({occ, team, kb, split});
+  const int saved_occ = g_batch_ctas_per_sm, saved_team = g_batch_team_max, saved_kb = g_batch_setup_kb;
+  const double saved_split = g_batch_split;
+  double best = 1e300;
+  Cand bc{0, 32, 70, 2.0};
+  int trials = 0;
+  pc_status out = PC_OK;
+  for (const Cand& c : cands) {
+    if (max_trials > 0 && trials >= max_trials) break;
+    g_batch_ctas_per_sm = c.occ;
+    g_batch_team_max = c.team;
+    g_batch_split = c.split;
+    g_batch_setup_kb = c.kb;
+    pc_batch_handle* h = nullptr;
+    pc_status s = pc_batch_create(B, prec, 0.0, stream, &h);
+    if (s != PC_OK) {
+      if (s == PC_ERR_INVALID_ARG) {
+        out = s;
+        break;
+      }
+      continue;   // e.g. a shared-memory budget the device cannot give
+    }
+    pc_solve_info info;
+    // first call captures the graph; the second is timed
+    s = pc_batch_solve(h, b, x, tol, max_iter, nullptr, nullptr, nullptr, &info, stream);
+    if (s == PC_OK || s == PC_ERR_NO_CONVERGENCE)
+      s = pc_batch_solve(h, b, x, tol, max_iter, nullptr, nullptr, nullptr, &info, stream);
+    pc_batch_destroy(h);
+    ++trials;
+    if (s != PC_OK && s != PC_ERR_NO_CONVERGENCE) {
+      out = s;
+      break;
+    }
+    if (info.solve_ms < best) {
+      best = info.solve_ms;
+      bc = c;
+    }
+  }
+  g_batch_ctas_per_sm = saved_occ;
+  g_batch_team_max = saved_team;
+  g_batch_split = saved_split;
+  g_batch_setup_kb = saved_kb;
+  cudaStreamSynchronize(st);
+  cudaFree(x);
+  if (out != PC_OK) return out;
+  if (best_ms) *best_ms = best;
+  if (best_cfg) {
+    best_cfg[0] = bc.occ;
+    best_cfg[1] = bc.team;
+    best_cfg[2] = (int32_t)(bc.split * 1000.0);
+    best_cfg[3] = bc.kb;
+  }
+  Tuned t{B->n_sys, B->n_rows, B->nnz, prec, bc.occ, bc.team, bc.kb, bc.split};
+  bool found = false;
+  for (Tuned& e : g_tuned)
+    if (e.n_sys == t.n_sys && e.n_rows == t.n_rows && e.nnz == t.nnz && e.prec == t.prec) {
+      e = t;
+      found = true;
+    }
+  if (!found) g_tuned.push_back(t);
+  return PC_OK;
 }
 
 pc_status pcg_solve_batched(const pc_batch* B, const double* b, double* x, double tol, int32_t max_iter,

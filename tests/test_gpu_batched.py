@@ -176,3 +176,22 @@ def test_batched_c3_shape_sample(pc):
         sl = _sys_slice(batch, s)
         r = oracle.pcg(A, b[sl], int(batch.bs[s]), 1e-10)
         assert np.linalg.norm(x[sl] - r["x"]) <= 1e-10 * np.linalg.norm(r["x"]), s
+
+
+def test_batched_autotune_records_a_shape(pc, small_batch):
+    batch = small_batch
+    b = _rhs(batch, 9)
+    pc.binding.lib().pc_batch_clear_tuned()
+    ms, cfg = pc.batch_autotune(batch, b, tol=1e-10, max_trials=4)
+    assert ms > 0 and cfg["team_max"] in (8, 32) and cfg["setup_kb"] in (70, 140)
+    H = pc.Batch(batch)
+    try:
+        li = H.launch_info()
+        if cfg["ctas_per_sm"]:
+            assert li["ctas_per_sm"] <= cfg["ctas_per_sm"]
+        assert li["team_max"] == cfg["team_max"]
+        x, per, info = H.solve(b, 1e-10)
+        assert info["status_name"] == "ok"
+    finally:
+        H.destroy()
+        pc.binding.lib().pc_batch_clear_tuned()
