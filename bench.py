@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=128, help="grid points per axis")
     ap.add_argument("--sigma", type=float, default=2.0)
-    ap.add_argument("--bs", type=int, default=16)
+    ap.add_argument("--bs", type=int, default=None, help="block size (default 16; 32 for powerlaw_8m)")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "tf32"])
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--maxit", type=int, default=200000)
@@ -57,15 +57,24 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-iters", type=int, default=0, help="oracle CG iterations per sample (0 = auto)")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="persistent CG CTAs per SM (0 = occupancy max)")
-    ap.add_argument("--workload", default="diffusion3d", choices=["diffusion3d", "batched_rgg_512"],
+    ap.add_argument("--workload", default="diffusion3d", choices=["diffusion3d", "batched_rgg_512", "powerlaw_8m"],
                     help="diffusion3d: the headline 128^3 solve; batched_rgg_512: 512 uneven RGG systems "
-                         "set up and solved in one persistent launch")
+                         "set up and solved in one persistent launch; powerlaw_8m: random SPD with power-law "
+                         "rows (N = 8M, ~256M nnz, FP32 values, bs 32)")
+    ap.add_argument("--pl-n", type=int, default=8_000_000, help="rows of the power-law workload")
+    ap.add_argument("--no-kappa", action="store_true", help="skip the Lanczos kappa timing")
+    ap.add_argument("--row-binning", default="auto", choices=["auto", "on", "off"],
+                    help="row order of the CG SpMV (auto: binned by length when rows are irregular)")
     ap.add_argument("--n-sys", type=int, default=512, help="systems in the batched workload")
     ap.add_argument("--no-tune", action="store_true", help="batched workload: skip the launch-shape autotuner")
     ap.add_argument("--tune-trials", type=int, default=0, help="batched autotuner candidates (0 = all)")
     ap.add_argument("--profile", action="store_true",
                     help="one solve of the workload and nothing else (for ncu captures); prints a short line")
-    return ap.parse_args()
+    args = ap.parse_args()
+    args.bs_given = args.bs is not None
+    if args.bs is None:
+        args.bs = 16
+    return args
 
 
 def run_profile(args):
@@ -75,14 +84,15 @@ def run_profile(args):
     import paper_2410_02408_gb300 as pc
 
     pc.load()
+    pc.set_row_binning(args.row_binning)
     if args.ctas_per_sm:
         pc.set_ctas_per_sm(args.ctas_per_sm)
-    A = W.diffusion3d(args.n, args.sigma)
+    A, _, bs = single_workload(args)
     b = torch.from_numpy(W.rhs(A.n, 0)).cuda()
     Ad = pc.csr(A)
-    x, info = pc.pcg(Ad, b, args.bs, tol=args.tol, max_iter=args.maxit, prec=args.prec, check=False)
+    x, info = pc.pcg(Ad, b, bs, tol=args.tol, max_iter=args.maxit, prec=args.prec, check=False)
     torch.cuda.synchronize()
-    print(json.dumps({"profile": True, "n": A.n, "bs": args.bs, "prec": args.prec, "iterations": info["iterations"],
+    print(json.dumps({"profile": True, "n": A.n, "bs": bs, "prec": args.prec, "iterations": info["iterations"],
                       "status": info["status"], "solve_ms": info["solve_ms"], "setup_ms": info["setup_ms"],
                       "grid_ctas": info["grid_ctas"]}))
 
@@ -211,6 +221,15 @@ def profiled_traffic(bs, prec):
     return float(m.group(1)) if m else None
 
 
+def single_workload(args):
+    """The single-system workload: (host CSR, name, block size)."""
+    if args.workload == "powerlaw_8m":
+        A = W.powerlaw_spd(args.pl_n, seed=5)
+        return A, f"powerlaw_{args.pl_n}_fp32vals", (args.bs if args.bs_given else 32)
+    A = W.diffusion3d(args.n, args.sigma)
+    return A, f"diffusion3d_{args.n}_sigma{args.sigma:g}", args.bs
+
+
 # ---------------------------------------------------------------- distributed plumbing
 def dist_init():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -260,7 +279,8 @@ def run_reference(args):
     rank, ws, dist = dist_init()
     if rank != 0:
         return
-    A = W.diffusion3d(args.n, args.sigma)
+    A, wname, bs = single_workload(args)
+    args.bs = bs
     b = W.rhs(A.n, 0)
     iters = args.cpu_sample_iters or 8
     vals = []
@@ -273,13 +293,45 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"diffusion3d_{args.n}_sigma{args.sigma:g}", "n": A.n, "nnz": A.nnz,
+        "config": {"workload": wname, "n": A.n, "nnz": A.nnz,
                    "block_size": args.bs, "prec": "fp64"},
         "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
                          "sample": f"oracle setup + {iters} CG iterations on the full matrix per step"},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
+
+
+def kappa_timing(pc, Ad, bd, bs, n, nnz, vb, steps=200):
+    """Lanczos kappa before (A) and after (L^{-1} A L^{-T}) with CGS2, timed with CUDA events.
+    Algorithmic bytes of step j (0-based): the operator (CSR + 2 vectors; after: + L^{-1}
+    twice and 4 more vectors) plus three passes over the j+1 basis vectors (two Gram-Schmidt
+    projections and the update) and the new vector."""
+    import torch
+
+    out = {}
+    st = torch.cuda.current_stream()
+    for name, h_bs in (("before", 0), ("after", bs)):
+        H = pc.setup(Ad, h_bs, prec="fp64") if h_bs else None
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        r = H.kappa(bd, max_steps=steps) if H else pc.kappa(Ad, bd, 0, max_steps=steps)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if H:
+            H.destroy()
+        m = r["steps"]
+        op = csr_bytes(n, nnz, vb) + 16 * n
+        if h_bs:
+            op += 2 * factor_bytes(n, h_bs, 8)[1] + 32 * n
+        byt = sum(op + 3 * (j + 1) * 8 * n + 8 * n for j in range(m))
+        out[name] = {"kappa": r["kappa"], "lambda_min": r["lambda_min"], "lambda_max": r["lambda_max"],
+                     "steps": m, "ms": ms, "GBs": byt / (ms / 1e3) / 1e9}
+    out["note"] = "200-step Lanczos with CGS2 (FP64 factors for 'after'); bytes include the basis passes"
+    return out
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -292,9 +344,12 @@ def run_ours(args):
     import paper_2410_02408_gb300 as pc
 
     pc.load()
+    pc.set_row_binning(args.row_binning)
     if args.ctas_per_sm:
         pc.set_ctas_per_sm(args.ctas_per_sm)
-    A = W.diffusion3d(args.n, args.sigma)
+    A, wname, bs = single_workload(args)
+    args.bs = bs
+    vb = A.val.dtype.itemsize
     b = W.rhs(A.n, 0)
     Ad = pc.csr(A)
     bd = torch.from_numpy(b).cuda()
@@ -328,12 +383,12 @@ def run_ours(args):
     iters = infos[-1]["iterations"]
     total_bytes = 0
     for inf in infos:
-        sb, b_it, kb = step_bytes(n, nnz, args.bs, args.prec, inf["iterations"])
+        sb, b_it, kb = step_bytes(n, nnz, args.bs, args.prec, inf["iterations"], vb)
         total_bytes += sb
     value = total_bytes * ws / (ms_total / 1e3) / 1e9
     solve_ms = statistics.mean(i["solve_ms"] for i in infos)
     peak, peak_kind = measured_hbm()
-    _, b_it, _ = step_bytes(n, nnz, args.bs, args.prec, iters)
+    _, b_it, _ = step_bytes(n, nnz, args.bs, args.prec, iters, vb)
     # Per-kernel times: one extra (untimed) solve in profiling mode, where the loop-body
     # kernels are launched one by one with CUDA events around each on the current stream.
     os.environ["PC_CG_PROFILE"] = "1"
@@ -344,12 +399,12 @@ def run_ours(args):
     del os.environ["PC_CG_PROFILE"]
     spmv_us, prec_us, upd_us = (float(kt[0]) / 1e3, float(kt[1]) / 1e3, float(kt[2]) / 1e3) if len(kt) >= 3 else (0.0, 0.0, 0.0)
     fb = 4 if args.prec != "fp64" else 8
-    spmv_bytes = csr_bytes(n, nnz, 8) + 2 * 8 * n                       # CSR, p (read once), q
+    spmv_bytes = csr_bytes(n, nnz, vb) + 2 * 8 * n                      # CSR, p (read once), q
     prec_bytes = factor_bytes(n, args.bs, fb)[0] + 4 * 8 * n              # M^{-1}, r, q in; r, z out
     upd_bytes = 5 * 8 * n                                                 # x, p, z in; x, p out
     # dominant kernel (largest share of the iteration): the SpMV q = A p with the p.q reduction
     achieved = spmv_bytes / (spmv_us * 1e-6) / 1e9 if spmv_us > 0 else 0.0
-    traffic = profiled_traffic(args.bs, args.prec)
+    traffic = profiled_traffic(args.bs, args.prec) if args.workload == "diffusion3d" else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind,
                 "kernel": "cg_spmv_kernel (q = A p and p.q; one launch per CG iteration)",
@@ -371,10 +426,11 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"diffusion3d_{args.n}_sigma{args.sigma:g}", "n": n, "nnz": nnz,
+        "config": {"workload": wname, "n": n, "nnz": nnz,
                    "block_size": args.bs, "prec": "mixed (fp32 factors, fp64 CG)" if args.prec != "fp64" else "fp64",
+                   "csr_values": "fp32" if vb == 4 else "fp64",
                    "tol": args.tol, "parallelism": f"replicas x{ws}",
-                   "l2": "inputs larger than L2 (CSR %.0f MB + factor)" % (csr_bytes(n, nnz, 8) / 1e6)},
+                   "l2": "inputs larger than L2 (CSR %.0f MB + factor)" % (csr_bytes(n, nnz, vb) / 1e6)},
         "iterations": iters, "true_rel_residual": true_res,
         "setup_ms": statistics.mean(i["setup_ms"] for i in infos), "solve_ms": solve_ms,
         "us_per_iteration": 1000.0 * solve_ms / max(iters, 1), "algorithmic_bytes_per_iteration": b_it,
@@ -400,11 +456,14 @@ def run_ours(args):
         t1.record(st)
         torch.cuda.synchronize()
         fms = t0.elapsed_time(t1) / reps
-        fb = sum(step_bytes(n, nnz, args.bs, "fp64", fi["iterations"])[0] for fi in finf) / reps
+        fb = sum(step_bytes(n, nnz, args.bs, "fp64", fi["iterations"], vb)[0] for fi in finf) / reps
         line["fp64"] = {"value": fb / (fms / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": fms,
                         "iterations": finf[-1]["iterations"], "solve_ms": finf[-1]["solve_ms"],
                         "setup_ms": finf[-1]["setup_ms"]}
         line["mixed_speedup_vs_fp64"] = fms / ms_step
+
+    if rank == 0 and not args.no_kappa:
+        line["kappa"] = kappa_timing(pc, Ad, bd, args.bs, n, nnz, vb)
 
     if not args.no_e2e:
         # end to end through the C ABI from pinned host buffers
@@ -433,7 +492,7 @@ def run_ours(args):
             db.copy_(hb, non_blocking=True)
             xd, ei = pc.pcg(pc.CSR(drp, dci, dva), db, args.bs, tol=args.tol, max_iter=args.maxit, prec=args.prec)
             hx.copy_(xd, non_blocking=True)
-            eb += step_bytes(n, nnz, args.bs, args.prec, ei["iterations"])[0]
+            eb += step_bytes(n, nnz, args.bs, args.prec, ei["iterations"], vb)[0]
         t1.record(st)
         torch.cuda.synchronize()
         ems = max_over_ranks(t0.elapsed_time(t1), dist)

@@ -360,6 +360,18 @@ void pc_set_ctas_per_sm(int32_t ctas);
  * (or the PC_CG_ENGINE environment variable: "graph" / "persistent"). */
 void pc_set_cg_engine(int32_t engine);
 
+/* Row order of the graph engine's CG SpMV (one row per lane, every lane running to the
+ * longest row of its warp).  Mode -1 (default): on the first solve of a handle, measure the
+ * FP64 operations that order would spend (sum over 32-row groups of 32 x the longest row)
+ * and, if they exceed 1.25 x nnz (irregular row lengths, e.g. power-law rows), sort the rows
+ * by length inside windows of 2048 rows (a stable, deterministic counting sort; 4 bytes per
+ * row of workspace).  0: natural order always; 1: binned always.  Applies to handles that
+ * have not solved yet.  Process-wide. */
+void pc_set_row_binning(int32_t mode);
+
+/* 1 if the handle's CG SpMV uses the binned row order, else 0. */
+int32_t pc_handle_row_binned(const pc_handle *h);
+
 /* Phase trace of the last pcg_solve_h on h, when the environment variable
  * PC_TRACE_BARRIERS=N (N > 0) was set for that solve: out[0] is the device globaltimer (ns)
  * at kernel start and out[k] the time after the k-th grid-wide synchronisation (entries

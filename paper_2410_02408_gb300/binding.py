@@ -110,6 +110,8 @@ def lib():
         "pc_set_wait_budget": (None, [_I64]),
         "pc_set_ctas_per_sm": (None, [_I32]),
         "pc_set_cg_engine": (None, [_I32]),
+        "pc_set_row_binning": (None, [_I32]),
+        "pc_handle_row_binned": (_I32, [_P]),
         "pc_status_string": (ctypes.c_char_p, [_I32]),
         "pc_version": (_I32, []),
     }
@@ -248,6 +250,10 @@ class Handle:
 
     def kappa(self, v0, max_steps: int = 200, tol: float = 1e-12, reorth: bool = True):
         return _kappa(self._h, self.A, v0, max_steps, tol, reorth)
+
+    def row_binned(self) -> bool:
+        """True if this handle's CG SpMV runs rows binned by length."""
+        return bool(lib().pc_handle_row_binned(self._h))
 
     def trace(self, max_entries: int = 4096) -> np.ndarray:
         """Barrier timestamps (ns) of the last solve when PC_TRACE_BARRIERS was set."""
@@ -490,6 +496,11 @@ def set_wait_budget(cycles: int):
 
 def set_ctas_per_sm(ctas: int):
     lib().pc_set_ctas_per_sm(int(ctas))
+
+
+def set_row_binning(mode: str):
+    """"auto" (default), "off" or "on": row order of the CG SpMV (see pc_set_row_binning)."""
+    lib().pc_set_row_binning({"off": 0, "on": 1}.get(mode, -1))
 
 
 def set_cg_engine(engine: str):

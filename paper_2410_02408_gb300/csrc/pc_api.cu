@@ -38,6 +38,9 @@ struct pc_handle {
   // graph engine
   void* graph;           // instantiated loop graph (pc::cg_graph_create)
   double* gbx;           // copies of b and x: 2 n
+  int32_t* perm;         // SpMV row order for irregular row lengths (null: natural order)
+  int32_t* gsplit;       // with perm: each SpMV warp's first 32-row group (balanced runs)
+  int perm_checked;      // the row-length statistics have been taken
   double* gpart;         // per-CTA partials
   void* gscal;           // CG scalars
   int64_t prof_ns[3];    // graph engine, profiling mode: mean ns per iteration of the 3 kernels
@@ -49,6 +52,7 @@ namespace {
 long long g_budget = 0;          // 0 = default
 int g_ctas_per_sm = 0;           // 0 = occupancy maximum
 int g_engine = -1;               // -1: from PC_CG_ENGINE (default graph); 0 graph; 1 persistent
+int g_row_binning = -1;          // -1: decided per matrix; 0 off; 1 on
 
 int cg_engine() {
   if (g_engine >= 0) return g_engine;
@@ -128,6 +132,10 @@ void pc_set_ctas_per_sm(int32_t ctas) { g_ctas_per_sm = ctas > 0 ? ctas : 0; }
 
 void pc_set_cg_engine(int32_t engine) { g_engine = (engine == 0 || engine == 1) ? engine : -1; }
 
+void pc_set_row_binning(int32_t mode) { g_row_binning = (mode == 0 || mode == 1) ? mode : -1; }
+
+int32_t pc_handle_row_binned(const pc_handle* h) { return h && h->perm ? 1 : 0; }
+
 const char* pc_status_string(int32_t s) {
   switch (s) {
     case PC_OK: return "ok";
@@ -156,6 +164,8 @@ pc_status pc_destroy(pc_handle* h) {
   dfree(h->trace_d);
   if (h->graph) pc::cg_graph_destroy(h->graph);
   dfree(h->gbx);
+  dfree(h->perm);
+  dfree(h->gsplit);
   dfree(h->gpart);
   dfree(h->gscal);
   delete h;
@@ -335,6 +345,36 @@ static pc_status ensure_cg_workspace(pc_handle* h, cudaStream_t st) {
 }
 
 // Graph engine: the CG loop is a CUDA graph `while` node over three kernels (pc_cg_graph.cu).
+// Row order of the graph engine's SpMV: rows are binned by length (pc_rowbin.cu) when the
+// natural order would make the warp-uniform SpMV spend more than 1.25x the FP64 operations
+// of the stored entries.  g_row_binning: -1 decide, 0 never, 1 always.
+static pc_status choose_row_order(pc_handle* h, cudaStream_t st) {
+  h->perm_checked = 1;
+  const int64_t n = h->A.n;
+  bool bin = g_row_binning == 1;
+  if (g_row_binning < 0) {
+    unsigned long long* d = reinterpret_cast<unsigned long long*>(h->tmp);   // n >= 1 doubles
+    unsigned long long waste = 0;
+    PC_TRY(cudaMemsetAsync(d, 0, sizeof(waste), st));
+    PC_TRY(pc::row_bin_waste(n, h->A.row_ptr, d, st));
+    PC_TRY(cudaMemcpyAsync(&waste, d, sizeof(waste), cudaMemcpyDeviceToHost, st));
+    PC_TRY(cudaStreamSynchronize(st));
+    bin = (double)waste > 1.25 * (double)h->A.nnz;
+  }
+  if (!bin) return PC_OK;
+  const int items = pc::cg_spmv_bin_warps();
+  pc_status s = dalloc(&h->perm, sizeof(int32_t) * (size_t)n);
+  if (s == PC_OK) s = dalloc(&h->gsplit, sizeof(int32_t) * (size_t)(items + 1));
+  if (s != PC_OK) {
+    dfree(h->perm);
+    h->perm = nullptr;
+    return s;
+  }
+  PC_TRY(pc::row_bin_build(n, h->A.row_ptr, h->perm, st));
+  PC_TRY(pc::row_bin_split(n, h->A.row_ptr, h->perm, items, h->gsplit, reinterpret_cast<int64_t*>(h->tmp), st));
+  return PC_OK;
+}
+
 static pc_status pcg_solve_graph(pc_handle* h, const double* b, double* x, double tol, int32_t max_iter,
                                  pc_solve_info* info, cudaStream_t st) {
   const int64_t n = h->A.n;
@@ -345,9 +385,13 @@ static pc_status pcg_solve_graph(pc_handle* h, const double* b, double* x, doubl
   if (s == PC_OK && !h->gscal) s = dalloc(&h->gscal, pc::cg_scalars_bytes());
   if (s != PC_OK) return s;
   if (!h->graph) {
+    if (!h->perm_checked) {
+      s = choose_row_order(h, st);
+      if (s != PC_OK) return s;
+    }
     PC_TRY(pc::cg_graph_create(&h->graph, h->L, h->A.row_ptr, h->A.col_idx, h->A.val, h->val_f32, h->minv,
                                h->fac_f32, h->gbx, h->gbx + n, h->cg, h->cg + n, h->cg + 2 * n, h->cg + 3 * n,
-                               h->gpart, h->gscal, st));
+                               h->gpart, h->gscal, h->perm, h->gsplit, st));
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   PC_TRY(cudaEventCreate(&e0));

@@ -77,20 +77,16 @@ __device__ __forceinline__ bool cg_last_cta(double* v, double* part, unsigned* c
 // only if some lane needs it (a fully masked FP64 instruction still costs FP64-pipe time),
 // and float values are widened on the integer pipe.
 template <typename VT>
-__device__ __forceinline__ double cg_row(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                         const VT* __restrict__ va, const double* __restrict__ x, int64_t row,
-                                         bool valid) {
-  const int32_t s = valid ? __ldg(rp + row) : 0;
-  const int32_t e = valid ? __ldg(rp + row + 1) : 0;
-  const int32_t cnt = e - s;
-  const int32_t wmax = __reduce_max_sync(FULL, cnt);
+__device__ __forceinline__ double cg_row_range(const int32_t* __restrict__ ci, const VT* __restrict__ va,
+                                               const double* __restrict__ x, int32_t s, int32_t cnt, int32_t wmax) {
+  const int32_t s0 = cnt > 0 ? s : 0;   // an empty row loads (and ignores) entry 0, which exists when wmax > 0
   double acc = 0.0;
   for (int32_t k0 = 0; k0 < wmax; k0 += 8) {
     int32_t c[8];
     VT v[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
-      const int32_t k = s + min(k0 + t, max(cnt, 1) - 1);
+      const int32_t k = s0 + min(k0 + t, max(cnt, 1) - 1);
       c[t] = __ldg(ci + k);
       v[t] = __ldg(va + k);
     }
@@ -109,6 +105,52 @@ __device__ __forceinline__ double cg_row(const int32_t* __restrict__ rp, const i
   return acc;
 }
 
+template <typename VT>
+__device__ __forceinline__ double cg_row(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                         const VT* __restrict__ va, const double* __restrict__ x, int64_t row,
+                                         bool valid) {
+  const int32_t s = valid ? __ldg(rp + row) : 0;
+  const int32_t e = valid ? __ldg(rp + row + 1) : 0;
+  const int32_t cnt = e - s;
+  return cg_row_range<VT>(ci, va, x, s, cnt, __reduce_max_sync(FULL, cnt));
+}
+
+// One row per group of LPR lanes: lane j of the group takes entries j, j+LPR, ... (coalesced
+// across the group), 8 per round, and the group's partial sums are added by an xor tree;
+// the sum is valid in every lane of the group.  gmax = the longest row of the pass
+// (warp-uniform).  Called by full warps.
+template <typename VT, int LPR>
+__device__ __forceinline__ double cg_row_lanes(const int32_t* __restrict__ ci, const VT* __restrict__ va,
+                                               const double* __restrict__ x, int32_t s, int32_t cnt,
+                                               int32_t gmax) {
+  const int j = threadIdx.x & (LPR - 1);
+  const int32_t s0 = cnt > 0 ? s : 0;
+  double acc = 0.0;
+  for (int32_t k0 = 0; k0 < gmax; k0 += 8 * LPR) {
+    int32_t c[8];
+    VT v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int32_t k = s0 + min(k0 + t * LPR + j, max(cnt, 1) - 1);
+      c[t] = __ldg(ci + k);
+      v[t] = __ldg(va + k);
+    }
+    double xv[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) xv[t] = __ldg(x + c[t]);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      if (k0 + t * LPR < gmax) {   // warp-uniform
+        const double pr = fma(from_ft(v[t]), xv[t], acc);
+        acc = (k0 + t * LPR + j < cnt) ? pr : acc;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+  return acc;
+}
+
 struct CgArgs {
   Layout lay;
   const int32_t* rp;
@@ -122,10 +164,12 @@ struct CgArgs {
   CgScalars* s;
   cudaGraphConditionalHandle cond;
   int32_t in_graph;    // 0 when the body kernels are launched one by one (profiling mode)
+  const int32_t* perm; // SpMV row order (rows sorted by length within windows), or null
+  const int32_t* gsplit; // with perm: first 32-row group of every warp of the SpMV grid
 };
 
 // MODE 0 (I1): r = b - A x, sum b^2.  MODE 1 (A): q = A p, sum p q.  MODE 2 (T): r = b - A x, sum r^2.
-template <typename VT, int MODE>
+template <typename VT, int MODE, bool BIN>
 __global__ void __launch_bounds__(256) cg_spmv_kernel(const CgArgs a) {
   __shared__ double sm[32];
   __shared__ int is_last;
@@ -134,25 +178,64 @@ __global__ void __launch_bounds__(256) cg_spmv_kernel(const CgArgs a) {
   const VT* va = reinterpret_cast<const VT*>(a.va);
   const int64_t n = a.lay.n;
   double acc = 0.0;
-  // warp-uniform trip count: every lane runs every iteration (rows past n are masked)
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = base + threadIdx.x;
-    const bool valid = row < n;
-    if (MODE == 1) {
-      const double qi = cg_row<VT>(a.rp, a.ci, va, a.p, row, valid);
-      if (valid) {
-        a.q[row] = qi;
-        acc = fma(__ldg(a.p + row), qi, acc);
-      }
-    } else {
-      const double ax = cg_row<VT>(a.rp, a.ci, va, a.x, row, valid);
-      if (valid) {
-        const double bi = __ldg(a.b + row);
-        const double ri = bi - ax;
-        a.r[row] = ri;
+  // Warp-uniform trip counts: every lane runs every iteration (rows past n are masked).
+  // Binned order (BIN): each warp walks its own run of 32-row groups of the permuted order,
+  // runs of about equal cost; otherwise a grid-stride loop over rows in natural order.
+  auto one = [&](int64_t idx) {
+    const bool valid = idx < n;
+    const int64_t row = (BIN && valid) ? (int64_t)__ldg(a.perm + idx) : idx;
+    const double* X = MODE == 1 ? a.p : a.x;
+    const int32_t s0 = valid ? __ldg(a.rp + row) : 0;
+    const int32_t cnt0 = valid ? __ldg(a.rp + row + 1) - s0 : 0;
+    const int32_t wmax = __reduce_max_sync(FULL, cnt0);
+    // the row's result goes to the lane that computed it
+    auto finish = [&](int64_t r_, double v_) {
+      if (MODE == 1) {
+        a.q[r_] = v_;
+        acc = fma(__ldg(a.p + r_), v_, acc);
+      } else {
+        const double bi = __ldg(a.b + r_);
+        const double ri = bi - v_;
+        a.r[r_] = ri;
         acc = MODE == 0 ? fma(bi, bi, acc) : fma(ri, ri, acc);
       }
+    };
+    if (!BIN || wmax <= 64) {
+      const double v = cg_row_range<VT>(a.ci, va, X, s0, cnt0, wmax);
+      if (valid) finish(row, v);
+    } else if (wmax <= 256) {
+      // binned rows of medium length: 8 lanes per row, 4 rows per pass
+      const int lane = threadIdx.x & 31;
+      for (int pp = 0; pp < 8; ++pp) {
+        const int src = pp * 4 + (lane >> 3);
+        const int32_t s = __shfl_sync(FULL, s0, src);
+        const int32_t cnt = __shfl_sync(FULL, cnt0, src);
+        const int64_t r_ = __shfl_sync(FULL, row, src);
+        const int vld = __shfl_sync(FULL, (int)valid, src);
+        const double v = cg_row_lanes<VT, 8>(a.ci, va, X, s, cnt, __reduce_max_sync(FULL, cnt));
+        if ((lane & 7) == 0 && vld) finish(r_, v);
+      }
+    } else {
+      // binned long rows: the whole warp on one row at a time
+      const int lane = threadIdx.x & 31;
+      for (int pp = 0; pp < 32; ++pp) {
+        const int32_t s = __shfl_sync(FULL, s0, pp);
+        const int32_t cnt = __shfl_sync(FULL, cnt0, pp);
+        const int64_t r_ = __shfl_sync(FULL, row, pp);
+        const int vld = __shfl_sync(FULL, (int)valid, pp);
+        const double v = cg_row_lanes<VT, 32>(a.ci, va, X, s, cnt, cnt);
+        if (lane == 0 && vld) finish(r_, v);
+      }
     }
+  };
+  if constexpr (BIN) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int32_t g1 = __ldg(a.gsplit + gw + 1);
+    for (int32_t g = __ldg(a.gsplit + gw); g < g1; ++g) one((int64_t)g * 32 + lane);
+  } else {
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x)
+      one(base + threadIdx.x);
   }
   double v[1] = {acc};
   if (!cg_last_cta<1>(v, a.part, &S->cnt[MODE == 2 ? 2 : 0], sm, &is_last)) return;
@@ -175,6 +258,23 @@ __global__ void __launch_bounds__(256) cg_spmv_kernel(const CgArgs a) {
       S->xupd = 1;
     }
   }
+}
+
+// The SpMV of a CG phase, binned or natural row order.
+constexpr int SPMV_BIN_CTAS_PER_SM = 4;   // the binned variants use up to 64 registers
+
+int cg_spmv_bin_warps() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return (sms > 0 ? sms : 1) * SPMV_BIN_CTAS_PER_SM * 8;
+}
+
+template <typename VT, int MODE>
+static void launch_spmv_mode(int grid, cudaStream_t st, const CgArgs& a) {
+  // the binned grid must match the split: one warp per work item
+  if (a.perm) cg_spmv_kernel<VT, MODE, true><<<cg_spmv_bin_warps() / 8, 256, 0, st>>>(a);
+  else cg_spmv_kernel<VT, MODE, false><<<grid, 256, 0, st>>>(a);
 }
 
 // RESTART (I2): z = M^{-1} r, p = z, rho, rr.  Otherwise (B): r -= alpha q, z = M^{-1} r.
@@ -509,7 +609,7 @@ static cudaError_t launch_precond(cudaStream_t cs, const CgGraph* g) {
 
 template <typename VT, typename FT, int BS>
 static cudaError_t capture_body(cudaStream_t cs, const CgGraph* g) {
-  cg_spmv_kernel<VT, 1><<<g->g_spmv, 256, 0, cs>>>(g->args);
+  launch_spmv_mode<VT, 1>(g->g_spmv, cs, g->args);
   cudaError_t e = launch_precond<FT, BS, false>(cs, g);
   if (e != cudaSuccess) return e;
   cg_update_kernel<<<g->g_upd, 256, 0, cs>>>(g->args);
@@ -529,7 +629,7 @@ static cudaError_t capture_body_bs(cudaStream_t cs, const CgGraph* g) {
 
 template <typename VT, typename FT, int BS>
 static cudaError_t launch_pre(cudaStream_t st, const CgGraph* g) {
-  cg_spmv_kernel<VT, 0><<<g->g_spmv, 256, 0, st>>>(g->args);
+  launch_spmv_mode<VT, 0>(g->g_spmv, st, g->args);
   return launch_precond<FT, BS, true>(st, g);
 }
 
@@ -559,7 +659,8 @@ size_t cg_scalars_bytes() { return sizeof(CgScalars); }
 // cg_graph_partials() doubles; scal points to cg_scalars_bytes() of device memory.
 cudaError_t cg_graph_create(void** out, const Layout& L, const int32_t* rp, const int32_t* ci, const void* va,
                             bool val_f32, const void* minv, bool fac_f32, const double* b, double* x, double* r,
-                            double* z, double* p, double* q, double* part, void* scal, cudaStream_t st) {
+                            double* z, double* p, double* q, double* part, void* scal, const int32_t* perm,
+                            const int32_t* gsplit, cudaStream_t st) {
   CgGraph* g = new CgGraph();
   memset(g, 0, sizeof(*g));
   const int sms = sms_now();
@@ -587,6 +688,8 @@ cudaError_t cg_graph_create(void** out, const Layout& L, const int32_t* rp, cons
   a.part = part;
   a.s = reinterpret_cast<CgScalars*>(scal);
   a.in_graph = 1;
+  a.perm = perm;
+  a.gsplit = gsplit;
   cudaError_t e = cudaGraphCreate(&g->graph, 0);
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&a.cond, g->graph, 0, 0);
   cudaGraphNode_t arm = nullptr, loop = nullptr;
@@ -663,8 +766,8 @@ cudaError_t cg_graph_round(void* h, bool val_f32, bool fac_f32, cudaStream_t st)
   if (e != cudaSuccess) return e;
   e = cudaGraphLaunch(g->exec, st);
   if (e != cudaSuccess) return e;
-  if (val_f32) cg_spmv_kernel<float, 2><<<g->g_spmv, 256, 0, st>>>(a);
-  else cg_spmv_kernel<double, 2><<<g->g_spmv, 256, 0, st>>>(a);
+  if (val_f32) launch_spmv_mode<float, 2>(g->g_spmv, st, a);
+  else launch_spmv_mode<double, 2>(g->g_spmv, st, a);
   return cudaGetLastError();
 }
 
@@ -682,7 +785,7 @@ static cudaError_t eager_round_t(CgGraph* g, cudaStream_t st, double* ms, int* i
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   while (e == cudaSuccess && cont) {
     cudaEventRecord(ev[0], st);
-    cg_spmv_kernel<VT, 1><<<eg.g_spmv, 256, 0, st>>>(eg.args);
+    launch_spmv_mode<VT, 1>(eg.g_spmv, st, eg.args);
     cudaEventRecord(ev[1], st);
     e = launch_precond<FT, BS, false>(st, &eg);
     cudaEventRecord(ev[2], st);
@@ -699,8 +802,8 @@ static cudaError_t eager_round_t(CgGraph* g, cudaStream_t st, double* ms, int* i
   }
   for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
   if (e != cudaSuccess) return e;
-  if (std::is_same<VT, float>::value) cg_spmv_kernel<float, 2><<<eg.g_spmv, 256, 0, st>>>(eg.args);
-  else cg_spmv_kernel<double, 2><<<eg.g_spmv, 256, 0, st>>>(eg.args);
+  if (std::is_same<VT, float>::value) launch_spmv_mode<float, 2>(eg.g_spmv, st, eg.args);
+  else launch_spmv_mode<double, 2>(eg.g_spmv, st, eg.args);
   return cudaGetLastError();
 }
 

@@ -152,7 +152,21 @@ int cg_graph_partials();
 size_t cg_scalars_bytes();
 cudaError_t cg_graph_create(void** out, const Layout& L, const int32_t* rp, const int32_t* ci, const void* va,
                             bool val_f32, const void* minv, bool fac_f32, const double* b, double* x, double* r,
-                            double* z, double* p, double* q, double* part, void* scal, cudaStream_t st);
+                            double* z, double* p, double* q, double* part, void* scal, const int32_t* perm,
+                            const int32_t* gsplit, cudaStream_t st);
+
+// Row binning (pc_rowbin.cu): rows sorted by length inside windows of ROWBIN_W rows.
+constexpr int ROWBIN_W = 2048;
+// d_out[0] += sum over 32-row groups of 32 * (longest row in the group).
+cudaError_t row_bin_waste(int64_t n, const int32_t* rp, unsigned long long* d_out, cudaStream_t st);
+// perm[n]: the rows of every window, stably sorted by length bucket.
+cudaError_t row_bin_build(int64_t n, const int32_t* rp, int32_t* perm, cudaStream_t st);
+// gsplit[n_items+1]: contiguous runs of 32-row groups of the binned order with about equal
+// SpMV cost, one per warp of the binned SpMV grid.  scratch: ceil(n/32) int64.
+cudaError_t row_bin_split(int64_t n, const int32_t* rp, const int32_t* perm, int n_items, int32_t* gsplit,
+                          int64_t* scratch, cudaStream_t st);
+// Warps of the binned SpMV grid (the number of work items of its split).
+int cg_spmv_bin_warps();
 void cg_graph_destroy(void* g);
 cudaError_t cg_graph_round(void* g, bool val_f32, bool fac_f32, cudaStream_t st);
 cudaError_t cg_graph_solve(void* g, double tol, int max_iter, int max_restarts, bool val_f32, bool fac_f32,

@@ -1,0 +1,212 @@
+// Row binning for the thread-per-row SpMV on matrices with irregular row lengths.
+//
+// The CG SpMV gives one row to each lane and runs every lane for the longest row of its
+// warp (predicated FP64 FMAs still occupy this GPU's narrow FP64 pipe), so a warp that
+// holds one hub row among short rows pays for 32 hub rows.  Sorting the rows by length
+// inside windows of ROWBIN_W consecutive rows makes the 32 rows of a warp similar in length
+// while keeping each warp's vector accesses inside the window (L1/L2 reuse).
+//
+// The permutation is a stable counting sort per window (deterministic: slices of 32 rows
+// in row order, ranks inside a slice by lane order), so the SpMV stays bit-reproducible.
+#include "pc_kernels.cuh"
+
+namespace pc {
+
+constexpr int ROWBIN_THREADS = 256;
+constexpr int ROWBIN_SLICES = ROWBIN_W / 32;           // 64 slices of 32 rows
+constexpr int ROWBIN_BUCKETS = 128;
+
+// Length bucket: exact up to 64 entries, then 8 buckets per octave (ratio 2^(1/8) within a
+// bucket).
+__device__ __forceinline__ int row_bucket(int32_t len) {
+  if (len <= 64) return len;
+  const int b = 64 + (int)ceilf(8.0f * log2f((float)len * (1.0f / 64.0f)));
+  return b < ROWBIN_BUCKETS - 1 ? b : ROWBIN_BUCKETS - 1;
+}
+
+// Sum over 32-row groups of 32 * (longest row of the group): the FP64 lane-operations the
+// unbinned SpMV spends.  out[0] += that sum (integer atomics: exact).
+__global__ void row_waste_kernel(int64_t n, const int32_t* __restrict__ rp, unsigned long long* out) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long mine = 0;
+  for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) - lane; base < n;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = base + lane;
+    const int32_t len = row < n ? __ldg(rp + row + 1) - __ldg(rp + row) : 0;
+    const int32_t m = __reduce_max_sync(FULL, len);
+    if (lane == 0) mine += 32ull * (unsigned long long)m;
+  }
+  if (lane == 0 && mine) atomicAdd(out, mine);
+}
+
+// perm[w0 .. w0+W) = the rows of window [w0, w0+W) sorted by length bucket (stable).
+__global__ void __launch_bounds__(ROWBIN_THREADS) row_bin_kernel(int64_t n, const int32_t* __restrict__ rp,
+                                                                 int32_t* __restrict__ perm) {
+  __shared__ int cnt[ROWBIN_SLICES][ROWBIN_BUCKETS];
+  __shared__ int base_b[ROWBIN_BUCKETS];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  constexpr int NW = ROWBIN_THREADS / 32;
+  const int64_t n_win = (n + ROWBIN_W - 1) / ROWBIN_W;
+  for (int64_t win = blockIdx.x; win < n_win; win += gridDim.x) {
+    const int64_t w0 = win * ROWBIN_W;
+    for (int t = threadIdx.x; t < ROWBIN_SLICES * ROWBIN_BUCKETS; t += ROWBIN_THREADS) (&cnt[0][0])[t] = 0;
+    __syncthreads();
+    // per slice: bucket of every lane's row, rank among equal buckets of the slice
+    int bk[ROWBIN_SLICES / NW], rk[ROWBIN_SLICES / NW];
+#pragma unroll
+    for (int k = 0; k < ROWBIN_SLICES / NW; ++k) {
+      const int slice = k * NW + warp;
+      const int64_t row = w0 + (int64_t)slice * 32 + lane;
+      const bool valid = row < n;
+      const int b = valid ? row_bucket(__ldg(rp + row + 1) - __ldg(rp + row)) : -1;
+      const unsigned peers = __match_any_sync(FULL, b);
+      const unsigned lower = peers & ((1u << lane) - 1u);
+      bk[k] = b;
+      rk[k] = __popc(lower);
+      if (valid && lower == 0u) cnt[slice][b] = __popc(peers);
+    }
+    __syncthreads();
+    // bucket totals, exclusive scan over buckets, then per bucket over slices in order
+    if (threadIdx.x < ROWBIN_BUCKETS) {
+      int tot = 0;
+      for (int s = 0; s < ROWBIN_SLICES; ++s) tot += cnt[s][threadIdx.x];
+      base_b[threadIdx.x] = tot;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int run = 0;
+      for (int b = 0; b < ROWBIN_BUCKETS; ++b) {
+        const int t = base_b[b];
+        base_b[b] = run;
+        run += t;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < ROWBIN_BUCKETS) {
+      int off = base_b[threadIdx.x];
+      for (int s = 0; s < ROWBIN_SLICES; ++s) {
+        const int t = cnt[s][threadIdx.x];
+        cnt[s][threadIdx.x] = off;
+        off += t;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < ROWBIN_SLICES / NW; ++k) {
+      const int slice = k * NW + warp;
+      const int64_t row = w0 + (int64_t)slice * 32 + lane;
+      if (bk[k] >= 0) perm[w0 + cnt[slice][bk[k]] + rk[k]] = (int32_t)row;
+    }
+    __syncthreads();
+  }
+}
+
+// Cost of every 32-row group of the binned order for the SpMV: the larger of its FP64
+// lane-operations and its dependent memory rounds (a round = index/value loads then the
+// gathers) weighted by the 256 entries a warp of short rows handles per round.  Modes of
+// cg_spmv_kernel: one lane per row up to 64 entries (8 entries per lane and round); 8 lanes
+// per row up to 256 (64 entries per row and round, 4 rows at a time); else the whole warp
+// per row (256 entries per round).  Plus a per-group overhead.
+__global__ void group_cost_kernel(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ perm,
+                                  int64_t* __restrict__ cost) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n_groups = (n + 31) / 32;
+  for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < n_groups;
+       g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t idx = g * 32 + lane;
+    int32_t len = 0;
+    if (idx < n) {
+      const int32_t row = __ldg(perm + idx);
+      len = __ldg(rp + row + 1) - __ldg(rp + row);
+    }
+    const int32_t m = __reduce_max_sync(FULL, len);
+    const int32_t sum = __reduce_add_sync(FULL, len);
+    int64_t ops, rounds;
+    if (m <= 64) {
+      ops = 32ll * m;
+      rounds = (m + 7) / 8;
+    } else if (m <= 256) {
+      ops = (int64_t)sum + 32ll * 3;
+      // 8 passes of 4 rows; a pass takes the rounds of its longest row
+      const int32_t pmax = __reduce_max_sync(FULL, len);   // upper bound per pass
+      rounds = 8ll * ((pmax + 63) / 64);
+    } else {
+      ops = (int64_t)sum + 32ll * 5;
+      rounds = __reduce_add_sync(FULL, (len + 255) / 256);
+    }
+    if (lane == 0) cost[g] = (ops > 256 * rounds ? ops : 256 * rounds) + 256;
+  }
+}
+
+// Inclusive prefix sum of cost[0..m) in place (one CTA of 1024 threads: each thread scans a
+// contiguous stretch, then the stretch totals are scanned).
+__global__ void __launch_bounds__(1024) cost_scan_kernel(int64_t m, int64_t* cost) {
+  __shared__ int64_t tot[1024];
+  const int64_t per = (m + 1023) / 1024;
+  const int64_t lo = threadIdx.x * per;
+  const int64_t hi = lo + per < m ? lo + per : m;
+  int64_t run = 0;
+  for (int64_t i = lo; i < hi; ++i) run += cost[i];
+  tot[threadIdx.x] = run;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int i = 1; i < 1024; ++i) tot[i] += tot[i - 1];
+  __syncthreads();
+  run = threadIdx.x ? tot[threadIdx.x - 1] : 0;
+  for (int64_t i = lo; i < hi; ++i) {
+    run += cost[i];
+    cost[i] = run;
+  }
+}
+
+// gsplit[w] = first group of work item w: the first group whose inclusive prefix exceeds
+// w * total / n_items (so every item gets a contiguous run of about equal cost).
+__global__ void group_split_kernel(int64_t m, const int64_t* __restrict__ prefix, int n_items,
+                                   int32_t* __restrict__ gsplit) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w > n_items) return;
+  if (w == n_items) {
+    gsplit[w] = (int32_t)m;
+    return;
+  }
+  const int64_t total = m > 0 ? prefix[m - 1] : 0;
+  const int64_t target = (int64_t)((double)total * (double)w / (double)n_items);
+  int64_t lo = 0, hi = m;   // first index with prefix > target
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (prefix[mid] > target) hi = mid;
+    else lo = mid + 1;
+  }
+  gsplit[w] = (int32_t)(w == 0 ? 0 : lo);
+}
+
+cudaError_t row_bin_split(int64_t n, const int32_t* rp, const int32_t* perm, int n_items, int32_t* gsplit,
+                          int64_t* scratch, cudaStream_t st) {
+  const int64_t m = (n + 31) / 32;
+  int64_t grid = (m * 32 + 255) / 256;
+  if (grid > 152 * 16) grid = 152 * 16;
+  if (grid < 1) grid = 1;
+  group_cost_kernel<<<(unsigned)grid, 256, 0, st>>>(n, rp, perm, scratch);
+  cost_scan_kernel<<<1, 1024, 0, st>>>(m, scratch);
+  group_split_kernel<<<(n_items + 1 + 255) / 256, 256, 0, st>>>(m, scratch, n_items, gsplit);
+  return cudaGetLastError();
+}
+
+cudaError_t row_bin_waste(int64_t n, const int32_t* rp, unsigned long long* d_out, cudaStream_t st) {
+  int64_t grid = (n + 255) / 256;
+  if (grid > 152 * 16) grid = 152 * 16;
+  if (grid < 1) grid = 1;
+  row_waste_kernel<<<(unsigned)grid, 256, 0, st>>>(n, rp, d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t row_bin_build(int64_t n, const int32_t* rp, int32_t* perm, cudaStream_t st) {
+  const int64_t n_win = (n + ROWBIN_W - 1) / ROWBIN_W;
+  int64_t grid = n_win < 152 * 8 ? n_win : 152 * 8;
+  if (grid < 1) grid = 1;
+  row_bin_kernel<<<(unsigned)grid, ROWBIN_THREADS, 0, st>>>(n, rp, perm);
+  return cudaGetLastError();
+}
+
+}  // namespace pc
