@@ -89,15 +89,20 @@ __global__ void __launch_bounds__(256) lz_reorth_kernel(LanczosState s, int j) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   const int nl = j + 1;
   const bool need_tile = MODE != 3;
-  double* Vs = dsm;                              // nl * 32
-  double* acc = Vs + (need_tile ? nl * LZ_TW : 0);  // nl
-  double* red = acc + nl;                        // 8 * 32
-  double* wt = red + 8 * 32;                     // 32
+  // Coefficient passes (MODE 0, 1) keep one partial sum per (basis vector, lane) in shared
+  // memory across all of the CTA's tiles and reduce across lanes once at the end: a warp
+  // shuffle tree per tile would cost five FP64 adds per 32 products on the narrow FP64 pipe.
+  constexpr bool COEF = MODE == 0 || MODE == 1;
+  double* Vs = dsm;                                  // nl * 32
+  double* acc = Vs + (need_tile ? nl * LZ_TW : 0);   // COEF: nl * 32 per-lane partials
+  double* red = acc + (COEF ? nl * LZ_TW : 0);       // 8 * 32
+  double* wt = red + 8 * 32;                         // 32
   const int64_t n = s.n;
   const double aj = s.alpha[j];
   const double* cin = MODE == 1 ? s.coef : s.coef + s.m;
   const double* qj = s.V + (int64_t)j * n;
-  for (int l = tid; l < nl; l += blockDim.x) acc[l] = 0.0;
+  if (COEF)
+    for (int i = tid; i < nl * LZ_TW; i += blockDim.x) acc[i] = 0.0;
   double nrm = 0.0;
   for (int64_t t = blockIdx.x; t * LZ_TW < n; t += gridDim.x) {
     const int64_t c0 = t * LZ_TW;
@@ -127,19 +132,20 @@ __global__ void __launch_bounds__(256) lz_reorth_kernel(LanczosState s, int j) {
       }
     }
     __syncthreads();
-    if (MODE == 0 || MODE == 1) {
-      for (int l = warp; l < nl; l += nwarp) {
-        const double p = warp_sum(Vs[l * LZ_TW + lane] * wt[lane]);
-        if (lane == 0) acc[l] += p;
-      }
+    if (COEF) {
+      const double wl = wt[lane];
+      for (int l = warp; l < nl; l += nwarp) acc[l * LZ_TW + lane] = fma(Vs[l * LZ_TW + lane], wl, acc[l * LZ_TW + lane]);
     } else if (tid < LZ_TW) {
       nrm = fma(wt[tid], wt[tid], nrm);
     }
   }
   __syncthreads();
   const int m = s.m;
-  if (MODE == 0 || MODE == 1) {
-    for (int l = tid; l < nl; l += blockDim.x) __stcg(s.part + (int64_t)blockIdx.x * m + l, acc[l]);
+  if (COEF) {
+    for (int l = warp; l < nl; l += nwarp) {
+      const double p = warp_sum(acc[l * LZ_TW + lane]);
+      if (lane == 0) __stcg(s.part + (int64_t)blockIdx.x * m + l, p);
+    }
   } else {
     double v[1] = {nrm};
     block_sum<1>(v, smr);
@@ -236,7 +242,9 @@ int lanczos_grid() {
   return 2 * sms;
 }
 
-static size_t reorth_smem(int nl, bool tile) { return sizeof(double) * ((tile ? nl * LZ_TW : 0) + nl + 8 * 32 + 32); }
+static size_t reorth_smem(int nl, bool tile, bool coef) {
+  return sizeof(double) * ((tile ? nl * LZ_TW : 0) + (coef ? nl * LZ_TW : 0) + 8 * 32 + 32);
+}
 
 cudaError_t lanczos_init(const LanczosState& s, const double* v0, bool precond, const Layout& L, const void* linv,
                          bool fac_f32, cudaStream_t st) {
@@ -291,12 +299,12 @@ cudaError_t lanczos_step(const LanczosState& s, int j, int reorth, bool precond,
   }
   const int nl = j + 1;
   if (reorth) {
-    const size_t sm = reorth_smem(nl, true);
+    const size_t sm = reorth_smem(nl, true, true);
     lz_reorth_kernel<0><<<G, 256, sm, st>>>(s, j);
     lz_reorth_kernel<1><<<G, 256, sm, st>>>(s, j);
-    lz_reorth_kernel<2><<<G, 256, sm, st>>>(s, j);
+    lz_reorth_kernel<2><<<G, 256, reorth_smem(nl, true, false), st>>>(s, j);
   } else {
-    lz_reorth_kernel<3><<<G, 256, reorth_smem(nl, false), st>>>(s, j);
+    lz_reorth_kernel<3><<<G, 256, reorth_smem(nl, false, false), st>>>(s, j);
   }
   if (j + 1 < s.m) lz_normalize_kernel<<<G, 256, 0, st>>>(s, j);
   return cudaGetLastError();
@@ -308,7 +316,7 @@ cudaError_t lanczos_finish(const LanczosState& s, cudaStream_t st) {
 }
 
 cudaError_t lanczos_configure(int m) {
-  const size_t sm = reorth_smem(m, true);
+  const size_t sm = reorth_smem(m, true, true);
   cudaError_t e = cudaFuncSetAttribute(lz_reorth_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(lz_reorth_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
