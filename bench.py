@@ -68,6 +68,11 @@ def parse():
     ap.add_argument("--n-sys", type=int, default=512, help="systems in the batched workload")
     ap.add_argument("--no-tune", action="store_true", help="batched workload: skip the launch-shape autotuner")
     ap.add_argument("--tune-trials", type=int, default=0, help="batched autotuner candidates (0 = all)")
+    ap.add_argument("--batch-shape", default="",
+                    help="batched workload: explicit launch shape 'ctas_per_sm,team_max,slots_per_cta,setup_kb' "
+                         "(skips the autotuner)")
+    ap.add_argument("--phase-profile", action="store_true",
+                    help="batched workload: one extra solve with per-phase device timers (not timed)")
     ap.add_argument("--profile", action="store_true",
                     help="one solve of the workload and nothing else (for ncu captures); prints a short line")
     args = ap.parse_args()
@@ -545,7 +550,12 @@ def run_batched(args):
     st = torch.cuda.current_stream()
     peak, peak_kind = measured_hbm()
     tuning = {}
-    if not args.no_tune:
+    if args.batch_shape:
+        occ, team, split, kb = args.batch_shape.split(",")
+        pc.batch_set_tuning(int(occ), int(team), float(split))
+        pc.binding.lib().pc_batch_set_setup_smem(int(kb))
+        tuning["explicit"] = args.batch_shape
+    elif not args.no_tune:
         for prec in ([args.prec, "fp64"] if args.prec != "fp64" and not args.no_fp64_compare else [args.prec]):
             t0 = time.time()
             tms, cfg = pc.batch_autotune(batch, bd, args.tol, args.maxit, prec, args.tune_trials)
@@ -601,6 +611,15 @@ def run_batched(args):
         "graph": bool(info["graph"]), "gpu_launches": 2 * args.steps, "generation_s": gen_s, "autotune": tuning,
     }
     line["clocks"] = clk.summary()
+    if args.phase_profile:
+        os.environ["PC_BATCH_PROFILE"] = "1"
+        Hp = pc.Batch(batch, args.prec)
+        Hp.solve(bd, args.tol, args.maxit)
+        prof = Hp.phase_profile()
+        Hp.destroy()
+        del os.environ["PC_BATCH_PROFILE"]
+        tot = sum(prof.values()) or 1
+        line["phase_profile"] = {k: {"cta_ms": v / 1e6, "share": v / tot} for k, v in prof.items()}
     if args.prec != "fp64" and not args.no_fp64_compare:
         _, per64, info64, ms64, kms64, _, _ = timed("fp64", max(1, min(args.steps, 2)), 1)
         b64 = batch_step_bytes(batch, "fp64", per64["iterations"], restarts)

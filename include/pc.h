@@ -296,6 +296,13 @@ pc_status pc_batch_destroy(pc_batch_handle *h);
  * written (<= max_entries). */
 int32_t pc_batch_info(const pc_batch_handle *h, int32_t *out, int32_t max_entries);
 
+/* Phase profile of a handle created with the environment variable PC_BATCH_PROFILE=1:
+ * nanoseconds summed over all CTAs and over every solve since creation, per phase:
+ * setup, start (x0 = 0 pass), SpMV, unit pass (r, x, z), p update, true residual,
+ * reductions and team waits, queue and idle (8 entries, host out[]).  Returns the count
+ * copied, 0 when profiling is off.  Synchronous. */
+int32_t pc_batch_profile(const pc_batch_handle *h, uint64_t *out, int32_t max_entries);
+
 /* Team size and first queue slot of every system (host arrays [n_sys], may be NULL).
  * Returns n_sys. */
 int32_t pc_batch_teams(const pc_batch_handle *h, int32_t *team, int32_t *slot0);

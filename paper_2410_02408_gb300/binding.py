@@ -101,6 +101,7 @@ def lib():
         "pc_batch_destroy": (_I32, [_P]),
         "pc_batch_info": (_I32, [_P, _P, _I32]),
         "pc_batch_teams": (_I32, [_P, _P, _P]),
+        "pc_batch_profile": (_I32, [_P, _P, _I32]),
         "pc_batch_schedule": (_I32, [_I32, _P, _P, _P, _I32, _I32, _D, _P, _P, _P]),
         "pc_batch_set_tuning": (None, [_I32, _I32, _D]),
         "pc_batch_set_setup_smem": (None, [_I32]),
@@ -430,6 +431,13 @@ class Batch:
         k = lib().pc_batch_info(self._h, ctypes.cast(out, ctypes.c_void_p), 8)
         keys = ("grid", "ctas_per_sm", "slots", "team_max", "smem", "setup_warps", "graph")
         return {keys[i]: int(out[i]) for i in range(min(k, len(keys)))}
+
+    def phase_profile(self) -> dict:
+        """Per-phase nanoseconds summed over CTAs (handles created with PC_BATCH_PROFILE=1)."""
+        out = np.zeros(8, dtype=np.uint64)
+        k = lib().pc_batch_profile(self._h, out.ctypes.data, 8)
+        names = ("setup", "start", "spmv", "units", "p_update", "true_residual", "sync", "idle")
+        return {names[i]: int(out[i]) for i in range(k)}
 
     def teams(self):
         team = np.zeros(self.n_sys, dtype=np.int32)

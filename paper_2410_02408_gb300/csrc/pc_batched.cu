@@ -67,6 +67,8 @@ struct BArgs {
   long long budget;
   int32_t setup_warps;       // warps per CTA with a shared-memory setup slot
   int32_t slot_bytes;        // shared memory per setup slot
+  unsigned long long* prof;  // null, or PH_N phase accumulators (profiling mode)
+  int32_t smem_bytes;        // dynamic shared memory of a CTA
 };
 
 struct Team {
@@ -88,8 +90,23 @@ struct Env {
   long long budget;
   double tol, pivot_tol;
   int32_t max_iter, max_restarts;
-  int32_t setup_warps, slot_bytes;
+  int32_t setup_warps, slot_bytes, smem_bytes;
+  unsigned long long* prof;   // null, or per-phase nanoseconds summed over CTAs (profiling mode)
 };
+
+// Profiling mode: thread 0 of every CTA adds the time since its previous mark to a phase
+// accumulator (globaltimer, ns).  Phases: 0 setup, 1 start (x0 = 0 pass), 2 SpMV,
+// 3 unit pass (r, x, z), 4 p update, 5 true residual, 6 reductions and team waits,
+// 7 queue and idle.
+enum { PH_SETUP = 0, PH_START, PH_SPMV, PH_UNITS, PH_PUPD, PH_TRUE, PH_SYNC, PH_IDLE, PH_N };
+
+__device__ __forceinline__ void prof_mark(const Env& e, int ph, unsigned long long& last) {
+  if (e.prof != nullptr && threadIdx.x == 0) {
+    const unsigned long long now = globaltimer_ns();
+    atomicAdd(e.prof + ph, now - last);
+    last = now;
+  }
+}
 
 __device__ __forceinline__ double* part_at(const Env& e, int slot, unsigned parity) {
   return e.part + ((size_t)slot * 2 + (parity & 1u)) * 4;
@@ -206,13 +223,18 @@ struct D2 {
 template <typename FT>
 __device__ __noinline__ void phase_setup(const Env& e, const SysCtx& c, unsigned char* dsm) {
   const int warp = threadIdx.x >> 5;
-  if (warp >= e.setup_warps) return;
   const Layout L = c.L;
-  FT* As = reinterpret_cast<FT*>(dsm + (size_t)warp * e.slot_bytes);
+  // as many warps as this system's block size allows in the CTA's shared memory
+  const int slot = (int)((setup_unit_smem(L, sizeof(FT)) + 15) & ~(size_t)15);
+  int nw = e.smem_bytes / slot;
+  nw = nw < BNW ? nw : BNW;
+  nw = nw > e.setup_warps ? nw : e.setup_warps;
+  if (warp >= nw) return;
+  FT* As = reinterpret_cast<FT*>(dsm + (size_t)warp * slot);
   FT* Xs = As + (size_t)L.U * (L.bs + 1);
   FT* Mf = reinterpret_cast<FT*>(const_cast<void*>(c.Mf));
   const int64_t uM = unit_elems_minv(L);
-  for (int64_t u = c.u0 + warp; u < c.u1; u += e.setup_warps)
+  for (int64_t u = c.u0 + warp; u < c.u1; u += nw)
     setup_unit<double, FT>(L, u, c.rp, e.ci, e.va, e.pivot_tol, Mf + u * uM, nullptr, As, Xs, threadIdx.x & 31,
                            &e.fail[c.s]);
 }
@@ -319,9 +341,11 @@ __device__ __noinline__ void solve_system(const Env& e, const SysCtx& c, Team t,
                                           int32_t* o_restarts, double* o_relres) {
   int status = ST_OK, it = 0, restarts = 0;
   double relres = -1.0;   // -1: not computed (setup failure, timeout)
+  unsigned long long last = e.prof != nullptr && threadIdx.x == 0 ? globaltimer_ns() : 0ull;
 
   phase_setup<FT>(e, c, dsm);
   __syncthreads();
+  prof_mark(e, PH_SETUP, last);
 
   // x0 = 0: r = b, z = M^{-1} r, p = z; ||b||^2, rho = r.z
   double v[2];
@@ -330,7 +354,10 @@ __device__ __noinline__ void solve_system(const Env& e, const SysCtx& c, Team t,
     v[0] = d.b;
     v[1] = d.a;
   }
-  if (!team_allreduce<2>(e, t, v, red, flag)) {
+  prof_mark(e, PH_START, last);
+  const bool ok0 = team_allreduce<2>(e, t, v, red, flag);
+  prof_mark(e, PH_SYNC, last);
+  if (!ok0) {
     status = ST_TIMEOUT;
   } else if (*(volatile unsigned long long*)&e.fail[t.s] != ~0ull) {
     status = ST_NOT_SPD;
@@ -352,7 +379,10 @@ __device__ __noinline__ void solve_system(const Env& e, const SysCtx& c, Team t,
           break;
         }
         double pq[1] = {phase_spmv(e, c)};
-        if (!team_allreduce<1>(e, t, pq, red, flag)) {
+        prof_mark(e, PH_SPMV, last);
+        const bool ok1 = team_allreduce<1>(e, t, pq, red, flag);
+        prof_mark(e, PH_SYNC, last);
+        if (!ok1) {
           status = ST_TIMEOUT;
           break;
         }
@@ -363,7 +393,10 @@ __device__ __noinline__ void solve_system(const Env& e, const SysCtx& c, Team t,
         const double alpha = rho / pq[0];
         const D2 d = phase_units<FT, BS, U_ITER>(c, alpha);
         double w[2] = {d.a, d.b};
-        if (!team_allreduce<2>(e, t, w, red, flag)) {
+        prof_mark(e, PH_UNITS, last);
+        const bool ok2 = team_allreduce<2>(e, t, w, red, flag);
+        prof_mark(e, PH_SYNC, last);
+        if (!ok2) {
           status = ST_TIMEOUT;
           break;
         }
@@ -373,7 +406,10 @@ __device__ __noinline__ void solve_system(const Env& e, const SysCtx& c, Team t,
         const double beta = w[0] / rho;
         rho = w[0];
         phase_p_update(c, beta);
-        if (!team_sync(e, t, flag)) {
+        prof_mark(e, PH_PUPD, last);
+        const bool ok3 = team_sync(e, t, flag);
+        prof_mark(e, PH_SYNC, last);
+        if (!ok3) {
           status = ST_TIMEOUT;
           break;
         }
@@ -383,7 +419,10 @@ __device__ __noinline__ void solve_system(const Env& e, const SysCtx& c, Team t,
       // iteration stopped without convergence.  Every exit from the loop above follows a
       // team barrier that came after the last x update, so the gathers of x are safe.
       double tv[1] = {phase_true_residual(e, c)};
-      if (!team_allreduce<1>(e, t, tv, red, flag)) {
+      prof_mark(e, PH_TRUE, last);
+      const bool ok4 = team_allreduce<1>(e, t, tv, red, flag);
+      prof_mark(e, PH_SYNC, last);
+      if (!ok4) {
         status = ST_TIMEOUT;
         break;
       }
@@ -438,13 +477,17 @@ __global__ void __launch_bounds__(BT, 2) batched_kernel(const __grid_constant__ 
     env.max_restarts = a.max_restarts;
     env.setup_warps = a.setup_warps;
     env.slot_bytes = a.slot_bytes;
+    env.prof = a.prof;
+    env.smem_bytes = a.smem_bytes;
   }
+  unsigned long long idle_from = a.prof != nullptr && threadIdx.x == 0 ? globaltimer_ns() : 0ull;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_slot = (int)atomicAdd(a.queue, 1u);
     __syncthreads();
     const int slot = s_slot;
     if (slot >= a.n_slots) break;
+    if (a.prof != nullptr && threadIdx.x == 0) atomicAdd(a.prof + PH_IDLE, globaltimer_ns() - idle_from);
     const int s = __ldg(a.slot_sys + slot);
     const BSys d = a.sys[s];
     Team t;
@@ -491,6 +534,7 @@ __global__ void __launch_bounds__(BT, 2) batched_kernel(const __grid_constant__ 
       case 64: solve_system<FT, 64>(env, ctx, t, dsm, red, &flag, a.o_status, a.o_iters, a.o_restarts, a.o_relres); break;
       default: solve_system<FT, 0>(env, ctx, t, dsm, red, &flag, a.o_status, a.o_iters, a.o_restarts, a.o_relres); break;
     }
+    if (a.prof != nullptr && threadIdx.x == 0) idle_from = globaltimer_ns();
   }
 }
 
@@ -555,6 +599,7 @@ struct pc_batch_handle {
   unsigned long long* fail = nullptr;
   unsigned* misc = nullptr;   // queue, err, bad
   int32_t* o_restarts = nullptr;
+  unsigned long long* prof = nullptr;   // PC_BATCH_PROFILE=1: phase accumulators
   int32_t* d_status = nullptr;
   int32_t* d_iters = nullptr;
   double* d_relres = nullptr;
@@ -688,7 +733,7 @@ pc_status pc_batch_destroy(pc_batch_handle* h) {
   if (h->exec) cudaGraphExecDestroy(h->exec);
   if (h->graph) cudaGraphDestroy(h->graph);
   void* ptrs[] = {h->sys, h->slot_sys, h->work, h->minv, h->part, h->cnt, h->fail, h->misc, h->o_restarts,
-                  h->d_status, h->d_iters, h->d_relres};
+                  h->d_status, h->d_iters, h->d_relres, h->prof};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -817,6 +862,13 @@ pc_status pc_batch_create(const pc_batch* B, int32_t prec, double pivot_tol, voi
   PCB_CHECK(balloc(&h->d_status, sizeof(int32_t) * n_sys));
   PCB_CHECK(balloc(&h->d_iters, sizeof(int32_t) * n_sys));
   PCB_CHECK(balloc(&h->d_relres, sizeof(double) * n_sys));
+  {
+    const char* pe = getenv("PC_BATCH_PROFILE");
+    if (pe && pe[0] == '1') {
+      PCB_CHECK(balloc(&h->prof, sizeof(unsigned long long) * pc::PH_N));
+      PCB_CUDA(cudaMemsetAsync(h->prof, 0, sizeof(unsigned long long) * pc::PH_N, st));
+    }
+  }
   PCB_CUDA(cudaMemcpyAsync(h->sys, h->hsys.data(), sizeof(BSys) * n_sys, cudaMemcpyHostToDevice, st));
   PCB_CUDA(cudaMemcpyAsync(h->slot_sys, h->hslot.data(), sizeof(int32_t) * n_slots, cudaMemcpyHostToDevice, st));
   PCB_CUDA(cudaStreamSynchronize(st));   // host vectors are the copy sources
@@ -850,6 +902,8 @@ pc_status pc_batch_create(const pc_batch* B, int32_t prec, double pivot_tol, voi
   a.budget = batch_budget();
   a.setup_warps = setup_warps;
   a.slot_bytes = slot_bytes;
+  a.prof = h->prof;
+  a.smem_bytes = h->smem;
   *out = h;
   return PC_OK;
 #undef PCB_CUDA
@@ -1002,6 +1056,18 @@ int32_t pc_batch_info(const pc_batch_handle* h, int32_t* out, int32_t max_entrie
                           h->graph_ok ? 1 : 0};
   const int32_t k = std::min<int32_t>(max_entries, (int32_t)(sizeof(vals) / sizeof(vals[0])));
   for (int32_t i = 0; i < k; ++i) out[i] = vals[i];
+  return k;
+}
+
+int32_t pc_batch_profile(const pc_batch_handle* h, uint64_t* out, int32_t max_entries) {
+  if (!h || !h->prof || !out || max_entries < 1) return 0;
+  unsigned long long v[pc::PH_N];
+  if (cudaMemcpy(v, h->prof, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const int32_t k = std::min<int32_t>(max_entries, (int32_t)pc::PH_N);
+  for (int32_t i = 0; i < k; ++i) out[i] = v[i];
   return k;
 }
 
