@@ -198,6 +198,61 @@ __device__ __forceinline__ double brow(const int32_t* __restrict__ rp, const int
   return acc;
 }
 
+// Staged rows: a warp copies the contiguous entry range of its 32 consecutive rows into its
+// own shared-memory slice with coalesced loads, then every lane walks its row there.  With
+// one row per lane and direct loads, each load instruction touches about one cache line per
+// few lanes; staged, it touches one per 32 entries.  Only the gathers of x stay global.
+constexpr int STAGE_CAP = 512;                                    // entries per warp slice
+constexpr int STAGE_BYTES = STAGE_CAP * (int)(sizeof(double) + sizeof(int32_t));
+
+__device__ __forceinline__ double brow_staged(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                              const double* __restrict__ va, const double* x, int64_t row, bool valid,
+                                              int32_t s_idle, unsigned char* slice) {
+  const int lane = threadIdx.x & 31;
+  const int32_t s0 = valid ? __ldg(rp + row) : 0;
+  const int32_t e = valid ? __ldg(rp + row + 1) : 0;
+  const int32_t cnt = e - s0;
+  const int32_t wmax = __reduce_max_sync(FULL, cnt);
+  if (wmax == 0) return 0.0;
+  // rows of the warp are consecutive: the range starts at lane 0's first entry
+  const int32_t e0 = __shfl_sync(FULL, s0, 0);
+  const int32_t e1 = (int32_t)__reduce_max_sync(FULL, (unsigned)(valid ? e : 0));
+  const int32_t T = e1 - e0;
+  if (T > STAGE_CAP) return brow(rp, ci, va, x, row, valid, s_idle);
+  double* sva = reinterpret_cast<double*>(slice);
+  int32_t* sci = reinterpret_cast<int32_t*>(slice + STAGE_CAP * sizeof(double));
+  for (int32_t k = lane; k < T; k += 32) {
+    sci[k] = __ldg(ci + e0 + k);
+    sva[k] = __ldg(va + e0 + k);
+  }
+  __syncwarp();
+  const int32_t off = cnt > 0 ? s0 - e0 : 0;   // an empty or idle row reads (and ignores) entry 0
+  double acc = 0.0;
+  for (int32_t k0 = 0; k0 < wmax; k0 += 8) {
+    int32_t c[8];
+    double v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int32_t k = off + min(k0 + t, max(cnt, 1) - 1);
+      c[t] = sci[k];
+      v[t] = sva[k];
+    }
+    double xv[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) xv[t] = x[c[t]];
+    const int rem = wmax - k0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      if (t < rem) {
+        const double pr = fma(v[t], xv[t], acc);
+        acc = (k0 + t < cnt) ? pr : acc;
+      }
+    }
+  }
+  __syncwarp();   // the slice is refilled by the next group
+  return acc;
+}
+
 enum { U_INIT = 0, U_ITER = 1, U_RESTART = 2 };
 
 // CTA-uniform description of this member's share of one system.  It lives in shared
@@ -240,13 +295,14 @@ __device__ __noinline__ void phase_setup(const Env& e, const SysCtx& c, unsigned
 }
 
 // q = A p over the member's rows; returns this thread's share of p.q.
-__device__ __noinline__ double phase_spmv(const Env& e, const SysCtx& c) {
+__device__ __noinline__ double phase_spmv(const Env& e, const SysCtx& c, unsigned char* dsm) {
   double pq = 0.0;
   const int64_t rl = c.rl, rh = c.rh;
+  unsigned char* slice = dsm + (size_t)(threadIdx.x >> 5) * STAGE_BYTES;
   for (int64_t base = rl; base < rh; base += BT) {
     const int64_t row = base + threadIdx.x;
     const bool valid = row < rh;
-    const double qi = brow(c.rp, e.ci, e.va, c.p, row, valid, c.s_idle);
+    const double qi = brow_staged(c.rp, e.ci, e.va, c.p, row, valid, c.s_idle, slice);
     if (valid) {
       c.q[row] = qi;
       pq = fma(c.p[row], qi, pq);
@@ -256,13 +312,14 @@ __device__ __noinline__ double phase_spmv(const Env& e, const SysCtx& c) {
 }
 
 // t = b - A x over the member's rows, stored in r; returns this thread's share of t.t.
-__device__ __noinline__ double phase_true_residual(const Env& e, const SysCtx& c) {
+__device__ __noinline__ double phase_true_residual(const Env& e, const SysCtx& c, unsigned char* dsm) {
   double tt = 0.0;
   const int64_t rl = c.rl, rh = c.rh;
+  unsigned char* slice = dsm + (size_t)(threadIdx.x >> 5) * STAGE_BYTES;
   for (int64_t base = rl; base < rh; base += BT) {
     const int64_t row = base + threadIdx.x;
     const bool valid = row < rh;
-    const double ax = brow(c.rp, e.ci, e.va, c.x, row, valid, c.s_idle);
+    const double ax = brow_staged(c.rp, e.ci, e.va, c.x, row, valid, c.s_idle, slice);
     if (valid) {
       const double ti = __ldg(c.b + row) - ax;
       c.r[row] = ti;
@@ -378,7 +435,7 @@ __device__ __noinline__ void solve_system(const Env& e, const SysCtx& c, Team t,
           status = ST_BREAKDOWN;
           break;
         }
-        double pq[1] = {phase_spmv(e, c)};
+        double pq[1] = {phase_spmv(e, c, dsm)};
         prof_mark(e, PH_SPMV, last);
         const bool ok1 = team_allreduce<1>(e, t, pq, red, flag);
         prof_mark(e, PH_SYNC, last);
@@ -418,7 +475,7 @@ __device__ __noinline__ void solve_system(const Env& e, const SysCtx& c, Team t,
       // True residual t = b - A x (kept in r for a restart); also reported when the
       // iteration stopped without convergence.  Every exit from the loop above follows a
       // team barrier that came after the last x update, so the gathers of x are safe.
-      double tv[1] = {phase_true_residual(e, c)};
+      double tv[1] = {phase_true_residual(e, c, dsm)};
       prof_mark(e, PH_TRUE, last);
       const bool ok4 = team_allreduce<1>(e, t, tv, red, flag);
       prof_mark(e, PH_SYNC, last);
@@ -807,7 +864,8 @@ pc_status pc_batch_create(const pc_batch* B, int32_t prec, double pivot_tol, voi
   const int setup_kb = g_batch_setup_kb ? g_batch_setup_kb : (tu ? tu->setup_kb : 70);
   const int budget = setup_kb * 1024;
   int setup_warps = std::max(1, std::min(pc::BNW, budget / slot_bytes));
-  h->smem = setup_warps * slot_bytes;
+  // the same dynamic shared memory holds the setup slots, then the SpMV warp slices
+  h->smem = std::max(setup_warps * slot_bytes, pc::BNW * pc::STAGE_BYTES);
   const void* fn = h->fac_f32 ? (const void*)pc::batched_kernel<float> : (const void*)pc::batched_kernel<double>;
   PCB_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem));
   int occ = 0;
