@@ -116,6 +116,12 @@ int sm_count() {
   return sms > 0 ? sms : 1;
 }
 
+// Element stride of the CG work vectors inside one allocation: a multiple of 32 doubles, so
+// that every vector (and every 16-byte row window a bulk copy reads) starts 16-byte aligned
+// whatever n is.  The allocation is 4 strides + 64 doubles of padding (bulk copies of the
+// last rows round their size up to 16 bytes).
+int64_t vec_stride(int64_t n) { return (n + 31) & ~(int64_t)31; }
+
 // Per-device scratch for pc_dot.
 std::mutex g_mu;
 double* g_dot_scratch[64] = {nullptr};
@@ -332,7 +338,7 @@ static pc_status ensure_cg_workspace(pc_handle* h, cudaStream_t st) {
   h->part = nullptr;
   h->split = nullptr;
   pc_status s = PC_OK;
-  if (!h->cg) s = dalloc(&h->cg, sizeof(double) * (4 * (size_t)h->A.n + 64));
+  if (!h->cg) s = dalloc(&h->cg, sizeof(double) * (4 * (size_t)vec_stride(h->A.n) + 64));
   if (s == PC_OK && !h->res) s = dalloc(&h->res, sizeof(double) * 4);
   if (s == PC_OK && !h->ctl) s = dalloc(&h->ctl, sizeof(pc::GridSync) + sizeof(pc::PcgOut));
   if (s == PC_OK) s = dalloc(&h->part, sizeof(double) * 4 * (size_t)grid);   // 2 buffers x 2 values
@@ -379,8 +385,9 @@ static pc_status pcg_solve_graph(pc_handle* h, const double* b, double* x, doubl
                                  pc_solve_info* info, cudaStream_t st) {
   const int64_t n = h->A.n;
   pc_status s = PC_OK;
-  if (!h->cg) s = dalloc(&h->cg, sizeof(double) * (4 * (size_t)n + 64));   // padded: bulk copies round up
-  if (s == PC_OK && !h->gbx) s = dalloc(&h->gbx, sizeof(double) * 2 * (size_t)n);
+  const int64_t vs = vec_stride(n);
+  if (!h->cg) s = dalloc(&h->cg, sizeof(double) * (4 * (size_t)vs + 64));
+  if (s == PC_OK && !h->gbx) s = dalloc(&h->gbx, sizeof(double) * 2 * (size_t)vs);
   if (s == PC_OK && !h->gpart) s = dalloc(&h->gpart, sizeof(double) * (size_t)pc::cg_graph_partials());
   if (s == PC_OK && !h->gscal) s = dalloc(&h->gscal, pc::cg_scalars_bytes());
   if (s != PC_OK) return s;
@@ -390,7 +397,7 @@ static pc_status pcg_solve_graph(pc_handle* h, const double* b, double* x, doubl
       if (s != PC_OK) return s;
     }
     PC_TRY(pc::cg_graph_create(&h->graph, h->L, h->A.row_ptr, h->A.col_idx, h->A.val, h->val_f32, h->minv,
-                               h->fac_f32, h->gbx, h->gbx + n, h->cg, h->cg + n, h->cg + 2 * n, h->cg + 3 * n,
+                               h->fac_f32, h->gbx, h->gbx + vs, h->cg, h->cg + vs, h->cg + 2 * vs, h->cg + 3 * vs,
                                h->gpart, h->gscal, h->perm, h->gsplit, st));
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -398,11 +405,11 @@ static pc_status pcg_solve_graph(pc_handle* h, const double* b, double* x, doubl
   cudaError_t e = cudaEventCreate(&e1);
   if (e == cudaSuccess) e = cudaEventRecord(e0, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->gbx, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h->gbx + n, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->gbx + vs, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
   pc::CgResult res;
   memset(&res, 0, sizeof(res));
   if (e == cudaSuccess) e = pc::cg_graph_solve(h->graph, tol, max_iter, 3, h->val_f32, h->fac_f32, st, &res);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(x, h->gbx + n, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(x, h->gbx + vs, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaEventRecord(e1, st);
   if (e == cudaSuccess) e = cudaEventSynchronize(e1);
   float ms = 0.f;
@@ -449,9 +456,9 @@ pc_status pcg_solve_h(pc_handle* h, const double* b, double* x, double tol, int3
   a.b = b;
   a.x = x;
   a.r = h->cg;
-  a.z = h->cg + n;
-  a.p = h->cg + 2 * n;
-  a.q = h->cg + 3 * n;
+  a.z = h->cg + vec_stride(n);
+  a.p = h->cg + 2 * vec_stride(n);
+  a.q = h->cg + 3 * vec_stride(n);
   a.part = h->part;
   a.res = h->res;
   a.split = h->split;

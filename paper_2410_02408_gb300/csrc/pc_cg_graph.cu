@@ -522,6 +522,115 @@ __global__ void __launch_bounds__(256) cg_precond_tma_kernel(const CgArgs a, con
   cg_precond_epilogue<RESTART>(a, v[0], v[1], zero_b);
 }
 
+// Warp-pipelined preconditioner kernel: every warp owns a contiguous run of warp units and
+// streams each unit's M^{-1} block and its r and q rows into its own ring of NS shared-memory
+// stages with bulk asynchronous copies (one mbarrier per stage, lane 0 issues), NS units
+// ahead; the warp applies M^{-1} from shared memory.  Warps never wait for each other until
+// the final reduction.  All operands were written before this kernel started, so the copies
+// need no cross-proxy ordering.
+struct CgWarpPlan {
+  int ns;          // stages per warp
+  int stage;       // bytes per stage
+  int off_r;       // r rows within a stage
+  int off_q;       // q rows within a stage
+  int smem;        // dynamic shared memory per CTA
+  int64_t units;   // warp units in the matrix
+};
+constexpr int CGW_WARPS = 8;
+
+template <typename FT, int BS, bool RESTART>
+__global__ void __launch_bounds__(256) cg_precond_wp_kernel(const CgArgs a, const CgWarpPlan pl) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  __shared__ double sm[64];
+  __shared__ int is_last;
+  CgScalars* S = a.s;
+  if (*(volatile int*)&S->done) return;
+  const Layout& L = a.lay;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int64_t uM = unit_elems_minv(L);
+  const int64_t W = (int64_t)gridDim.x * CGW_WARPS;
+  const int64_t gw = (int64_t)blockIdx.x * CGW_WARPS + warp;
+  const int64_t u0 = pl.units * gw / W, u1 = pl.units * (gw + 1) / W;
+  const int64_t nu = u1 - u0;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(dsm) + warp * 8;               // up to 8 stages
+  unsigned char* ring = dsm + 128 * 4 + (size_t)warp * pl.ns * pl.stage;      // 512 B of barriers
+  const double alpha = RESTART ? 0.0 : S->alpha;
+  const bool zero_b = RESTART && S->bb == 0.0;
+  constexpr int NSLOT = (BS > 0 && BS <= 32) ? 1 : 2;
+  const int nslot = NSLOT == 1 ? 1 : L.S;
+  const uint32_t fb = (uint32_t)(uM * (int64_t)sizeof(FT));
+  auto issue = [&](int64_t i) {   // lane 0: unit u0 + i into stage i % ns
+    const int st = (int)(i % pl.ns);
+    const int64_t u = u0 + i;
+    const int64_t row0 = u * L.U;
+    const int64_t rows = min((int64_t)L.U, L.n - row0);
+    const uint32_t vb = (uint32_t)(((rows * 8) + 15) & ~(int64_t)15);   // vectors are padded by the caller
+    unsigned char* dst = ring + (size_t)st * pl.stage;
+    mbar_arrive_expect_tx(&mbar[st], fb + vb * (RESTART ? 1u : 2u));
+    bulk_g2s(dst, reinterpret_cast<const FT*>(a.minv) + u * uM, fb, &mbar[st]);
+    bulk_g2s(dst + pl.off_r, a.r + row0, vb, &mbar[st]);
+    if (!RESTART) bulk_g2s(dst + pl.off_q, a.q + row0, vb, &mbar[st]);
+  };
+  if (lane == 0) {
+    for (int st = 0; st < pl.ns; ++st) mbar_init(&mbar[st], 1);
+    mbar_fence_init();
+    for (int64_t i = 0; i < nu && i < pl.ns; ++i) issue(i);
+  }
+  __syncwarp();
+  double v0 = 0.0, v1 = 0.0;
+  for (int64_t i = 0; i < nu; ++i) {
+    const int st = (int)(i % pl.ns);
+    const uint32_t parity = (uint32_t)((i / pl.ns) & 1);
+    const bool ok = mbar_wait_bounded(&mbar[st], parity, 4000000000LL);
+    if (!__all_sync(FULL, ok)) {
+      if (lane == 0) {
+        atomicCAS(&S->status, ST_OK, ST_TIMEOUT);
+        for (int64_t t = i + 1; t < nu && t < i + pl.ns; ++t)
+          mbar_wait_bounded(&mbar[t % pl.ns], (uint32_t)((t / pl.ns) & 1), 4000000000LL);
+      }
+      break;   // this warp's partials stay short; the status reports the failure
+    }
+    const int64_t u = u0 + i;
+    const unsigned char* sbuf = ring + (size_t)st * pl.stage;
+    const double* sr = reinterpret_cast<const double*>(sbuf + pl.off_r);
+    const double* sq = reinterpret_cast<const double*>(sbuf + pl.off_q);
+    double rv[2] = {0.0, 0.0}, zv[2];
+    int64_t rows[2];
+    bool okr[2] = {false, false};
+#pragma unroll
+    for (int t = 0; t < NSLOT; ++t) {
+      if (t >= nslot) break;
+      bool vld;
+      const int rh = unit_row(L, lane, t, vld);
+      rows[t] = u * L.U + rh;
+      okr[t] = vld && rows[t] < L.n;
+      if (okr[t]) rv[t] = RESTART ? sr[rh] : fma(-alpha, sq[rh], sr[rh]);
+    }
+    unit_apply_inv<FT, BS, true>(L, reinterpret_cast<const FT*>(sbuf), lane, rv, zv);
+#pragma unroll
+    for (int t = 0; t < NSLOT; ++t) {
+      if (t >= nslot) break;
+      if (!okr[t]) continue;
+      if (zero_b) {
+        a.x[rows[t]] = 0.0;
+        continue;
+      }
+      if (!RESTART) a.r[rows[t]] = rv[t];
+      a.z[rows[t]] = zv[t];
+      if (RESTART) a.p[rows[t]] = zv[t];
+      v0 = fma(rv[t], zv[t], v0);
+      v1 = fma(rv[t], rv[t], v1);
+    }
+    __syncwarp();   // every lane is done with the stage before it is refilled
+    if (lane == 0 && i + pl.ns < nu) issue(i + pl.ns);
+  }
+  double v[2] = {v0, v1};
+  if (!cg_last_cta<2>(v, a.part, &S->cnt[1], sm, &is_last)) return;
+  if (threadIdx.x != 0) return;
+  cg_precond_epilogue<RESTART>(a, v[0], v[1], zero_b);
+}
+
 // C: x += alpha p (if due); p = z + beta p (if due).
 __global__ void __launch_bounds__(256) cg_update_kernel(const CgArgs a) {
   const CgScalars* S = a.s;
@@ -564,7 +673,28 @@ struct CgGraph {
   int g_spmv, g_prec, g_upd;
   bool tma;              // staged preconditioner kernel usable
   CgPrecondPlan pl;
+  bool wp;               // warp-pipelined preconditioner kernel usable
+  CgWarpPlan wpl;
 };
+
+// Plan of the warp-pipelined preconditioner: NS stages of one warp unit each per warp, as
+// deep as fits in about 110 KB per CTA.  Needs 16-byte aligned vector rows (U even).
+static CgWarpPlan warp_plan(const Layout& L, bool fac_f32, bool* usable) {
+  CgWarpPlan pl;
+  auto up = [](int64_t v, int64_t m) { return (v + m - 1) / m * m; };
+  const int64_t unit_bytes = unit_elems_minv(L) * (fac_f32 ? 4 : 8);
+  const int64_t vec = up((int64_t)L.U * 8 + 16, 128);
+  pl.off_r = (int)up(unit_bytes, 128);
+  pl.off_q = (int)(pl.off_r + vec);
+  pl.stage = (int)(pl.off_q + vec);
+  pl.units = L.n_units;
+  pl.ns = 4;
+  while (pl.ns > 2 && (int64_t)CGW_WARPS * pl.ns * pl.stage > 110 * 1024) --pl.ns;
+  pl.smem = 512 + CGW_WARPS * pl.ns * pl.stage;
+  const char* e = getenv("PC_PRECOND_WP");
+  *usable = (L.U % 2 == 0) && pl.smem <= 110 * 1024 + 512 && !(e && e[0] == '0');
+  return pl;
+}
 
 // Tile plan of the staged preconditioner kernel (about 24 KB per stage, 8 units per tile).
 static CgPrecondPlan precond_plan(const Layout& L, bool fac_f32, bool* usable) {
@@ -596,6 +726,13 @@ static CgPrecondPlan precond_plan(const Layout& L, bool fac_f32, bool* usable) {
 
 template <typename FT, int BS, bool RESTART>
 static cudaError_t launch_precond(cudaStream_t cs, const CgGraph* g) {
+  if (g->wp) {
+    cudaError_t e = cudaFuncSetAttribute(cg_precond_wp_kernel<FT, BS, RESTART>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, g->wpl.smem);
+    if (e != cudaSuccess) return e;
+    cg_precond_wp_kernel<FT, BS, RESTART><<<g->g_prec, 256, g->wpl.smem, cs>>>(g->args, g->wpl);
+    return cudaGetLastError();
+  }
   if (g->tma) {
     cudaError_t e = cudaFuncSetAttribute(cg_precond_tma_kernel<FT, BS, RESTART>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, g->pl.smem);
@@ -667,8 +804,16 @@ cudaError_t cg_graph_create(void** out, const Layout& L, const int32_t* rp, cons
   const int64_t n = L.n;
   g->g_spmv = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
   g->pl = precond_plan(L, fac_f32, &g->tma);
-  if (g->tma) g->g_prec = (int)std::min<int64_t>(g->pl.tiles, (int64_t)sms * std::max(1, (200 * 1024) / g->pl.smem));
-  else g->g_prec = (int)std::min<int64_t>((L.n_units + 7) / 8, (int64_t)sms * 8);
+  g->wpl = warp_plan(L, fac_f32, &g->wp);
+  if (g->wp) {
+    // one wave of resident CTAs, at most one CTA per 8 units
+    const int per_sm = std::max(1, std::min(8, (228 * 1024) / (g->wpl.smem + 1024)));
+    g->g_prec = (int)std::min<int64_t>((L.n_units + 7) / 8, (int64_t)sms * per_sm);
+  } else if (g->tma) {
+    g->g_prec = (int)std::min<int64_t>(g->pl.tiles, (int64_t)sms * std::max(1, (200 * 1024) / g->pl.smem));
+  } else {
+    g->g_prec = (int)std::min<int64_t>((L.n_units + 7) / 8, (int64_t)sms * 8);
+  }
   g->g_upd = (int)std::min<int64_t>((n + 1023) / 1024, (int64_t)sms * 8);
   if (g->g_spmv < 1) g->g_spmv = 1;
   if (g->g_prec < 1) g->g_prec = 1;

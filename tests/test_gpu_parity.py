@@ -233,6 +233,22 @@ def test_pcg_diffusion_fp64_matches_oracle(pc, engine, bs):
     assert res <= 1e-10
 
 
+@pytest.mark.parametrize("bs,prec", [(16, "fp64"), (16, "fp32"), (9, "fp64"), (9, "fp32"), (64, "fp32")])
+def test_pcg_odd_n_matches_oracle(pc, engine, bs, prec):
+    """n = 2197 (odd): the CG work vectors and every row window the preconditioner kernels
+    copy stay 16-byte aligned; bs 9 gives warp units of 27 rows (odd)."""
+    A = CASES["diff13_s2"]
+    b = W.rhs(A.n, 0)
+    x, info = pc.pcg(A, b, bs, tol=1e-10, prec=prec)
+    assert info["status"] == 0
+    res = np.linalg.norm(b - oracle.spmv(A, x.cpu().numpy())) / np.linalg.norm(b)
+    assert res <= 1e-10
+    if prec == "fp64":
+        o = oracle.pcg(A, b, bs, 1e-10)
+        assert abs(info["iterations"] - o["iterations"]) <= 2
+        assert rel(x.cpu().numpy(), o["x"]) <= 1e-10
+
+
 @pytest.mark.parametrize("bs", [8, 16, 32, 64])
 def test_pcg_diffusion_mixed_reaches_tolerance(pc, engine, bs):
     A = W.diffusion3d(24, 2.0)
