@@ -23,6 +23,14 @@ namespace pc {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// Streaming multiprocessors of the current device (host side; grid sizing).
+inline int device_sms() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
 enum : int {
   ST_OK = 0,
   ST_INVALID = 1,

@@ -148,7 +148,8 @@ __global__ void grad_edges_kernel(int64_t n_edges, const int32_t* __restrict__ e
 // ------------------------------------------------------------------ launchers
 static unsigned grid_for(int64_t work, int per) {
   int64_t g = (work + per - 1) / per;
-  if (g > 152 * 64) g = 152 * 64;
+  const int64_t gmax = (int64_t)device_sms() * 64;
+  if (g > gmax) g = gmax;
   if (g < 1) g = 1;
   return (unsigned)g;
 }

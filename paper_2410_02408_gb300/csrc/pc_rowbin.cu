@@ -185,7 +185,7 @@ cudaError_t row_bin_split(int64_t n, const int32_t* rp, const int32_t* perm, int
                           int64_t* scratch, cudaStream_t st) {
   const int64_t m = (n + 31) / 32;
   int64_t grid = (m * 32 + 255) / 256;
-  if (grid > 152 * 16) grid = 152 * 16;
+  if (grid > (int64_t)device_sms() * 16) grid = (int64_t)device_sms() * 16;
   if (grid < 1) grid = 1;
   group_cost_kernel<<<(unsigned)grid, 256, 0, st>>>(n, rp, perm, scratch);
   cost_scan_kernel<<<1, 1024, 0, st>>>(m, scratch);
@@ -195,7 +195,7 @@ cudaError_t row_bin_split(int64_t n, const int32_t* rp, const int32_t* perm, int
 
 cudaError_t row_bin_waste(int64_t n, const int32_t* rp, unsigned long long* d_out, cudaStream_t st) {
   int64_t grid = (n + 255) / 256;
-  if (grid > 152 * 16) grid = 152 * 16;
+  if (grid > (int64_t)device_sms() * 16) grid = (int64_t)device_sms() * 16;
   if (grid < 1) grid = 1;
   row_waste_kernel<<<(unsigned)grid, 256, 0, st>>>(n, rp, d_out);
   return cudaGetLastError();
@@ -203,7 +203,7 @@ cudaError_t row_bin_waste(int64_t n, const int32_t* rp, unsigned long long* d_ou
 
 cudaError_t row_bin_build(int64_t n, const int32_t* rp, int32_t* perm, cudaStream_t st) {
   const int64_t n_win = (n + ROWBIN_W - 1) / ROWBIN_W;
-  int64_t grid = n_win < 152 * 8 ? n_win : 152 * 8;
+  int64_t grid = n_win < (int64_t)device_sms() * 8 ? n_win : (int64_t)device_sms() * 8;
   if (grid < 1) grid = 1;
   row_bin_kernel<<<(unsigned)grid, ROWBIN_THREADS, 0, st>>>(n, rp, perm);
   return cudaGetLastError();
