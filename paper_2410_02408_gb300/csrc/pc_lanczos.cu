@@ -18,6 +18,18 @@ namespace pc {
 
 constexpr int LZ_TW = 32;
 
+// Ampere-style asynchronous 8-byte copy global -> shared (cache at all levels), with
+// commit / wait of this thread's groups.
+__device__ __forceinline__ void cp_async8(double* dst, const double* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 __global__ void __launch_bounds__(256) lz_sumsq_kernel(LanczosState s, const double* __restrict__ v) {
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < s.n; i += (int64_t)gridDim.x * blockDim.x)
@@ -93,8 +105,13 @@ __global__ void __launch_bounds__(256) lz_reorth_kernel(LanczosState s, int j) {
   // memory across all of the CTA's tiles and reduce across lanes once at the end: a warp
   // shuffle tree per tile would cost five FP64 adds per 32 products on the narrow FP64 pipe.
   constexpr bool COEF = MODE == 0 || MODE == 1;
-  double* Vs = dsm;                                  // nl * 32
-  double* acc = Vs + (need_tile ? nl * LZ_TW : 0);   // COEF: nl * 32 per-lane partials
+  // Shared memory: two tile buffers (the next tile streams in with cp.async while the current
+  // one is used), each nl rows of 32 basis values plus the 32 values of w; then the per-lane
+  // partials (COEF), the cross-warp sums and the updated w of the tile.
+  const int tile_elems = need_tile ? nl * LZ_TW + LZ_TW : LZ_TW;
+  double* buf0 = dsm;
+  double* buf1 = buf0 + tile_elems;
+  double* acc = buf1 + tile_elems;                   // COEF: nl * 32 per-lane partials
   double* red = acc + (COEF ? nl * LZ_TW : 0);       // 8 * 32
   double* wt = red + 8 * 32;                         // 32
   const int64_t n = s.n;
@@ -104,17 +121,44 @@ __global__ void __launch_bounds__(256) lz_reorth_kernel(LanczosState s, int j) {
   if (COEF)
     for (int i = tid; i < nl * LZ_TW; i += blockDim.x) acc[i] = 0.0;
   double nrm = 0.0;
-  for (int64_t t = blockIdx.x; t * LZ_TW < n; t += gridDim.x) {
-    const int64_t c0 = t * LZ_TW;
-    const int64_t col = c0 + lane;
-    __syncthreads();
-    if (need_tile)
-      for (int l = warp; l < nl; l += nwarp) Vs[l * LZ_TW + lane] = col < n ? s.V[(int64_t)l * n + col] : 0.0;
-    __syncthreads();
+  // Stage tile t (columns t*32 .. t*32+31) into buf: basis rows (warp-strided, one 8-byte
+  // element per lane) and w; columns past n are zero (plain stores).
+  auto stage = [&](int64_t t, double* buf) {
+    const int64_t col = t * LZ_TW + lane;
+    if (need_tile) {
+      for (int l = warp; l < nl; l += nwarp) {
+        double* dst = buf + l * LZ_TW + lane;
+        if (col < n) cp_async8(dst, s.V + (int64_t)l * n + col);
+        else *dst = 0.0;
+      }
+    }
+    if (warp == nwarp - 1) {
+      double* dst = buf + (need_tile ? nl * LZ_TW : 0) + lane;
+      if (col < n) cp_async8(dst, s.w + col);
+      else *dst = 0.0;
+    }
+    cp_async_commit();
+  };
+  int64_t t = blockIdx.x;
+  if (t * LZ_TW < n) stage(t, buf0);
+  for (int k = 0; t * LZ_TW < n; t += gridDim.x, ++k) {
+    double* cur = (k & 1) ? buf1 : buf0;
+    double* nxt = (k & 1) ? buf0 : buf1;
+    const bool more = (t + gridDim.x) * LZ_TW < n;
+    if (more) {
+      stage(t + gridDim.x, nxt);
+      cp_async_wait<1>();   // this thread's copies of the current tile have landed
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();      // everyone's copies of the current tile are visible
+    const double* Vs = cur;
+    const double* wsrc = cur + (need_tile ? nl * LZ_TW : 0);
+    const int64_t col = t * LZ_TW + lane;
     if (MODE == 0 || MODE == 3) {
       if (tid < LZ_TW) {
         const double qv = MODE == 0 ? Vs[j * LZ_TW + tid] : (col < n ? qj[col] : 0.0);
-        const double w = col < n ? fma(-aj, qv, s.w[col]) : 0.0;
+        const double w = col < n ? fma(-aj, qv, wsrc[tid]) : 0.0;
         wt[tid] = w;
         if (col < n) s.w[col] = w;
       }
@@ -126,7 +170,7 @@ __global__ void __launch_bounds__(256) lz_reorth_kernel(LanczosState s, int j) {
       if (tid < LZ_TW) {
         double sum = 0.0;
         for (int q = 0; q < nwarp; ++q) sum += red[q * LZ_TW + tid];
-        const double w = col < n ? s.w[col] - sum : 0.0;
+        const double w = col < n ? wsrc[tid] - sum : 0.0;
         wt[tid] = w;
         if (col < n) s.w[col] = w;
       }
@@ -138,6 +182,7 @@ __global__ void __launch_bounds__(256) lz_reorth_kernel(LanczosState s, int j) {
     } else if (tid < LZ_TW) {
       nrm = fma(wt[tid], wt[tid], nrm);
     }
+    __syncthreads();      // the current buffer is refilled two tiles later
   }
   __syncthreads();
   const int m = s.m;
@@ -243,7 +288,8 @@ int lanczos_grid() {
 }
 
 static size_t reorth_smem(int nl, bool tile, bool coef) {
-  return sizeof(double) * ((tile ? nl * LZ_TW : 0) + (coef ? nl * LZ_TW : 0) + 8 * 32 + 32);
+  const size_t tile_elems = tile ? (size_t)nl * LZ_TW + LZ_TW : LZ_TW;
+  return sizeof(double) * (2 * tile_elems + (coef ? (size_t)nl * LZ_TW : 0) + 8 * 32 + 32);
 }
 
 cudaError_t lanczos_init(const LanczosState& s, const double* v0, bool precond, const Layout& L, const void* linv,
