@@ -4,7 +4,14 @@ sigma = 2, b ~ N(0,1) seed 0), mixed precision (FP32 block factors, FP64 CG) aga
 all-FP64.
 
 One step = pcg_solve through the C ABI: block extraction + batched block Cholesky/inverse
-(setup) and the persistent CG solve to ||r||/||b|| <= 1e-10 with the true-residual check.
+(setup) and the CG solve (a CUDA graph with a device-driven loop) to ||r||/||b|| <= 1e-10
+with the true-residual check.  The line also carries the per-kernel breakdown, the roofline
+of the dominant kernel (the SpMV), the FP64-factor comparison, the Lanczos kappa estimates
+before and after preconditioning, the end-to-end figure and the oracle's CPU baseline.
+
+Other workloads (each prints its own line): --workload batched_rgg_512 (512 uneven RGG
+systems set up and solved in one persistent launch) and --workload powerlaw_8m (random SPD
+with power-law rows, FP32 values).
 
 value   = algorithmic bytes of the step / step time (GB/s), inputs resident in HBM.
           bytes = setup (CSR read + factor writes) + per-solve extras (initial and final

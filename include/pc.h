@@ -88,7 +88,7 @@ typedef struct {
   double true_rel_residual;  /* ||b - A x|| / ||b|| recomputed at exit                */
   double setup_ms;           /* pc_setup time inside pcg_solve (0 for pcg_solve_h)    */
   double solve_ms;           /* CG kernel time (CUDA events on the stream)            */
-  int32_t grid_ctas;         /* CTAs of the persistent CG launch                      */
+  int32_t grid_ctas;         /* CTAs of the persistent CG launch (0: graph engine)     */
   int32_t block_size;
   int32_t prec;              /* pc_prec used                                          */
   int32_t reserved;
@@ -173,8 +173,12 @@ pc_status kappa_estimate_h(pc_handle *h, const pc_csr *A, int32_t max_steps, dou
 /* ---------------------------------------------------------------------------------
  * pcg_solve - solve A x = b by block-Jacobi preconditioned CG until the recurrence
  * residual satisfies ||r|| <= tol ||b|| (Sec. 3.7), then recompute b - A x; if that is
- * above tol, restart from x (at most 3 times).  The whole iteration runs in one
- * persistent cooperative kernel (two reductions and one plain grid barrier per step).
+ * above tol, restart from x (at most 3 times).  Default engine: a CUDA graph whose device-
+ * driven `while` node runs three kernels per iteration (q = A p with p.q; r update,
+ * z = M^{-1} r with r.z and r.r; x and p updates) until the last kernel's last CTA clears the
+ * loop condition, with the host out of the loop; the alternative (pc_set_cg_engine(1)) is one
+ * persistent cooperative kernel with two reductions and one plain grid barrier per step.
+ * Both use fixed-order reductions (bit-reproducible for a given device).
  *   x    device [n]: in = initial guess x0, out = solution (last iterate on failure).
  *   prec pc_prec of the preconditioner; CG itself is FP64.
  * pcg_solve builds (and frees) the preconditioner; pcg_solve_h reuses a handle. */
@@ -184,8 +188,9 @@ pc_status pcg_solve(const pc_csr *A, int32_t block_size, const double *b, double
 pc_status pcg_solve_h(pc_handle *h, const double *b, double *x, double tol, int32_t max_iter,
                       pc_solve_info *info, void *stream);
 
-/* pcg_solve_noalloc - the same solve as pcg_solve (same kernels, same results), for
- * callers that cannot allocate device memory.  The paper has no counterpart; this is a
+/* pcg_solve_noalloc - the same solve as pcg_solve with the persistent engine
+ * (pc_set_cg_engine(1): same kernels, same results), for callers that cannot allocate
+ * device memory.  The paper has no counterpart; this is a
  * deployment variant.  Examples of such callers: code that runs while a stream is being
  * captured into a CUDA graph (cudaMalloc/cudaFree are not stream-ordered and cudaFree
  * synchronises the device), plug-ins hosted by a framework whose caching allocator owns
