@@ -195,3 +195,26 @@ def test_batched_autotune_records_a_shape(pc, small_batch):
     finally:
         H.destroy()
         pc.binding.lib().pc_batch_clear_tuned()
+
+
+def test_batched_team_wait_timeout_reports_and_recovers(pc, small_batch):
+    """A 1-cycle wait budget makes the team barriers give up: the launch ends with
+    PC_ERR_TIMEOUT instead of hanging, and a handle created afterwards solves normally."""
+    import os
+
+    batch = small_batch
+    b = _rhs(batch, 5)
+    pc.batch_set_tuning(0, 8, 64.0)          # force multi-CTA teams
+    os.environ["PC_WAIT_BUDGET"] = "1"
+    try:
+        H = pc.Batch(batch)
+        team, _ = H.teams()
+        assert team.max() > 1
+        x, per, info = H.solve(b, 1e-10, check=False)
+        H.destroy()
+    finally:
+        del os.environ["PC_WAIT_BUDGET"]
+        pc.batch_set_tuning(0, 0, 0.0)
+    assert info["status_name"] == "timeout"
+    x, per, info = pc.pcg_batched(batch, b, tol=1e-10)
+    assert info["status_name"] == "ok" and np.all(per["relres"] <= 1e-10)
