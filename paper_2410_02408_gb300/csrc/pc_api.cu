@@ -28,7 +28,6 @@ struct pc_handle {
   // CG workspace (allocated on first solve)
   double* cg;            // r, z, p, q: 4 n
   double* part;          // grid * 2
-  double* res;           // 2
   int64_t* split;        // grid + 1
   unsigned char* ctl;    // GridSync + PcgOut
   int grid;
@@ -164,7 +163,6 @@ pc_status pc_destroy(pc_handle* h) {
   dfree(h->failed_d);
   dfree(h->cg);
   dfree(h->part);
-  dfree(h->res);
   dfree(h->split);
   dfree(h->ctl);
   dfree(h->trace_d);
@@ -339,7 +337,6 @@ static pc_status ensure_cg_workspace(pc_handle* h, cudaStream_t st) {
   h->split = nullptr;
   pc_status s = PC_OK;
   if (!h->cg) s = dalloc(&h->cg, sizeof(double) * (4 * (size_t)vec_stride(h->A.n) + 64));
-  if (s == PC_OK && !h->res) s = dalloc(&h->res, sizeof(double) * 4);
   if (s == PC_OK && !h->ctl) s = dalloc(&h->ctl, sizeof(pc::GridSync) + sizeof(pc::PcgOut));
   if (s == PC_OK) s = dalloc(&h->part, sizeof(double) * 4 * (size_t)grid);   // 2 buffers x 2 values
   if (s == PC_OK) s = dalloc(&h->split, sizeof(int64_t) * (size_t)(grid + 1));
@@ -460,7 +457,6 @@ pc_status pcg_solve_h(pc_handle* h, const double* b, double* x, double tol, int3
   a.p = h->cg + 2 * vec_stride(n);
   a.q = h->cg + 3 * vec_stride(n);
   a.part = h->part;
-  a.res = h->res;
   a.split = h->split;
   a.gs = reinterpret_cast<pc::GridSync*>(h->ctl);
   a.out = reinterpret_cast<pc::PcgOut*>(h->ctl + sizeof(pc::GridSync));

@@ -691,8 +691,7 @@ static CgWarpPlan warp_plan(const Layout& L, bool fac_f32, bool* usable) {
   pl.ns = 4;
   while (pl.ns > 2 && (int64_t)CGW_WARPS * pl.ns * pl.stage > 110 * 1024) --pl.ns;
   pl.smem = 512 + CGW_WARPS * pl.ns * pl.stage;
-  const char* e = getenv("PC_PRECOND_WP");
-  *usable = (L.U % 2 == 0) && pl.smem <= 110 * 1024 + 512 && !(e && e[0] == '0');
+  *usable = (L.U % 2 == 0) && pl.smem <= 110 * 1024 + 512;
   return pl;
 }
 

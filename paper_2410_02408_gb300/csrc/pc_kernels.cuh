@@ -76,7 +76,6 @@ struct PcgArgs {
   double* p;
   double* q;
   double* part;          // 2 * gridDim * 2 doubles (double-buffered per-CTA partials)
-  double* res;           // unused
   const int64_t* split;  // gridDim + 1 SpMV row boundaries
   GridSync* gs;
   PcgOut* out;

@@ -95,10 +95,9 @@ extern "C" pc_status pcg_solve_noalloc(const pc_csr* A, int32_t block_size, cons
   const size_t sz_fail = 256;
   const size_t sz_vec = round256(sizeof(double) * 4 * n);
   const size_t sz_part = round256(sizeof(double) * 4 * (size_t)grid);
-  const size_t sz_res = 256;
   const size_t sz_split = round256(sizeof(int64_t) * (size_t)(grid + 1));
   const size_t sz_ctl = round256(sizeof(pc::GridSync) + sizeof(pc::PcgOut));
-  const size_t total = sz_minv + sz_linv + sz_fail + sz_vec + sz_part + sz_res + sz_split + sz_ctl;
+  const size_t total = sz_minv + sz_linv + sz_fail + sz_vec + sz_part + sz_split + sz_ctl;
   if (total > kScratchBytes) return PC_ERR_INVALID_ARG;
 
   unsigned char* base = nullptr;
@@ -115,8 +114,6 @@ extern "C" pc_status pcg_solve_noalloc(const pc_csr* A, int32_t block_size, cons
   cur += sz_vec;
   double* part = reinterpret_cast<double*>(cur);
   cur += sz_part;
-  double* res = reinterpret_cast<double*>(cur);
-  cur += sz_res;
   int64_t* split = reinterpret_cast<int64_t*>(cur);
   cur += sz_split;
   unsigned char* ctl = cur;
@@ -159,7 +156,6 @@ extern "C" pc_status pcg_solve_noalloc(const pc_csr* A, int32_t block_size, cons
   a.p = vec + 2 * n;
   a.q = vec + 3 * n;
   a.part = part;
-  a.res = res;
   a.split = split;
   a.gs = reinterpret_cast<pc::GridSync*>(ctl);
   a.out = reinterpret_cast<pc::PcgOut*>(ctl + sizeof(pc::GridSync));
