@@ -70,6 +70,7 @@ def parse():
                          "rows (N = 8M, ~256M nnz, FP32 values, bs 32)")
     ap.add_argument("--pl-n", type=int, default=8_000_000, help="rows of the power-law workload")
     ap.add_argument("--no-kappa", action="store_true", help="skip the Lanczos kappa timing")
+    ap.add_argument("--no-bs-sweep", action="store_true", help="skip the block-size sweep (8/16/32/64)")
     ap.add_argument("--row-binning", default="auto", choices=["auto", "on", "off"],
                     help="row order of the CG SpMV (auto: binned by length when rows are irregular)")
     ap.add_argument("--n-sys", type=int, default=512, help="systems in the batched workload")
@@ -480,6 +481,29 @@ def run_ours(args):
 
     if rank == 0 and not args.no_kappa:
         line["kappa"] = kappa_timing(pc, Ad, bd, args.bs, n, nnz, vb)
+
+    if rank == 0 and not args.no_bs_sweep and args.workload == "diffusion3d":
+        # one timed setup+solve per block size and precision (after one untimed solve)
+        sweep = {}
+        for bsz in (8, 16, 32, 64):
+            row = {}
+            for prec in ("fp32", "fp64"):
+                pc.pcg(Ad, bd, bsz, tol=args.tol, max_iter=args.maxit, prec=prec)
+                torch.cuda.synchronize()
+                t0 = torch.cuda.Event(enable_timing=True)
+                t1 = torch.cuda.Event(enable_timing=True)
+                t0.record(st)
+                _, si = pc.pcg(Ad, bd, bsz, tol=args.tol, max_iter=args.maxit, prec=prec)
+                t1.record(st)
+                torch.cuda.synchronize()
+                sms = t0.elapsed_time(t1)
+                sb = step_bytes(n, nnz, bsz, prec, si["iterations"], vb)[0]
+                row["mixed" if prec == "fp32" else "fp64"] = {
+                    "ms": sms, "iterations": si["iterations"], "GBs": sb / (sms / 1e3) / 1e9,
+                    "true_rel_residual": si["true_rel_residual"]}
+            row["mixed_speedup_vs_fp64"] = row["fp64"]["ms"] / row["mixed"]["ms"]
+            sweep[str(bsz)] = row
+        line["bs_sweep"] = sweep
 
     if not args.no_e2e:
         # end to end through the C ABI from pinned host buffers
