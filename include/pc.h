@@ -125,6 +125,11 @@ pc_status pc_setup(const pc_csr *A, int32_t block_size, double tol, int32_t prec
 /* First failing block of the last pc_setup on h (-1 if none). */
 int64_t pc_handle_failed_block(const pc_handle *h);
 
+/* 1 if the handle was created with FP32/TF32 factors and an FP32 pivot broke down, so that
+ * pc_setup factored every block again in FP64 arithmetic (the stored factors stay FP32);
+ * NOT_SPD is reported only if that FP64 factorisation fails too.  0 otherwise. */
+int32_t pc_handle_refactored_fp64(const pc_handle *h);
+
 /* pc_apply - out = op(in) for op in pc_apply_mode; in and out are device [n] doubles and
  * must not overlap.  Stream-ordered, does not synchronise. */
 pc_status pc_apply(pc_handle *h, int32_t mode, const double *in, double *out, void *stream);

@@ -112,6 +112,7 @@ def lib():
         "pc_set_ctas_per_sm": (None, [_I32]),
         "pc_set_cg_engine": (None, [_I32]),
         "pc_set_row_binning": (None, [_I32]),
+        "pc_handle_refactored_fp64": (_I32, [_P]),
         "pc_handle_row_binned": (_I32, [_P]),
         "pc_status_string": (ctypes.c_char_p, [_I32]),
         "pc_version": (_I32, []),
@@ -251,6 +252,10 @@ class Handle:
 
     def kappa(self, v0, max_steps: int = 200, tol: float = 1e-12, reorth: bool = True):
         return _kappa(self._h, self.A, v0, max_steps, tol, reorth)
+
+    def refactored_fp64(self) -> bool:
+        """True if an FP32 breakdown made pc_setup factor the blocks in FP64 arithmetic."""
+        return bool(lib().pc_handle_refactored_fp64(self._h))
 
     def row_binned(self) -> bool:
         """True if this handle's CG SpMV runs rows binned by length."""

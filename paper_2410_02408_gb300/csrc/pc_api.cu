@@ -12,6 +12,11 @@
 
 using pc::Layout;
 
+namespace pc {
+// pc_setup.cu: FP64 arithmetic with FP32 stored factors (fallback of the FP32 setup).
+cudaError_t launch_setup_f64_store_f32(const SetupArgs& a, bool val_f32, cudaStream_t st);
+}  // namespace pc
+
 struct pc_handle {
   pc_csr A;
   int32_t bs;
@@ -25,6 +30,7 @@ struct pc_handle {
   double* tmp;
   unsigned long long* failed_d;
   int64_t failed_block;
+  int refactored_fp64;   // FP32 factors recomputed in FP64 arithmetic after an FP32 breakdown
   // CG workspace (allocated on first solve)
   double* cg;            // r, z, p, q: 4 n
   double* part;          // grid * 2
@@ -194,6 +200,8 @@ int32_t pc_get_trace(const pc_handle* h, int64_t* out, int32_t max_entries) {
 
 int64_t pc_handle_failed_block(const pc_handle* h) { return h ? h->failed_block : -1; }
 
+int32_t pc_handle_refactored_fp64(const pc_handle* h) { return h ? h->refactored_fp64 : 0; }
+
 pc_status pc_setup(const pc_csr* A, int32_t block_size, double tol, int32_t prec, void* stream, pc_handle** out) {
   if (!out) return PC_ERR_INVALID_ARG;
   *out = nullptr;
@@ -233,6 +241,15 @@ pc_status pc_setup(const pc_csr* A, int32_t block_size, double tol, int32_t prec
   unsigned long long failed = ~0ull;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&failed, h->failed_d, sizeof(failed), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && failed != ~0ull && h->fac_f32) {
+    // An FP32 pivot broke down: factor every block again in FP64 arithmetic (stored as FP32)
+    // and report NOT_SPD only if that fails too.
+    e = cudaMemsetAsync(h->failed_d, 0xff, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = pc::launch_setup_f64_store_f32(a, h->val_f32, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&failed, h->failed_d, sizeof(failed), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    h->refactored_fp64 = 1;
+  }
   if (e != cudaSuccess) {
     pc_destroy(h);
     return from_cuda(e);

@@ -290,7 +290,7 @@ __device__ __noinline__ void phase_setup(const Env& e, const SysCtx& c, unsigned
   FT* Mf = reinterpret_cast<FT*>(const_cast<void*>(c.Mf));
   const int64_t uM = unit_elems_minv(L);
   for (int64_t u = c.u0 + warp; u < c.u1; u += nw)
-    setup_unit<double, FT>(L, u, c.rp, e.ci, e.va, e.pivot_tol, Mf + u * uM, nullptr, As, Xs, threadIdx.x & 31,
+    setup_unit<double, FT, FT>(L, u, c.rp, e.ci, e.va, e.pivot_tol, Mf + u * uM, nullptr, As, Xs, threadIdx.x & 31,
                            &e.fail[c.s]);
 }
 

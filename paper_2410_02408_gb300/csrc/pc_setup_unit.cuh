@@ -23,11 +23,13 @@ __host__ __device__ inline size_t setup_unit_smem(const Layout& L, size_t ft_byt
 // are relative to the same origin as the rows.  Mu (and Lu unless null) point at this
 // unit's slots of the factor arrays.  A pivot <= tol * (largest diagonal entry of its
 // block) makes the block count as failed: atomicMin(failed, block index); the pivot is
-// then replaced by 1 so that the factor stays finite.
-template <typename VT, typename FT>
+// then replaced by 1 so that the factor stays finite.  FT is the arithmetic type (and the
+// type of the shared-memory tiles), ST the stored type (FP64 arithmetic can be stored as
+// FP32 factors).
+template <typename VT, typename FT, typename ST = FT>
 __device__ __forceinline__ void setup_unit(const Layout& L, int64_t u, const int32_t* __restrict__ rp,
                                            const int32_t* __restrict__ ci, const VT* __restrict__ va, double tol,
-                                           FT* __restrict__ Mu, FT* __restrict__ Lu, FT* As, FT* Xs, int lane,
+                                           ST* __restrict__ Mu, ST* __restrict__ Lu, FT* As, FT* Xs, int lane,
                                            unsigned long long* failed) {
   const int bs = L.bs;
   const int ld = bs + 1;
@@ -131,12 +133,12 @@ __device__ __forceinline__ void setup_unit(const Layout& L, int64_t u, const int
         const int m0 = i > j ? i : j;
         for (int m = m0; m < bs; ++m) acc = fma(Xs[(gb + m) * ld + i], Xs[(gb + m) * ld + j], acc);
       }
-      Mu[(k * L.S + s) * 32 + lane] = acc;
+      Mu[(k * L.S + s) * 32 + lane] = (ST)acc;
     }
     if (Lu) {
       for (int k = 0; k < bs; ++k) {
         const FT v = (valid && i >= k) ? Xs[rho * ld + (i - k)] : FT(0);
-        Lu[(k * L.S + s) * 32 + lane] = v;
+        Lu[(k * L.S + s) * 32 + lane] = (ST)v;
       }
     }
   }

@@ -335,3 +335,41 @@ def test_grad_val_matches_oracle(pc):
     x = W.rhs(A.n, 8)
     g = pc.grad_val(A, lam, x).cpu().numpy()
     assert np.array_equal(g, oracle.grad_val(A, lam, x))
+
+
+def _pair_blocks(nb, eps, bad=None):
+    """Block-diagonal matrix of nb 2x2 blocks [[1, 1-eps], [1-eps, 1]] (block `bad`, if given,
+    gets off-diagonals 2: indefinite)."""
+    rows, cols, vals = [], [], []
+    for k in range(nb):
+        off = 2.0 if k == bad else 1.0 - eps
+        for i in range(2):
+            for j in range(2):
+                rows.append(2 * k + i)
+                cols.append(2 * k + j)
+                vals.append(1.0 if i == j else off)
+    n = 2 * nb
+    row_ptr = np.zeros(n + 1, dtype=np.int32)
+    np.cumsum(np.bincount(np.array(rows), minlength=n), out=row_ptr[1:])
+    return W.CSR(row_ptr, np.array(cols, dtype=np.int32), np.array(vals))
+
+
+def test_fp32_breakdown_refactors_in_fp64(pc):
+    """1 - 1e-9 rounds to 1 in FP32, so the FP32 Cholesky of every block hits a zero pivot;
+    pc_setup then factors the blocks in FP64 arithmetic and stores FP32 factors."""
+    A = _pair_blocks(40, 1e-9)
+    H = pc.setup(A, 2, prec="fp32")
+    try:
+        assert H.refactored_fp64()
+        m = H.factor("minv").cpu().numpy()
+    finally:
+        H.destroy()
+    ref = np.linalg.inv(np.array([[1.0, 1.0 - 1e-9], [1.0 - 1e-9, 1.0]]))
+    for k in range(40):
+        assert np.linalg.norm(m[k] - ref) <= 1e-6 * np.linalg.norm(ref)
+    H64 = pc.setup(A, 2, prec="fp64")
+    assert not H64.refactored_fp64()
+    H64.destroy()
+    with pytest.raises(pc.PcError) as ei:
+        pc.setup(_pair_blocks(40, 1e-9, bad=7), 2, prec="fp32")
+    assert ei.value.name == "not_spd"
