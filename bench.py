@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--no-bs-sweep", action="store_true", help="skip the block-size sweep (8/16/32/64)")
     ap.add_argument("--row-binning", default="auto", choices=["auto", "on", "off"],
                     help="row order of the CG SpMV (auto: binned by length when rows are irregular)")
+    ap.add_argument("--col-segments", default="auto",
+                    help="column segments of the binned SpMV: auto (by the size of x) or 1..8")
     ap.add_argument("--n-sys", type=int, default=512, help="systems in the batched workload")
     ap.add_argument("--no-tune", action="store_true", help="batched workload: skip the launch-shape autotuner")
     ap.add_argument("--tune-trials", type=int, default=0, help="batched autotuner candidates (0 = all)")
@@ -99,6 +101,7 @@ def run_profile(args):
 
     pc.load()
     pc.set_row_binning(args.row_binning)
+    pc.set_col_segments(args.col_segments)
     if args.ctas_per_sm:
         pc.set_ctas_per_sm(args.ctas_per_sm)
     A, _, bs = single_workload(args)
@@ -363,6 +366,7 @@ def run_ours(args):
 
     pc.load()
     pc.set_row_binning(args.row_binning)
+    pc.set_col_segments(args.col_segments)
     if args.ctas_per_sm:
         pc.set_ctas_per_sm(args.ctas_per_sm)
     A, wname, bs = single_workload(args)
@@ -413,6 +417,7 @@ def run_ours(args):
     hp = pc.setup(Ad, args.bs, prec=args.prec)
     hp.pcg(bd, tol=args.tol, max_iter=args.maxit)
     kt = hp.trace(8)
+    spmv_order = {"binned": hp.row_binned(), "col_segments": hp.col_segments()}
     hp.destroy()
     del os.environ["PC_CG_PROFILE"]
     spmv_us, prec_us, upd_us = (float(kt[0]) / 1e3, float(kt[1]) / 1e3, float(kt[2]) / 1e3) if len(kt) >= 3 else (0.0, 0.0, 0.0)
@@ -435,8 +440,11 @@ def run_ours(args):
                    "bytes": upd_bytes},
         "note": "profiling-mode launches (events around each kernel), includes per-launch overhead",
     }
-    # launches of this library's kernels per step: setup; per round I1, I2, arm, T; 3 per iteration
-    launches = sum(1 + 4 * (i["restarts"] + 1) + 3 * i["iterations"] for i in infos)
+    # launches of this library's kernels per step: setup; the row-length statistic (auto row
+    # order) and, when binned, the binning, cost split (3) and segment bounds; per round I1,
+    # I2, arm, T; 3 per iteration
+    order_launches = (1 if args.row_binning == "auto" else 0) + (5 if spmv_order["binned"] else 0)
+    launches = sum(1 + order_launches + 4 * (i["restarts"] + 1) + 3 * i["iterations"] for i in infos)
     xr = x.cpu().numpy()
     true_res = float(np.linalg.norm(b - A.to_scipy() @ xr) / np.linalg.norm(b))   # report only
 
@@ -455,6 +463,7 @@ def run_ours(args):
         "frac_of_hbm_peak": value / peak,
         "roofline": roofline,
         "kernels": kernels,
+        "spmv_order": spmv_order,
         "gpu_launches": launches,
     }
     line["clocks"] = clk.summary()

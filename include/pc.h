@@ -389,6 +389,20 @@ void pc_set_row_binning(int32_t mode);
 /* 1 if the handle's CG SpMV uses the binned row order, else 0. */
 int32_t pc_handle_row_binned(const pc_handle *h);
 
+/* Column segments of the binned CG SpMV.  The binned SpMV sweeps its rows once per segment
+ * of columns [s * ceil(n/S), (s+1) * ceil(n/S)), each sweep gathering only that part of x
+ * (so that it stays in L2 while the matrix streams), and adds the sweeps' partial sums in
+ * order.  segs -1 (default): S = 1 (on an 8M-row power-law matrix every S > 1 measured
+ * slower: the extra sweeps cost more dependent load rounds than the L2 hits save); 1..8:
+ * exactly that many.
+ * Workspace: 4 (S + 1) bytes per row, plus 8 per row when S > 1.  Segments need sorted
+ * column indices; a matrix whose rows are not strictly increasing is swept whole (S = 1).
+ * Applies to binned handles that have not solved yet.  Process-wide. */
+void pc_set_col_segments(int32_t segs);
+
+/* Column segments of the handle's binned CG SpMV (1 if unsegmented or not binned). */
+int32_t pc_handle_col_segments(const pc_handle *h);
+
 /* Phase trace of the last pcg_solve_h on h, when the environment variable
  * PC_TRACE_BARRIERS=N (N > 0) was set for that solve: out[0] is the device globaltimer (ns)
  * at kernel start and out[k] the time after the k-th grid-wide synchronisation (entries

@@ -112,6 +112,8 @@ def lib():
         "pc_set_ctas_per_sm": (None, [_I32]),
         "pc_set_cg_engine": (None, [_I32]),
         "pc_set_row_binning": (None, [_I32]),
+        "pc_set_col_segments": (None, [_I32]),
+        "pc_handle_col_segments": (_I32, [_P]),
         "pc_handle_refactored_fp64": (_I32, [_P]),
         "pc_handle_row_binned": (_I32, [_P]),
         "pc_status_string": (ctypes.c_char_p, [_I32]),
@@ -260,6 +262,10 @@ class Handle:
     def row_binned(self) -> bool:
         """True if this handle's CG SpMV runs rows binned by length."""
         return bool(lib().pc_handle_row_binned(self._h))
+
+    def col_segments(self) -> int:
+        """Column segments swept by this handle's binned CG SpMV (1: whole rows)."""
+        return int(lib().pc_handle_col_segments(self._h))
 
     def trace(self, max_entries: int = 4096) -> np.ndarray:
         """Barrier timestamps (ns) of the last solve when PC_TRACE_BARRIERS was set."""
@@ -514,6 +520,11 @@ def set_ctas_per_sm(ctas: int):
 def set_row_binning(mode: str):
     """"auto" (default), "off" or "on": row order of the CG SpMV (see pc_set_row_binning)."""
     lib().pc_set_row_binning({"off": 0, "on": 1}.get(mode, -1))
+
+
+def set_col_segments(segs):
+    """"auto" (default) or 1..8: column segments of the binned CG SpMV (see pc_set_col_segments)."""
+    lib().pc_set_col_segments(-1 if segs in (None, "auto") else int(segs))
 
 
 def set_cg_engine(engine: str):

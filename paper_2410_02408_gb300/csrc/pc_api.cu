@@ -45,6 +45,11 @@ struct pc_handle {
   double* gbx;           // copies of b and x: 2 n
   int32_t* perm;         // SpMV row order for irregular row lengths (null: natural order)
   int32_t* gsplit;       // with perm: each SpMV warp's first 32-row group (balanced runs)
+  int32_t* gmax;         // with perm: longest row of each 32-row group
+  int32_t* bnd;          // with perm: column-segment entry boundaries by binned position
+  double* spart;         // with nseg > 1: partial sums between segment sweeps
+  int32_t nseg;          // column segments of the binned SpMV
+  int32_t bin_pipe;      // the binned SpMV uses the pipelined row loop
   int perm_checked;      // the row-length statistics have been taken
   double* gpart;         // per-CTA partials
   void* gscal;           // CG scalars
@@ -58,6 +63,7 @@ long long g_budget = 0;          // 0 = default
 int g_ctas_per_sm = 0;           // 0 = occupancy maximum
 int g_engine = -1;               // -1: from PC_CG_ENGINE (default graph); 0 graph; 1 persistent
 int g_row_binning = -1;          // -1: decided per matrix; 0 off; 1 on
+int g_col_segments = -1;         // -1: default (1); 1..8 forced
 
 int cg_engine() {
   if (g_engine >= 0) return g_engine;
@@ -147,6 +153,10 @@ void pc_set_row_binning(int32_t mode) { g_row_binning = (mode == 0 || mode == 1)
 
 int32_t pc_handle_row_binned(const pc_handle* h) { return h && h->perm ? 1 : 0; }
 
+void pc_set_col_segments(int32_t segs) { g_col_segments = (segs >= 1 && segs <= 8) ? segs : -1; }
+
+int32_t pc_handle_col_segments(const pc_handle* h) { return h && h->perm ? h->nseg : 1; }
+
 const char* pc_status_string(int32_t s) {
   switch (s) {
     case PC_OK: return "ok";
@@ -176,6 +186,9 @@ pc_status pc_destroy(pc_handle* h) {
   dfree(h->gbx);
   dfree(h->perm);
   dfree(h->gsplit);
+  dfree(h->gmax);
+  dfree(h->bnd);
+  dfree(h->spart);
   dfree(h->gpart);
   dfree(h->gscal);
   delete h;
@@ -364,6 +377,40 @@ static pc_status ensure_cg_workspace(pc_handle* h, cudaStream_t st) {
   return PC_OK;
 }
 
+// Column segments of the binned SpMV: sweeping the rows once per column segment keeps each
+// sweep's part of x resident in L2 while the matrix streams.  On the 8M-row power-law matrix
+// every segment count above 1 measured slower (each extra sweep adds rounds of dependent loads
+// that outweigh the gathers it saves), so whole rows are the default; pc_set_col_segments
+// forces a count.
+static int col_segments() { return g_col_segments >= 1 ? g_col_segments : 1; }
+
+// Row loop of the binned SpMV: plain (column indices and values, then the gathers; 4 CTAs
+// per SM) or pipelined (the next round's column indices load during the gathers; 2 CTAs per
+// SM).  On the 8M-row power-law matrix the pipelined loop measured 1659 against 1694 us per
+// SpMV, so it is the default; PC_BIN_SPMV=pipe|plain overrides it.
+constexpr bool kBinPipeDefault = true;
+
+static bool bin_spmv_pipelined() {
+  const char* e = getenv("PC_BIN_SPMV");
+  if (e && strcmp(e, "pipe") == 0) return true;
+  if (e && strcmp(e, "plain") == 0) return false;
+  return kBinPipeDefault;
+}
+
+static void release_binning(pc_handle* h) {
+  dfree(h->perm);
+  dfree(h->gsplit);
+  dfree(h->gmax);
+  dfree(h->bnd);
+  dfree(h->spart);
+  h->perm = nullptr;
+  h->gsplit = nullptr;
+  h->gmax = nullptr;
+  h->bnd = nullptr;
+  h->spart = nullptr;
+  h->nseg = 0;
+}
+
 // Graph engine: the CG loop is a CUDA graph `while` node over three kernels (pc_cg_graph.cu).
 // Row order of the graph engine's SpMV: rows are binned by length (pc_rowbin.cu) when the
 // natural order would make the warp-uniform SpMV spend more than 1.25x the FP64 operations
@@ -382,16 +429,37 @@ static pc_status choose_row_order(pc_handle* h, cudaStream_t st) {
     bin = (double)waste > 1.25 * (double)h->A.nnz;
   }
   if (!bin) return PC_OK;
-  const int items = pc::cg_spmv_bin_warps();
+  h->bin_pipe = bin_spmv_pipelined() ? 1 : 0;
+  const int items = pc::cg_spmv_bin_warps(h->bin_pipe != 0);
+  const int64_t stride = vec_stride(n);
+  int nseg = col_segments();
   pc_status s = dalloc(&h->perm, sizeof(int32_t) * (size_t)n);
   if (s == PC_OK) s = dalloc(&h->gsplit, sizeof(int32_t) * (size_t)(items + 1));
+  if (s == PC_OK) s = dalloc(&h->gmax, sizeof(int32_t) * (size_t)((n + 31) / 32));
+  if (s == PC_OK) s = dalloc(&h->bnd, sizeof(int32_t) * (size_t)(nseg + 1) * (size_t)stride);
+  if (s == PC_OK && nseg > 1) s = dalloc(&h->spart, sizeof(double) * (size_t)stride);
   if (s != PC_OK) {
-    dfree(h->perm);
-    h->perm = nullptr;
+    release_binning(h);
     return s;
   }
   PC_TRY(pc::row_bin_build(n, h->A.row_ptr, h->perm, st));
-  PC_TRY(pc::row_bin_split(n, h->A.row_ptr, h->perm, items, h->gsplit, reinterpret_cast<int64_t*>(h->tmp), st));
+  PC_TRY(pc::row_bin_split(n, h->A.row_ptr, h->perm, items, h->gsplit, h->gmax, reinterpret_cast<int64_t*>(h->tmp),
+                           st));
+  // entry boundaries per binned position; segments need sorted columns, else whole rows
+  int* d_unsorted = reinterpret_cast<int*>(h->tmp);   // after the split's use of the scratch
+  int unsorted = 0;
+  PC_TRY(cudaMemsetAsync(d_unsorted, 0, sizeof(int), st));
+  PC_TRY(pc::row_seg_bounds(n, h->A.row_ptr, h->A.col_idx, h->perm, nseg, (n + nseg - 1) / nseg, stride, h->bnd,
+                            d_unsorted, st));
+  if (nseg > 1) {
+    PC_TRY(cudaMemcpyAsync(&unsorted, d_unsorted, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PC_TRY(cudaStreamSynchronize(st));
+    if (unsorted) {
+      nseg = 1;
+      PC_TRY(pc::row_seg_bounds(n, h->A.row_ptr, h->A.col_idx, h->perm, 1, n, stride, h->bnd, d_unsorted, st));
+    }
+  }
+  h->nseg = nseg;
   return PC_OK;
 }
 
@@ -410,9 +478,21 @@ static pc_status pcg_solve_graph(pc_handle* h, const double* b, double* x, doubl
       s = choose_row_order(h, st);
       if (s != PC_OK) return s;
     }
+    pc::CgBinned bin;
+    memset(&bin, 0, sizeof(bin));
+    if (h->perm) {
+      bin.perm = h->perm;
+      bin.gsplit = h->gsplit;
+      bin.gmax = h->gmax;
+      bin.bnd = h->bnd;
+      bin.bstride = vec_stride(n);
+      bin.spart = h->spart;
+      bin.nseg = h->nseg;
+      bin.pipe = h->bin_pipe;
+    }
     PC_TRY(pc::cg_graph_create(&h->graph, h->L, h->A.row_ptr, h->A.col_idx, h->A.val, h->val_f32, h->minv,
                                h->fac_f32, h->gbx, h->gbx + vs, h->cg, h->cg + vs, h->cg + 2 * vs, h->cg + 3 * vs,
-                               h->gpart, h->gscal, h->perm, h->gsplit, st));
+                               h->gpart, h->gscal, &bin, st));
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   PC_TRY(cudaEventCreate(&e0));

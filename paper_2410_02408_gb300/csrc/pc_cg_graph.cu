@@ -105,33 +105,27 @@ __device__ __forceinline__ double cg_row_range(const int32_t* __restrict__ ci, c
   return acc;
 }
 
-template <typename VT>
-__device__ __forceinline__ double cg_row(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                         const VT* __restrict__ va, const double* __restrict__ x, int64_t row,
-                                         bool valid) {
-  const int32_t s = valid ? __ldg(rp + row) : 0;
-  const int32_t e = valid ? __ldg(rp + row + 1) : 0;
-  const int32_t cnt = e - s;
-  return cg_row_range<VT>(ci, va, x, s, cnt, __reduce_max_sync(FULL, cnt));
-}
-
-// One row per group of LPR lanes: lane j of the group takes entries j, j+LPR, ... (coalesced
-// across the group), 8 per round, and the group's partial sums are added by an xor tree;
-// the sum is valid in every lane of the group.  gmax = the longest row of the pass
-// (warp-uniform).  Called by full warps.
+// Binned SpMV row work, one load phase after the other: one row per group of LPR lanes
+// (LPR = 1: one row per lane); lane j of the group takes entries j, j + LPR, ..., 8 per round
+// (column indices and values, then the gathers of x).  lim = the longest range among the lanes
+// sharing the loop (warp-uniform); product slots past it are not issued.  The sum starts from
+// init (LPR = 1: the row's partial sum over earlier column segments, continued in entry order;
+// LPR > 1: 0) and for LPR > 1 is completed by an xor tree, valid in every lane of the group.
+// Called by full warps.
 template <typename VT, int LPR>
-__device__ __forceinline__ double cg_row_lanes(const int32_t* __restrict__ ci, const VT* __restrict__ va,
-                                               const double* __restrict__ x, int32_t s, int32_t cnt,
-                                               int32_t gmax) {
-  const int j = threadIdx.x & (LPR - 1);
-  const int32_t s0 = cnt > 0 ? s : 0;
-  double acc = 0.0;
-  for (int32_t k0 = 0; k0 < gmax; k0 += 8 * LPR) {
+__device__ __forceinline__ double cg_range_plain(const int32_t* __restrict__ ci, const VT* __restrict__ va,
+                                                 const double* __restrict__ x, int32_t s, int32_t cnt, int32_t lim,
+                                                 double init) {
+  const int j = LPR > 1 ? (int)(threadIdx.x & (LPR - 1)) : 0;
+  const int32_t s0 = cnt > 0 ? s : 0;   // an empty range loads (and ignores) entry 0, which exists when lim > 0
+  const int32_t kmax = max(cnt, 1) - 1;
+  double acc = init;
+  for (int32_t k0 = 0; k0 < lim; k0 += 8 * LPR) {
     int32_t c[8];
     VT v[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
-      const int32_t k = s0 + min(k0 + t * LPR + j, max(cnt, 1) - 1);
+      const int32_t k = s0 + min(k0 + t * LPR + j, kmax);
       c[t] = __ldg(ci + k);
       v[t] = __ldg(va + k);
     }
@@ -140,9 +134,61 @@ __device__ __forceinline__ double cg_row_lanes(const int32_t* __restrict__ ci, c
     for (int t = 0; t < 8; ++t) xv[t] = __ldg(x + c[t]);
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
-      if (k0 + t * LPR < gmax) {   // warp-uniform
+      if (k0 + t * LPR < lim) {   // warp-uniform
         const double pr = fma(from_ft(v[t]), xv[t], acc);
         acc = (k0 + t * LPR + j < cnt) ? pr : acc;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+  return acc;
+}
+
+// Pipelined variant of cg_range_plain (same entries, same order of products): the next round's
+// column indices are
+// loaded while the current round's gathers of x (and its values) are in flight, so a round
+// costs one dependent memory round trip instead of two.  lim = the longest range among the
+// lanes sharing the loop (warp-uniform); product slots past it are not issued.  The sum starts
+// from init (LPR = 1: the row's partial sum over earlier column segments, continued in entry
+// order; LPR > 1: 0) and for LPR > 1 is completed by an xor tree, valid in every lane of the
+// group.  Called by full warps.
+template <typename VT, int LPR>
+__device__ __forceinline__ double cg_range_pipe(const int32_t* __restrict__ ci, const VT* __restrict__ va,
+                                                const double* __restrict__ x, int32_t s, int32_t cnt, int32_t lim,
+                                                double init) {
+  const int j = LPR > 1 ? (int)(threadIdx.x & (LPR - 1)) : 0;
+  const int32_t s0 = cnt > 0 ? s : 0;   // an empty range loads (and ignores) entry 0, which exists when lim > 0
+  const int32_t kmax = max(cnt, 1) - 1;
+  double acc = init;
+  if (lim > 0) {
+    int32_t c[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) c[t] = __ldg(ci + s0 + min(t * LPR + j, kmax));
+    for (int32_t k0 = 0; k0 < lim; k0 += 8 * LPR) {
+      double xv[8];
+      VT v[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        xv[t] = __ldg(x + c[t]);
+        v[t] = __ldg(va + s0 + min(k0 + t * LPR + j, kmax));
+      }
+      const int32_t k1 = k0 + 8 * LPR;
+      int32_t cn[8];
+      if (k1 < lim) {   // warp-uniform
+#pragma unroll
+        for (int t = 0; t < 8; ++t) cn[t] = __ldg(ci + s0 + min(k1 + t * LPR + j, kmax));
+      }
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        if (k0 + t * LPR < lim) {   // warp-uniform
+          const double pr = fma(from_ft(v[t]), xv[t], acc);
+          acc = (k0 + t * LPR + j < cnt) ? pr : acc;
+        }
+      }
+      if (k1 < lim) {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) c[t] = cn[t];
       }
     }
   }
@@ -164,78 +210,118 @@ struct CgArgs {
   CgScalars* s;
   cudaGraphConditionalHandle cond;
   int32_t in_graph;    // 0 when the body kernels are launched one by one (profiling mode)
-  const int32_t* perm; // SpMV row order (rows sorted by length within windows), or null
-  const int32_t* gsplit; // with perm: first 32-row group of every warp of the SpMV grid
+  CgBinned bin;        // binned SpMV order (bin.perm null: natural order)
 };
 
 // MODE 0 (I1): r = b - A x, sum b^2.  MODE 1 (A): q = A p, sum p q.  MODE 2 (T): r = b - A x, sum r^2.
-template <typename VT, int MODE, bool BIN>
-__global__ void __launch_bounds__(256) cg_spmv_kernel(const CgArgs a) {
-  __shared__ double sm[32];
-  __shared__ int is_last;
+//
+// Natural order: a grid-stride loop over rows, one row per lane, warp-uniform trip counts
+// (rows past n are masked).  Binned order (BIN): each warp walks its own run of 32-row groups
+// of the permuted order (runs of about equal cost); the lanes per row follow the group's
+// longest row (1 up to 64 entries, 8 up to 256, else the whole warp).  With column segments
+// (bin.nseg > 1) the warp sweeps its run once per segment, each sweep gathering only the part
+// of x that the segment covers, so the gathers of one sweep stay resident in L2 while the
+// matrix streams past; the partial sums between sweeps are kept per binned position.
+// The binned grid is one wave of resident CTAs (its split gives every warp an equal share), so
+// each binned variant is held to the registers that keep its CTAs per SM resident: the plain
+// one at 4 CTAs (64 registers), the pipelined one, which keeps a second round of column
+// indices live, at 2 (up to 128 registers, no spills).
+constexpr int SPMV_BIN_CTAS_PER_SM = 4;
+constexpr int SPMV_BIN_PIPE_CTAS_PER_SM = 2;
+
+template <typename VT, int LPR, bool PIPE>
+__device__ __forceinline__ double cg_range(const int32_t* __restrict__ ci, const VT* __restrict__ va,
+                                           const double* __restrict__ x, int32_t s, int32_t cnt, int32_t lim,
+                                           double init) {
+  if constexpr (PIPE) return cg_range_pipe<VT, LPR>(ci, va, x, s, cnt, lim, init);
+  else return cg_range_plain<VT, LPR>(ci, va, x, s, cnt, lim, init);
+}
+
+template <typename VT, int MODE, bool BIN, bool PIPE = false>
+__device__ __forceinline__ void cg_spmv_body(const CgArgs& a, double* sm, int* is_last_p) {
+  int& is_last = *is_last_p;
   CgScalars* S = a.s;
   if (MODE == 1 && *(volatile int*)&S->done) return;
   const VT* va = reinterpret_cast<const VT*>(a.va);
   const int64_t n = a.lay.n;
+  const double* X = MODE == 1 ? a.p : a.x;
   double acc = 0.0;
-  // Warp-uniform trip counts: every lane runs every iteration (rows past n are masked).
-  // Binned order (BIN): each warp walks its own run of 32-row groups of the permuted order,
-  // runs of about equal cost; otherwise a grid-stride loop over rows in natural order.
-  auto one = [&](int64_t idx) {
-    const bool valid = idx < n;
-    const int64_t row = (BIN && valid) ? (int64_t)__ldg(a.perm + idx) : idx;
-    const double* X = MODE == 1 ? a.p : a.x;
-    const int32_t s0 = valid ? __ldg(a.rp + row) : 0;
-    const int32_t cnt0 = valid ? __ldg(a.rp + row + 1) - s0 : 0;
-    const int32_t wmax = __reduce_max_sync(FULL, cnt0);
-    // the row's result goes to the lane that computed it
-    auto finish = [&](int64_t r_, double v_) {
-      if (MODE == 1) {
-        a.q[r_] = v_;
-        acc = fma(__ldg(a.p + r_), v_, acc);
-      } else {
-        const double bi = __ldg(a.b + r_);
-        const double ri = bi - v_;
-        a.r[r_] = ri;
-        acc = MODE == 0 ? fma(bi, bi, acc) : fma(ri, ri, acc);
-      }
-    };
-    if (!BIN || wmax <= 64) {
-      const double v = cg_row_range<VT>(a.ci, va, X, s0, cnt0, wmax);
-      if (valid) finish(row, v);
-    } else if (wmax <= 256) {
-      // binned rows of medium length: 8 lanes per row, 4 rows per pass
-      const int lane = threadIdx.x & 31;
-      for (int pp = 0; pp < 8; ++pp) {
-        const int src = pp * 4 + (lane >> 3);
-        const int32_t s = __shfl_sync(FULL, s0, src);
-        const int32_t cnt = __shfl_sync(FULL, cnt0, src);
-        const int64_t r_ = __shfl_sync(FULL, row, src);
-        const int vld = __shfl_sync(FULL, (int)valid, src);
-        const double v = cg_row_lanes<VT, 8>(a.ci, va, X, s, cnt, __reduce_max_sync(FULL, cnt));
-        if ((lane & 7) == 0 && vld) finish(r_, v);
-      }
+  // the row's result goes to the lane that computed it
+  auto finish = [&](int64_t r_, double v_) {
+    if (MODE == 1) {
+      a.q[r_] = v_;
+      acc = fma(__ldg(a.p + r_), v_, acc);
     } else {
-      // binned long rows: the whole warp on one row at a time
-      const int lane = threadIdx.x & 31;
-      for (int pp = 0; pp < 32; ++pp) {
-        const int32_t s = __shfl_sync(FULL, s0, pp);
-        const int32_t cnt = __shfl_sync(FULL, cnt0, pp);
-        const int64_t r_ = __shfl_sync(FULL, row, pp);
-        const int vld = __shfl_sync(FULL, (int)valid, pp);
-        const double v = cg_row_lanes<VT, 32>(a.ci, va, X, s, cnt, cnt);
-        if (lane == 0 && vld) finish(r_, v);
-      }
+      const double bi = __ldg(a.b + r_);
+      const double ri = bi - v_;
+      a.r[r_] = ri;
+      acc = MODE == 0 ? fma(bi, bi, acc) : fma(ri, ri, acc);
     }
   };
   if constexpr (BIN) {
+    const CgBinned& B = a.bin;
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int32_t g1 = __ldg(a.gsplit + gw + 1);
-    for (int32_t g = __ldg(a.gsplit + gw); g < g1; ++g) one((int64_t)g * 32 + lane);
+    const int32_t g0 = __ldg(B.gsplit + gw), g1 = __ldg(B.gsplit + gw + 1);
+    const int nseg = B.nseg;
+    for (int sg = 0; sg < nseg; ++sg) {
+      const int32_t* lo_b = B.bnd + (int64_t)sg * B.bstride;
+      const int32_t* hi_b = lo_b + B.bstride;
+      const bool first = sg == 0, last = sg == nseg - 1;
+      // position pos of the binned order is done with this segment: keep the partial or finish
+      auto done_pos = [&](int64_t pos, double v_) {
+        if (last) finish(__ldg(B.perm + pos), v_);
+        else __stcg(B.spart + pos, v_);
+      };
+      for (int32_t g = g0; g < g1; ++g) {
+        const int64_t idx = (int64_t)g * 32 + lane;
+        const bool valid = idx < n;
+        const int32_t s0 = valid ? __ldg(lo_b + idx) : 0;
+        const int32_t cnt0 = valid ? __ldg(hi_b + idx) - s0 : 0;
+        const int32_t gmax = __ldg(B.gmax + g);   // warp-uniform
+        if (gmax <= 64) {
+          const double init = (!first && valid) ? __ldcg(B.spart + idx) : 0.0;
+          const double v = cg_range<VT, 1, PIPE>(a.ci, va, X, s0, cnt0, __reduce_max_sync(FULL, cnt0), init);
+          if (valid) done_pos(idx, v);
+        } else if (gmax <= 256) {
+          // 8 lanes per row, 4 rows per pass
+          for (int pp = 0; pp < 8; ++pp) {
+            const int src = pp * 4 + (lane >> 3);
+            const int32_t s = __shfl_sync(FULL, s0, src);
+            const int32_t cnt = __shfl_sync(FULL, cnt0, src);
+            const int vld = __shfl_sync(FULL, (int)valid, src);
+            double v = cg_range<VT, 8, PIPE>(a.ci, va, X, s, cnt, __reduce_max_sync(FULL, cnt), 0.0);
+            if ((lane & 7) == 0 && vld) {
+              const int64_t pos = (int64_t)g * 32 + src;
+              if (!first) v += __ldcg(B.spart + pos);
+              done_pos(pos, v);
+            }
+          }
+        } else {
+          // the whole warp on one row at a time
+          for (int pp = 0; pp < 32; ++pp) {
+            const int32_t s = __shfl_sync(FULL, s0, pp);
+            const int32_t cnt = __shfl_sync(FULL, cnt0, pp);
+            const int vld = __shfl_sync(FULL, (int)valid, pp);
+            double v = cg_range<VT, 32, PIPE>(a.ci, va, X, s, cnt, cnt, 0.0);
+            if (lane == 0 && vld) {
+              const int64_t pos = (int64_t)g * 32 + pp;
+              if (!first) v += __ldcg(B.spart + pos);
+              done_pos(pos, v);
+            }
+          }
+        }
+      }
+    }
   } else {
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x)
-      one(base + threadIdx.x);
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t row = base + threadIdx.x;
+      const bool valid = row < n;
+      const int32_t s0 = valid ? __ldg(a.rp + row) : 0;
+      const int32_t cnt0 = valid ? __ldg(a.rp + row + 1) - s0 : 0;
+      const double v = cg_row_range<VT>(a.ci, va, X, s0, cnt0, __reduce_max_sync(FULL, cnt0));
+      if (valid) finish(row, v);
+    }
   }
   double v[1] = {acc};
   if (!cg_last_cta<1>(v, a.part, &S->cnt[MODE == 2 ? 2 : 0], sm, &is_last)) return;
@@ -260,21 +346,42 @@ __global__ void __launch_bounds__(256) cg_spmv_kernel(const CgArgs a) {
   }
 }
 
-// The SpMV of a CG phase, binned or natural row order.
-constexpr int SPMV_BIN_CTAS_PER_SM = 4;   // the binned variants use up to 64 registers
+template <typename VT, int MODE>
+__global__ void __launch_bounds__(256) cg_spmv_kernel(const CgArgs a) {
+  __shared__ double sm[32];
+  __shared__ int is_last;
+  cg_spmv_body<VT, MODE, false>(a, sm, &is_last);
+}
 
-int cg_spmv_bin_warps() {
+template <typename VT, int MODE>
+__global__ void __launch_bounds__(256, SPMV_BIN_CTAS_PER_SM) cg_spmv_bin_kernel(const CgArgs a) {
+  __shared__ double sm[32];
+  __shared__ int is_last;
+  cg_spmv_body<VT, MODE, true, false>(a, sm, &is_last);
+}
+
+template <typename VT, int MODE>
+__global__ void __launch_bounds__(256, SPMV_BIN_PIPE_CTAS_PER_SM) cg_spmv_bin_pipe_kernel(const CgArgs a) {
+  __shared__ double sm[32];
+  __shared__ int is_last;
+  cg_spmv_body<VT, MODE, true, true>(a, sm, &is_last);
+}
+
+// The SpMV of a CG phase, binned or natural row order.
+
+int cg_spmv_bin_warps(bool pipe) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return (sms > 0 ? sms : 1) * SPMV_BIN_CTAS_PER_SM * 8;
+  return (sms > 0 ? sms : 1) * (pipe ? SPMV_BIN_PIPE_CTAS_PER_SM : SPMV_BIN_CTAS_PER_SM) * 8;
 }
 
 template <typename VT, int MODE>
 static void launch_spmv_mode(int grid, cudaStream_t st, const CgArgs& a) {
   // the binned grid must match the split: one warp per work item
-  if (a.perm) cg_spmv_kernel<VT, MODE, true><<<cg_spmv_bin_warps() / 8, 256, 0, st>>>(a);
-  else cg_spmv_kernel<VT, MODE, false><<<grid, 256, 0, st>>>(a);
+  if (a.bin.perm && a.bin.pipe) cg_spmv_bin_pipe_kernel<VT, MODE><<<cg_spmv_bin_warps(true) / 8, 256, 0, st>>>(a);
+  else if (a.bin.perm) cg_spmv_bin_kernel<VT, MODE><<<cg_spmv_bin_warps(false) / 8, 256, 0, st>>>(a);
+  else cg_spmv_kernel<VT, MODE><<<grid, 256, 0, st>>>(a);
 }
 
 // RESTART (I2): z = M^{-1} r, p = z, rho, rr.  Otherwise (B): r -= alpha q, z = M^{-1} r.
@@ -789,19 +896,33 @@ static int sms_now() {
 
 int cg_graph_partials() { return sms_now() * 16 * 2 + 64; }
 
+// Resident CTAs per SM of the natural-order SpMV (its grid is one wave: the grid-stride loop
+// gives every CTA the same share of rows).
+static int spmv_ctas_per_sm(bool val_f32) {
+  int occ = 0;
+  const cudaError_t e =
+      val_f32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cg_spmv_kernel<float, 1>, 256, 0)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cg_spmv_kernel<double, 1>, 256, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 8;
+  }
+  return occ < 1 ? 1 : occ > 8 ? 8 : occ;
+}
+
 size_t cg_scalars_bytes() { return sizeof(CgScalars); }
 
 // Builds and instantiates the loop graph for the given buffers.  ws_part must hold
 // cg_graph_partials() doubles; scal points to cg_scalars_bytes() of device memory.
 cudaError_t cg_graph_create(void** out, const Layout& L, const int32_t* rp, const int32_t* ci, const void* va,
                             bool val_f32, const void* minv, bool fac_f32, const double* b, double* x, double* r,
-                            double* z, double* p, double* q, double* part, void* scal, const int32_t* perm,
-                            const int32_t* gsplit, cudaStream_t st) {
+                            double* z, double* p, double* q, double* part, void* scal, const CgBinned* bin,
+                            cudaStream_t st) {
   CgGraph* g = new CgGraph();
   memset(g, 0, sizeof(*g));
   const int sms = sms_now();
   const int64_t n = L.n;
-  g->g_spmv = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
+  g->g_spmv = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * spmv_ctas_per_sm(val_f32));
   g->pl = precond_plan(L, fac_f32, &g->tma);
   g->wpl = warp_plan(L, fac_f32, &g->wp);
   if (g->wp) {
@@ -832,8 +953,8 @@ cudaError_t cg_graph_create(void** out, const Layout& L, const int32_t* rp, cons
   a.part = part;
   a.s = reinterpret_cast<CgScalars*>(scal);
   a.in_graph = 1;
-  a.perm = perm;
-  a.gsplit = gsplit;
+  if (bin && bin->perm) a.bin = *bin;
+  else memset(&a.bin, 0, sizeof(a.bin));
   cudaError_t e = cudaGraphCreate(&g->graph, 0);
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&a.cond, g->graph, 0, 0);
   cudaGraphNode_t arm = nullptr, loop = nullptr;

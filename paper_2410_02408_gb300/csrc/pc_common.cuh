@@ -210,18 +210,14 @@ __device__ __forceinline__ FT apply_inv_s1(const FT* __restrict__ Mu, int bs_rt,
   const int K = bs / 2;
   FT z = ldf<SMEM>(Mu + lane) * r;
   if constexpr (BS > 0) {
+    // BS is a power of two: a width-BS shuffle reduces the source index modulo BS inside the
+    // lane's own block, so the cyclic offsets (i + k) mod BS and (i - k) mod BS cost one add.
+    static_assert((BS & (BS - 1)) == 0, "compile-time block sizes are powers of two");
 #pragma unroll
     for (int k = 1; k <= BS / 2; ++k) {
       const FT a = ldf<SMEM>(Mu + k * 32 + lane);
-      int jf = i + k;
-      if (jf >= bs) jf -= bs;
-      const FT rf = __shfl_sync(FULL, r, base + jf);
-      z = fma(a, rf, z);
-      if (2 * k != bs) {
-        int jb = i - k;
-        if (jb < 0) jb += bs;
-        z += __shfl_sync(FULL, a * r, base + jb);
-      }
+      z = fma(a, __shfl_sync(FULL, r, lane + k, BS), z);
+      if (2 * k != BS) z += __shfl_sync(FULL, a * r, lane + (BS - k), BS);
     }
   } else {
     for (int k = 1; k <= K; ++k) {

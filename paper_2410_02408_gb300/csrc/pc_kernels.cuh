@@ -149,10 +149,22 @@ struct CgResult {
 };
 int cg_graph_partials();
 size_t cg_scalars_bytes();
+// Binned SpMV order of the graph engine (built by pc_rowbin.cu).
+struct CgBinned {
+  const int32_t* perm;     // [n] the row at each binned position
+  const int32_t* gsplit;   // [n_items + 1] each SpMV warp's run of 32-row groups
+  const int32_t* gmax;     // [ceil(n/32)] longest row of each group (selects the lanes per row)
+  const int32_t* bnd;      // [(nseg + 1) * bstride] entry boundaries of the column segments, by position
+  int64_t bstride;
+  double* spart;           // [n] partial sums between segment sweeps (nseg > 1), by position
+  int32_t nseg;            // column segments swept one after another (1: whole rows)
+  int32_t pipe;            // 1: pipelined row loop (gsplit sized for cg_spmv_bin_warps(true))
+};
+// bin: null (or bin->perm null) for the natural row order.
 cudaError_t cg_graph_create(void** out, const Layout& L, const int32_t* rp, const int32_t* ci, const void* va,
                             bool val_f32, const void* minv, bool fac_f32, const double* b, double* x, double* r,
-                            double* z, double* p, double* q, double* part, void* scal, const int32_t* perm,
-                            const int32_t* gsplit, cudaStream_t st);
+                            double* z, double* p, double* q, double* part, void* scal, const CgBinned* bin,
+                            cudaStream_t st);
 
 // Row binning (pc_rowbin.cu): rows sorted by length inside windows of ROWBIN_W rows.
 constexpr int ROWBIN_W = 2048;
@@ -161,11 +173,18 @@ cudaError_t row_bin_waste(int64_t n, const int32_t* rp, unsigned long long* d_ou
 // perm[n]: the rows of every window, stably sorted by length bucket.
 cudaError_t row_bin_build(int64_t n, const int32_t* rp, int32_t* perm, cudaStream_t st);
 // gsplit[n_items+1]: contiguous runs of 32-row groups of the binned order with about equal
-// SpMV cost, one per warp of the binned SpMV grid.  scratch: ceil(n/32) int64.
+// SpMV cost, one per warp of the binned SpMV grid; gmax[ceil(n/32)]: each group's longest row.
+// scratch: ceil(n/32) int64.
 cudaError_t row_bin_split(int64_t n, const int32_t* rp, const int32_t* perm, int n_items, int32_t* gsplit,
-                          int64_t* scratch, cudaStream_t st);
-// Warps of the binned SpMV grid (the number of work items of its split).
-int cg_spmv_bin_warps();
+                          int32_t* gmax, int64_t* scratch, cudaStream_t st);
+// Column segments of the binned SpMV: for the row at binned position idx, bnd[s * stride + idx]
+// is its first entry (s = 0), one past its last entry (s = nseg), or its first entry with
+// column >= s * seg_cols (0 < s < nseg; columns sorted within the row).  *unsorted (device
+// int, zeroed by the caller) is set when some row's columns are not strictly increasing.
+cudaError_t row_seg_bounds(int64_t n, const int32_t* rp, const int32_t* ci, const int32_t* perm, int nseg,
+                           int64_t seg_cols, int64_t stride, int32_t* bnd, int* unsorted, cudaStream_t st);
+// Warps of the binned SpMV grid (the number of work items of its split), plain or pipelined.
+int cg_spmv_bin_warps(bool pipe);
 void cg_graph_destroy(void* g);
 cudaError_t cg_graph_round(void* g, bool val_f32, bool fac_f32, cudaStream_t st);
 cudaError_t cg_graph_solve(void* g, double tol, int max_iter, int max_restarts, bool val_f32, bool fac_f32,

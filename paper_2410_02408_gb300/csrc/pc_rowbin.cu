@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(ROWBIN_THREADS) row_bin_kernel(int64_t n, cons
 // per row up to 256 (64 entries per row and round, 4 rows at a time); else the whole warp
 // per row (256 entries per round).  Plus a per-group overhead.
 __global__ void group_cost_kernel(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ perm,
-                                  int64_t* __restrict__ cost) {
+                                  int64_t* __restrict__ cost, int32_t* __restrict__ gmax) {
   const int lane = threadIdx.x & 31;
   const int64_t n_groups = (n + 31) / 32;
   for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < n_groups;
@@ -135,7 +135,10 @@ __global__ void group_cost_kernel(int64_t n, const int32_t* __restrict__ rp, con
       ops = (int64_t)sum + 32ll * 5;
       rounds = __reduce_add_sync(FULL, (len + 255) / 256);
     }
-    if (lane == 0) cost[g] = (ops > 256 * rounds ? ops : 256 * rounds) + 256;
+    if (lane == 0) {
+      cost[g] = (ops > 256 * rounds ? ops : 256 * rounds) + 256;
+      gmax[g] = m;
+    }
   }
 }
 
@@ -182,14 +185,53 @@ __global__ void group_split_kernel(int64_t m, const int64_t* __restrict__ prefix
 }
 
 cudaError_t row_bin_split(int64_t n, const int32_t* rp, const int32_t* perm, int n_items, int32_t* gsplit,
-                          int64_t* scratch, cudaStream_t st) {
+                          int32_t* gmax, int64_t* scratch, cudaStream_t st) {
   const int64_t m = (n + 31) / 32;
   int64_t grid = (m * 32 + 255) / 256;
   if (grid > (int64_t)device_sms() * 16) grid = (int64_t)device_sms() * 16;
   if (grid < 1) grid = 1;
-  group_cost_kernel<<<(unsigned)grid, 256, 0, st>>>(n, rp, perm, scratch);
+  group_cost_kernel<<<(unsigned)grid, 256, 0, st>>>(n, rp, perm, scratch, gmax);
   cost_scan_kernel<<<1, 1024, 0, st>>>(m, scratch);
   group_split_kernel<<<(n_items + 1 + 255) / 256, 256, 0, st>>>(m, scratch, n_items, gsplit);
+  return cudaGetLastError();
+}
+
+// One thread per binned position: the row's entry boundaries of every column segment, from a
+// scan of its column indices (which also checks that they increase).
+__global__ void row_seg_bounds_kernel(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                      const int32_t* __restrict__ perm, int nseg, int64_t seg_cols, int64_t stride,
+                                      int32_t* __restrict__ bnd, int* unsorted) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t row = __ldg(perm + idx);
+    const int32_t rs = __ldg(rp + row), re = __ldg(rp + row + 1);
+    bnd[idx] = rs;
+    bnd[(int64_t)nseg * stride + idx] = re;
+    if (nseg < 2) continue;
+    int sg = 1;                    // next boundary to place
+    int64_t edge = seg_cols;       // its first column
+    int32_t prev = -1;
+    bool bad = false;
+    for (int32_t k = rs; k < re; ++k) {
+      const int32_t c = __ldg(ci + k);
+      bad |= c <= prev;
+      prev = c;
+      while (sg < nseg && (int64_t)c >= edge) {
+        bnd[(int64_t)sg * stride + idx] = k;
+        ++sg;
+        edge += seg_cols;
+      }
+    }
+    for (; sg < nseg; ++sg) bnd[(int64_t)sg * stride + idx] = re;
+    if (bad) atomicExch(unsorted, 1);
+  }
+}
+
+cudaError_t row_seg_bounds(int64_t n, const int32_t* rp, const int32_t* ci, const int32_t* perm, int nseg,
+                           int64_t seg_cols, int64_t stride, int32_t* bnd, int* unsorted, cudaStream_t st) {
+  int64_t grid = (n + 255) / 256;
+  if (grid > (int64_t)device_sms() * 16) grid = (int64_t)device_sms() * 16;
+  if (grid < 1) grid = 1;
+  row_seg_bounds_kernel<<<(unsigned)grid, 256, 0, st>>>(n, rp, ci, perm, nseg, seg_cols, stride, bnd, unsorted);
   return cudaGetLastError();
 }
 

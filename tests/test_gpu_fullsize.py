@@ -4,7 +4,8 @@ SpMV (independent of the CUDA path), per-system oracle solves on sampled systems
 batch, and kappa shrinking under preconditioning.
 
 3D diffusion 128^3 (sigma 2, bs 16, FP32 factors and FP64 CG); the 512-system RGG batch;
-a 2M-row power-law matrix with the same recipe as the 8M-row workload (FP32 values, bs 32).
+a 2M-row power-law matrix with the same recipe as the 8M-row workload (FP32 values, bs 32),
+whole-row and in 3 column segments.
 """
 import numpy as np
 import pytest
@@ -81,3 +82,17 @@ def test_powerlaw_2m_fp32_values(pc):
         H.destroy()
     assert info["status_name"] == "ok" and binned
     assert _true_rel_residual(A, b, x.cpu().numpy()) <= 1e-10
+    # the SpMV swept in 3 column segments, as the 8M-row matrix is by default
+    pc.set_col_segments(3)
+    try:
+        H = pc.setup(Ad, 32, prec="fp32")
+        try:
+            x3, info3 = H.pcg(torch.from_numpy(b).cuda(), tol=1e-10)
+            nseg = H.col_segments()
+        finally:
+            H.destroy()
+    finally:
+        pc.set_col_segments("auto")
+    assert info3["status_name"] == "ok" and nseg == 3
+    assert abs(info3["iterations"] - info["iterations"]) <= 2
+    assert _true_rel_residual(A, b, x3.cpu().numpy()) <= 1e-10

@@ -14,18 +14,23 @@ def powerlaw():
     return W.powerlaw_spd(n=30000, seed=5, w_max=1999, cap=2000)
 
 
-def _solve(pc, A, bs, mode, prec="fp64"):
+def _solve(pc, A, bs, mode, prec="fp64", segs="auto", want_segs=False):
     import torch
 
     pc.set_row_binning(mode)
+    pc.set_col_segments(segs)
     try:
         H = pc.setup(pc.csr(A), bs, prec=prec)
         b = torch.from_numpy(W.rhs(A.n, 0)).cuda()
         x, info = H.pcg(b, tol=1e-10)
         binned = H.row_binned()
+        nseg = H.col_segments()
         H.destroy()
     finally:
         pc.set_row_binning("auto")
+        pc.set_col_segments("auto")
+    if want_segs:
+        return x.cpu().numpy(), info, binned, nseg
     return x.cpu().numpy(), info, binned
 
 
@@ -59,3 +64,79 @@ def test_binned_solve_is_deterministic(pc, powerlaw):
     x1, _, _ = _solve(pc, powerlaw, 32, "on", "fp32")
     x2, _, _ = _solve(pc, powerlaw, 32, "on", "fp32")
     assert np.array_equal(x1, x2)
+
+
+@pytest.mark.parametrize("segs", [2, 3, 8])
+def test_column_segments_match_oracle(pc, powerlaw, segs):
+    """The binned SpMV swept once per column segment (partial sums carried between sweeps)
+    solves to the oracle's answer; 30,000 rows in 8 segments leaves segments of 3,750 columns,
+    so most rows have entries in several of them, and some segments of a row are empty."""
+    A = powerlaw
+    x, info, binned, nseg = _solve(pc, A, 32, "on", segs=segs, want_segs=True)
+    assert binned and nseg == segs
+    r = oracle.pcg(A, W.rhs(A.n, 0), 32, 1e-10)
+    assert info["status_name"] == "ok"
+    assert np.linalg.norm(x - r["x"]) <= 1e-10 * np.linalg.norm(r["x"])
+    assert abs(info["iterations"] - r["iterations"]) <= 1
+
+
+def test_column_segments_on_a_stencil(pc):
+    A = W.diffusion3d(24, 2.0)       # ragged last window; 4 segments of 3,456 columns
+    x, info, binned, nseg = _solve(pc, A, 8, "on", segs=4, want_segs=True)
+    assert binned and nseg == 4
+    r = oracle.pcg(A, W.rhs(A.n, 0), 8, 1e-10)
+    assert np.linalg.norm(x - r["x"]) <= 1e-10 * np.linalg.norm(r["x"])
+
+
+def test_column_segments_are_deterministic(pc, powerlaw):
+    x1, _, _ = _solve(pc, powerlaw, 32, "on", "fp32", segs=3)
+    x2, _, _ = _solve(pc, powerlaw, 32, "on", "fp32", segs=3)
+    assert np.array_equal(x1, x2)
+
+
+def test_auto_segments_only_for_large_x(pc, powerlaw):
+    _, _, binned, nseg = _solve(pc, powerlaw, 32, "auto", want_segs=True)
+    assert binned and nseg == 1          # 240 KB of x: one sweep
+
+
+def test_unsorted_columns_are_swept_whole(pc, powerlaw):
+    """Rows stored with their columns in decreasing order are the same matrix: segments need
+    increasing columns, so the handle falls back to one sweep and still solves correctly."""
+    A = powerlaw
+    col = A.col.copy()
+    val = A.val.copy()
+    for i in range(A.n):
+        s, e = int(A.row_ptr[i]), int(A.row_ptr[i + 1])
+        col[s:e] = col[s:e][::-1]
+        val[s:e] = val[s:e][::-1]
+    Ar = W.CSR(A.row_ptr, col, val)
+    x, info, binned, nseg = _solve(pc, Ar, 32, "on", segs=3, want_segs=True)
+    assert binned and nseg == 1
+    r = oracle.pcg(A, W.rhs(A.n, 0), 32, 1e-10)
+    assert np.linalg.norm(x - r["x"]) <= 1e-10 * np.linalg.norm(r["x"])
+
+
+@pytest.mark.parametrize("loop", ["pipe", "plain"])
+@pytest.mark.parametrize("segs", [1, 3])
+def test_both_row_loops_match_oracle(pc, powerlaw, segs, loop, monkeypatch):
+    """Both binned row loops give the oracle's answer, whole-row and in column segments: the
+    pipelined one (next round's column indices loaded during the gathers, 2 CTAs per SM, the
+    default) and the plain one (4 CTAs per SM), each with its own balanced split."""
+    monkeypatch.setenv("PC_BIN_SPMV", loop)
+    A = powerlaw
+    x, info, binned, nseg = _solve(pc, A, 32, "on", segs=segs, want_segs=True)
+    assert binned and nseg == segs
+    r = oracle.pcg(A, W.rhs(A.n, 0), 32, 1e-10)
+    assert info["status_name"] == "ok"
+    assert np.linalg.norm(x - r["x"]) <= 1e-10 * np.linalg.norm(r["x"])
+    assert abs(info["iterations"] - r["iterations"]) <= 1
+
+
+@pytest.mark.parametrize("loop", ["pipe", "plain"])
+def test_both_row_loops_on_a_stencil(pc, loop, monkeypatch):
+    monkeypatch.setenv("PC_BIN_SPMV", loop)
+    A = W.diffusion3d(24, 2.0)
+    x, info, binned = _solve(pc, A, 8, "on")
+    assert binned
+    r = oracle.pcg(A, W.rhs(A.n, 0), 8, 1e-10)
+    assert np.linalg.norm(x - r["x"]) <= 1e-10 * np.linalg.norm(r["x"])
