@@ -30,6 +30,17 @@
  *   - Block partition: block k covers rows [k*bs, min(n, (k+1)*bs)); the last block may
  *     be shorter and is padded with the identity internally (the result is unchanged).
  *     1 <= block_size <= 64.
+ *
+ * Environment variables (read when the setting is needed; the pc_set_* calls take
+ * precedence where both exist):
+ *   PC_CG_ENGINE=graph|persistent   CG engine (pc_set_cg_engine).
+ *   PC_WAIT_BUDGET=<cycles>         bound of every device-side wait (pc_set_wait_budget).
+ *   PC_BIN_SPMV=pipe|plain          row loop of the binned CG SpMV, read when a handle first
+ *                                   solves: pipelined (default, 2 CTAs per SM) or plain (4).
+ *   PC_CG_PROFILE=1                 graph engine: launch the loop body kernels one by one with
+ *                                   events around each (per-kernel times, pc_get_trace).
+ *   PC_TRACE_BARRIERS=N             persistent engine: record N barrier timestamps.
+ *   PC_BATCH_PROFILE=1              batched mode: per-phase device timers (pc_batch_profile).
  */
 #ifndef PC_H_
 #define PC_H_
