@@ -75,7 +75,7 @@ def parse():
     ap.add_argument("--row-binning", default="auto", choices=["auto", "on", "off"],
                     help="row order of the CG SpMV (auto: binned by length when rows are irregular)")
     ap.add_argument("--col-segments", default="auto",
-                    help="column segments of the binned SpMV: auto (by the size of x) or 1..8")
+                    help="column segments of the binned SpMV: auto (the library default, 1) or 1..8")
     ap.add_argument("--n-sys", type=int, default=512, help="systems in the batched workload")
     ap.add_argument("--no-tune", action="store_true", help="batched workload: skip the launch-shape autotuner")
     ap.add_argument("--tune-trials", type=int, default=0, help="batched autotuner candidates (0 = all)")

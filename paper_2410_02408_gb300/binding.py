@@ -523,7 +523,8 @@ def set_row_binning(mode: str):
 
 
 def set_col_segments(segs):
-    """"auto" (default) or 1..8: column segments of the binned CG SpMV (see pc_set_col_segments)."""
+    """"auto" (the library default: whole rows) or 1..8: column segments of the binned CG SpMV
+    (see pc_set_col_segments)."""
     lib().pc_set_col_segments(-1 if segs in (None, "auto") else int(segs))
 
 
