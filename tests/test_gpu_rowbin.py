@@ -94,9 +94,9 @@ def test_column_segments_are_deterministic(pc, powerlaw):
     assert np.array_equal(x1, x2)
 
 
-def test_auto_segments_only_for_large_x(pc, powerlaw):
+def test_default_is_whole_rows(pc, powerlaw):
     _, _, binned, nseg = _solve(pc, powerlaw, 32, "auto", want_segs=True)
-    assert binned and nseg == 1          # 240 KB of x: one sweep
+    assert binned and nseg == 1
 
 
 def test_unsorted_columns_are_swept_whole(pc, powerlaw):
