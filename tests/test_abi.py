@@ -96,3 +96,19 @@ int main(void) {
             if key.startswith(cls.__name__ + "."):
                 field = key.split(".", 1)[1]
                 assert getattr(cls, field).offset == int(v), key
+
+
+def test_handle_queries_on_a_null_handle(libpc):
+    """The handle queries and process-wide settings are host-only: they answer for a null
+    handle without touching the GPU."""
+    libpc.pc_handle_failed_block.restype = ctypes.c_int64
+    assert libpc.pc_handle_failed_block(None) == -1
+    assert libpc.pc_handle_refactored_fp64(None) == 0
+    assert libpc.pc_handle_row_binned(None) == 0
+    assert libpc.pc_handle_col_segments(None) == 1
+    for setter, values in ((libpc.pc_set_row_binning, (-1, 0, 1, 7)), (libpc.pc_set_col_segments, (3, 0, 9, -1)),
+                           (libpc.pc_set_cg_engine, (1, 0, -1))):
+        for v in values:
+            setter(ctypes.c_int32(v))
+    libpc.pc_set_row_binning(ctypes.c_int32(-1))
+    libpc.pc_set_col_segments(ctypes.c_int32(-1))
