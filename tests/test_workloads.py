@@ -85,3 +85,23 @@ def test_powerlaw_small():
     off = np.asarray(abs(S).sum(axis=1)).ravel() - np.abs(d)
     assert np.all(d - off > 0.009)                          # strictly diagonally dominant
     assert A.val.dtype == np.float32
+
+
+def test_powerlaw_exponent_gives_the_mean_degree():
+    g = W._powerlaw_exponent(8, 1999, 31.0)
+    w = np.arange(8, 2000, dtype=np.float64)
+    p = w ** (-g)
+    assert abs((w * p).sum() / p.sum() - 31.0) < 1e-6
+
+
+def test_powerlaw_values_follow_the_recipe():
+    """Off-diagonals in [-1, 0) as FP32; the diagonal is the FP32 rounding of the sum of the
+    already-rounded off-diagonal magnitudes plus 1e-2."""
+    A = W.powerlaw_spd(n=5000, seed=5, w_max=300, cap=200)
+    rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
+    off = rows != A.col
+    assert np.all(A.val[off] < 0) and np.all(A.val[off] >= -1)
+    absum = np.bincount(rows[off], weights=np.abs(A.val[off].astype(np.float64)), minlength=A.n)
+    diag = A.val[~off]
+    assert np.array_equal(rows[~off], np.arange(A.n))
+    assert np.array_equal(diag, (absum + 1e-2).astype(np.float32))
