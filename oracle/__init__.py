@@ -40,7 +40,19 @@ def lib():
         path = _build.build()
         _lib = ctypes.CDLL(path)
         _declare(_lib)
+        _lib.or_set_threads(1)
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's parallel loops (1 = sequential; results are identical for
+    any count).  Returns the count in effect (1 when built without OpenMP)."""
+    lib().or_set_threads(int(n))
+    return int(lib().or_get_threads())
+
+
+def threads() -> int:
+    return int(lib().or_get_threads())
 
 
 _i64 = ctypes.c_int64
@@ -50,6 +62,10 @@ _p = ctypes.c_void_p
 
 
 def _declare(L):
+    L.or_set_threads.restype = None
+    L.or_set_threads.argtypes = [_i32]
+    L.or_get_threads.restype = _i32
+    L.or_get_threads.argtypes = []
     L.or_num_blocks.restype = _i64
     L.or_num_blocks.argtypes = [_i64, _i32]
     L.or_extract_blocks.restype = None

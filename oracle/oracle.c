@@ -28,6 +28,12 @@
  *
  * Condition number (Sec. 3.1): for the SPD operators here kappa = lambda_max/lambda_min.
  *
+ * Threads (or_set_threads, default 1): when built with OpenMP, the loops over rows, blocks
+ * and vector elements are shared among threads.  No loop changes its arithmetic with the
+ * thread count: an element loop computes every element the same way whoever runs it, and a
+ * dot product always adds its terms in index order within fixed chunks of OR_CHUNK entries,
+ * then the chunk sums in chunk order.  Results are therefore identical for any thread count.
+ *
  * Status codes returned: 0 ok, 2 not SPD (Cholesky pivot), 3 CG breakdown,
  * 4 no convergence within max_iter.
  */
@@ -37,10 +43,36 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #define OR_OK 0
 #define OR_NOT_SPD 2
 #define OR_BREAKDOWN 3
 #define OR_NO_CONVERGENCE 4
+
+/* Loops shorter than OR_PAR_MIN iterations run on the calling thread only (the result is
+ * the same either way; this only avoids the cost of waking threads for tiny inputs). */
+#define OR_CHUNK 4096
+#define OR_PAR_MIN 32768
+
+void or_set_threads(int32_t t) {
+#ifdef _OPENMP
+  omp_set_num_threads(t > 0 ? t : 1);
+#else
+  (void)t;
+#endif
+}
+
+/* Threads the parallel loops use (1 when built without OpenMP). */
+int32_t or_get_threads(void) {
+#ifdef _OPENMP
+  return (int32_t)omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 int64_t or_num_blocks(int64_t n, int32_t bs) { return (n + bs - 1) / bs; }
 
@@ -73,6 +105,7 @@ void or_extract_block(int64_t n, const int32_t *row_ptr, const int32_t *col,
 void or_extract_blocks(int64_t n, const int32_t *row_ptr, const int32_t *col,
                        const double *val, int32_t bs, double *out) {
   int64_t nb = or_num_blocks(n, bs);
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
   for (int64_t k = 0; k < nb; ++k)
     or_extract_block(n, row_ptr, col, val, bs, k, out + k * (int64_t)bs * bs);
 }
@@ -111,12 +144,24 @@ int32_t or_cholesky(int32_t b, int32_t ld, const double *D, double *L, double to
 /* Factor every block.  Returns -1 if all blocks are SPD, else the first failing block. */
 int64_t or_cholesky_blocks(int64_t n, int32_t bs, const double *D, double *L, double tol) {
   int64_t nb = or_num_blocks(n, bs);
+  int64_t first = -1;
+  if (n < OR_PAR_MIN) {
+    for (int64_t k = 0; k < nb; ++k) {
+      int32_t b = block_rows(n, bs, k);
+      int32_t f = or_cholesky(b, bs, D + k * (int64_t)bs * bs, L + k * (int64_t)bs * bs, tol);
+      if (f >= 0) return k;
+    }
+    return -1;
+  }
+  /* every block is factored; the smallest failing index is the answer */
+  first = nb;
+#pragma omp parallel for schedule(static) reduction(min : first)
   for (int64_t k = 0; k < nb; ++k) {
     int32_t b = block_rows(n, bs, k);
     int32_t f = or_cholesky(b, bs, D + k * (int64_t)bs * bs, L + k * (int64_t)bs * bs, tol);
-    if (f >= 0) return k;
+    if (f >= 0 && k < first) first = k;
   }
-  return -1;
+  return first < nb ? first : -1;
 }
 
 /* L^{-1}: for each column c solve L y = e_c by forward substitution. */
@@ -145,12 +190,14 @@ void or_minv_from_linv(int32_t b, int32_t ld, const double *X, double *Minv) {
 
 void or_tri_inv_blocks(int64_t n, int32_t bs, const double *L, double *X) {
   int64_t nb = or_num_blocks(n, bs);
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
   for (int64_t k = 0; k < nb; ++k)
     or_tri_inv_lower(block_rows(n, bs, k), bs, L + k * (int64_t)bs * bs, X + k * (int64_t)bs * bs);
 }
 
 void or_minv_blocks(int64_t n, int32_t bs, const double *X, double *Minv) {
   int64_t nb = or_num_blocks(n, bs);
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
   for (int64_t k = 0; k < nb; ++k)
     or_minv_from_linv(block_rows(n, bs, k), bs, X + k * (int64_t)bs * bs, Minv + k * (int64_t)bs * bs);
 }
@@ -179,26 +226,31 @@ static void backward_block(int32_t b, int32_t ld, const double *L, const double 
 void or_block_apply(int64_t n, int32_t bs, const double *L, int32_t mode, const double *r,
                     double *z) {
   int64_t nb = or_num_blocks(n, bs);
-  double *y = (double *)malloc(sizeof(double) * bs);
-  for (int64_t k = 0; k < nb; ++k) {
-    int64_t s = k * (int64_t)bs;
-    int32_t b = block_rows(n, bs, k);
-    const double *Lk = L + k * (int64_t)bs * bs;
-    if (mode == 0) {
-      forward_block(b, bs, Lk, r + s, y);
-      backward_block(b, bs, Lk, y, z + s);
-    } else if (mode == 2) {
-      forward_block(b, bs, Lk, r + s, z + s);
-    } else {
-      backward_block(b, bs, Lk, r + s, z + s);
+#pragma omp parallel if (n >= OR_PAR_MIN)
+  {
+    double *y = (double *)malloc(sizeof(double) * bs);
+#pragma omp for schedule(static)
+    for (int64_t k = 0; k < nb; ++k) {
+      int64_t s = k * (int64_t)bs;
+      int32_t b = block_rows(n, bs, k);
+      const double *Lk = L + k * (int64_t)bs * bs;
+      if (mode == 0) {
+        forward_block(b, bs, Lk, r + s, y);
+        backward_block(b, bs, Lk, y, z + s);
+      } else if (mode == 2) {
+        forward_block(b, bs, Lk, r + s, z + s);
+      } else {
+        backward_block(b, bs, Lk, r + s, z + s);
+      }
     }
+    free(y);
   }
-  free(y);
 }
 
 /* ------------------------------------------------------------------------- */
 void or_spmv(int64_t n, const int32_t *row_ptr, const int32_t *col, const double *val,
              const double *x, double *y) {
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
   for (int64_t i = 0; i < n; ++i) {
     double s = 0.0;
     for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) s += val[e] * x[col[e]];
@@ -206,9 +258,33 @@ void or_spmv(int64_t n, const int32_t *row_ptr, const int32_t *col, const double
   }
 }
 
-double or_dot(int64_t n, const double *x, const double *y) {
+/* x.y: the terms of each chunk of OR_CHUNK entries added in index order, then the chunk
+ * sums added in chunk order. */
+static double dot_chunk(int64_t lo, int64_t hi, const double *x, const double *y) {
   double s = 0.0;
-  for (int64_t i = 0; i < n; ++i) s += x[i] * y[i];
+  for (int64_t i = lo; i < hi; ++i) s += x[i] * y[i];
+  return s;
+}
+
+static double dot_serial(int64_t n, const double *x, const double *y) {
+  double s = 0.0;
+  for (int64_t lo = 0; lo < n; lo += OR_CHUNK)
+    s += dot_chunk(lo, lo + OR_CHUNK < n ? lo + OR_CHUNK : n, x, y);
+  return s;
+}
+
+double or_dot(int64_t n, const double *x, const double *y) {
+  if (n < OR_PAR_MIN) return dot_serial(n, x, y);
+  int64_t nc = (n + OR_CHUNK - 1) / OR_CHUNK;
+  double *part = (double *)malloc(sizeof(double) * nc);
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < nc; ++c) {
+    int64_t lo = c * OR_CHUNK;
+    part[c] = dot_chunk(lo, lo + OR_CHUNK < n ? lo + OR_CHUNK : n, x, y);
+  }
+  double s = 0.0;
+  for (int64_t c = 0; c < nc; ++c) s += part[c];
+  free(part);
   return s;
 }
 
@@ -241,6 +317,7 @@ int32_t or_lanczos(int64_t n, const int32_t *row_ptr, const int32_t *col, const 
   if (L) or_block_apply(n, bs, L, 2, v0, q0);
   else memcpy(q0, v0, sizeof(double) * n);
   double nrm = sqrt(or_dot(n, q0, q0));
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
   for (int64_t i = 0; i < n; ++i) q0[i] = q0[i] / nrm;
   double tnorm = 0.0;
   int32_t steps = 0;
@@ -250,17 +327,27 @@ int32_t or_lanczos(int64_t n, const int32_t *row_ptr, const int32_t *col, const 
     else or_spmv(n, row_ptr, col, val, qj, w);
     if (j > 0) {
       double *qp = basis + (int64_t)(j - 1) * n;
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
       for (int64_t i = 0; i < n; ++i) w[i] -= beta[j - 1] * qp[i];
     }
     double a = or_dot(n, qj, w);
     alpha[j] = a;
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
     for (int64_t i = 0; i < n; ++i) w[i] -= a * qj[i];
     if (reorth) {
       for (int pass = 0; pass < 2; ++pass) {
-        for (int32_t l = 0; l <= j; ++l) c[l] = or_dot(n, basis + (int64_t)l * n, w);
-        for (int32_t l = 0; l <= j; ++l) {
-          const double *ql = basis + (int64_t)l * n;
-          for (int64_t i = 0; i < n; ++i) w[i] -= c[l] * ql[i];
+        /* c_l = q_l . w (each the chunked dot of or_dot, computed one per thread) */
+#pragma omp parallel for schedule(dynamic, 1) if (n >= OR_PAR_MIN)
+        for (int32_t l = 0; l <= j; ++l) c[l] = dot_serial(n, basis + (int64_t)l * n, w);
+        /* w -= sum_l c_l q_l: every w_i takes its subtractions in the order l = 0, 1, ..., j
+           (the loops run over chunks of i, then l, then i within the chunk) */
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
+        for (int64_t lo = 0; lo < n; lo += OR_CHUNK) {
+          int64_t hi = lo + OR_CHUNK < n ? lo + OR_CHUNK : n;
+          for (int32_t l = 0; l <= j; ++l) {
+            const double *ql = basis + (int64_t)l * n;
+            for (int64_t i = lo; i < hi; ++i) w[i] -= c[l] * ql[i];
+          }
         }
       }
     }
@@ -272,6 +359,7 @@ int32_t or_lanczos(int64_t n, const int32_t *row_ptr, const int32_t *col, const 
     if (bj <= tol * tnorm || j + 1 == m) break;
     if ((int64_t)(j + 1) >= n) break; /* the Krylov space is the whole space */
     double *qn = basis + (int64_t)(j + 1) * n;
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
     for (int64_t i = 0; i < n; ++i) qn[i] = w[i] / bj;
   }
   free(w); free(t1); free(t2); free(c);
@@ -341,15 +429,18 @@ int32_t or_pcg(int64_t n, const int32_t *row_ptr, const int32_t *col, const doub
   double rnorm = 0.0, tnorm = 0.0;
   int first_cycle = 1;
   if (bnorm == 0.0) {
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
     for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
     goto done;
   }
   for (;;) {
     /* (re)start: r = b - A x, z = M^{-1} r, p = z, rho = r.z */
     or_spmv(n, row_ptr, col, val, x, q);
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
     for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
     if (L) or_block_apply(n, bs, L, 0, r, z);
     else memcpy(z, r, sizeof(double) * n);
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
     for (int64_t i = 0; i < n; ++i) p[i] = z[i];
     double rho = or_dot(n, r, z);
     rnorm = sqrt(or_dot(n, r, r));
@@ -362,7 +453,9 @@ int32_t or_pcg(int64_t n, const int32_t *row_ptr, const int32_t *col, const doub
       if (!(pq > 0.0) || !isfinite(pq)) { status = OR_BREAKDOWN; goto done; }
       double alpha = rho / pq;
       if (first_cycle && alphas) alphas[it] = alpha;
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
       for (int64_t i = 0; i < n; ++i) x[i] += alpha * p[i];
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
       for (int64_t i = 0; i < n; ++i) r[i] -= alpha * q[i];
       ++it;
       rnorm = sqrt(or_dot(n, r, r));
@@ -373,10 +466,12 @@ int32_t or_pcg(int64_t n, const int32_t *row_ptr, const int32_t *col, const doub
       double beta = rho_new / rho;
       if (first_cycle && betas) betas[it - 1] = beta;
       rho = rho_new;
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
       for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
     }
     /* true residual check */
     or_spmv(n, row_ptr, col, val, x, q);
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
     for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
     tnorm = sqrt(or_dot(n, r, r));
     if (tnorm <= tol * bnorm) break;
@@ -390,6 +485,7 @@ done:
     out[1] = bnorm > 0.0 ? rnorm / bnorm : 0.0;
     if (bnorm > 0.0) {
       or_spmv(n, row_ptr, col, val, x, q);
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
       for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
       tnorm = sqrt(or_dot(n, r, r));
       out[2] = tnorm / bnorm;

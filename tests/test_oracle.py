@@ -318,6 +318,59 @@ def test_pcg_status_codes():
     assert r["status"] == "breakdown"
 
 
+def test_pcg_restart_is_a_fresh_start_from_the_current_iterate():
+    # 10^3 diffusion (sigma 2, bs 8) at tol 3e-13: the recurrence residual reaches tol while
+    # the true residual b - A x is still above it, so the solve restarts once.  A restart must
+    # be exactly a new solve from the current x (r = b - A x, z = M^-1 r, p = z, rho = r.z):
+    # the first cycle alone (no restarts allowed) followed by a solve from its x must give the
+    # same iterate bit for bit and the same total iteration count.
+    A = W.diffusion3d(10, 2.0)
+    b = W.rhs(A.n, 0)
+    tol = 3e-13
+    r = oracle.pcg(A, b, 8, tol)
+    assert r["status"] == "ok" and r["restarts"] >= 1
+    r1 = oracle.pcg(A, b, 8, tol, max_restarts=0)
+    assert r1["status"] == "no_convergence" and r1["true_rel_residual"] > tol
+    r2 = oracle.pcg(A, b, 8, tol, x0=r1["x"], max_restarts=r["restarts"] - 1)
+    assert r2["status"] == "ok"
+    assert r["iterations"] == r1["iterations"] + r2["iterations"]
+    assert np.array_equal(r["x"], r2["x"])
+    # and the restarted result is a solution: dense residual and forward error vs LAPACK
+    D = A.to_dense()
+    assert np.linalg.norm(b - D @ r["x"]) <= tol * np.linalg.norm(b)
+    x_ref = np.linalg.solve(D, b)
+    ev = np.linalg.eigvalsh(D)
+    assert np.linalg.norm(r["x"] - x_ref) <= 2 * tol * ev[-1] / ev[0] * np.linalg.norm(x_ref)
+
+
+def test_dot_is_independent_of_the_thread_count():
+    # the chunked dot adds chunk sums in a fixed order, so any thread count gives the same bits;
+    # the value is the exact sum to within the usual bound
+    x = np.random.default_rng(11).standard_normal(200_003)
+    y = np.random.default_rng(12).standard_normal(200_003)
+    vals = []
+    for t in (1, 3, 4):
+        oracle.set_threads(t)
+        vals.append(oracle.dot(x, y))
+    oracle.set_threads(1)
+    assert vals[0] == vals[1] == vals[2]
+    assert abs(vals[0] - math.fsum(x * y)) <= 1e-12 * np.abs(x * y).sum()
+
+
+def test_pcg_and_lanczos_are_independent_of_the_thread_count():
+    A = W.diffusion3d(40, 2.0)     # 64,000 rows: above the size where loops are shared
+    b = W.rhs(A.n, 0)
+    res = []
+    for t in (1, 4):
+        oracle.set_threads(t)
+        p = oracle.pcg(A, b, 16, 1e-10, max_iter=60)
+        k = oracle.kappa(A, b, 20, 16)
+        res.append((p["x"], p["iterations"], k["kappa"]))
+    oracle.set_threads(1)
+    assert np.array_equal(res[0][0], res[1][0]) and res[0][1] == res[1][1]
+    assert res[0][2] == res[1][2]
+
+
 def test_pcg_warm_start_from_solution():
     A = W.poisson2d(16)
     b = W.rhs(A.n, 0)
