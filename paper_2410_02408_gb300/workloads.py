@@ -17,6 +17,7 @@ Conventions
 from __future__ import annotations
 
 import math
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -256,7 +257,17 @@ def rgg_batch(n_sys: int = 512, seed: int = 3, n_min: float = 1e3, n_max: float 
     rng = np.random.default_rng(seed)
     sizes = np.floor(np.exp(rng.uniform(math.log(n_min), math.log(n_max), n_sys))).astype(np.int64)
     bss = rng.choice(np.asarray(block_sizes), n_sys)
-    systems = [rgg_laplacian(rng.random((int(N), 3))) for N in sizes]
+    points = [rng.random((int(N), 3)) for N in sizes]
+    workers = min(len(points), os.cpu_count() or 1, 16)
+    if workers > 1 and sum(p.shape[0] for p in points) >= 1_000_000:
+        # the Laplacians are independent: build them on worker threads (the neighbour search
+        # and the sparse assembly run in compiled code that releases the interpreter lock)
+        from concurrent.futures import ThreadPoolExecutor
+
+        with ThreadPoolExecutor(workers) as ex:
+            systems = list(ex.map(rgg_laplacian, points))
+    else:
+        systems = [rgg_laplacian(p) for p in points]
     return concat_batch(systems, bss)
 
 
@@ -282,17 +293,30 @@ def _powerlaw_exponent(w_min: int, w_max: int, mean: float) -> float:
 
 def powerlaw_spd(n: int = 8_000_000, seed: int = 5, w_min: int = 8, w_max: int = 1999,
                  mean_deg: float = 31.0, cap: int = 2000, rcm: bool = True,
-                 dtype=np.float32) -> CSR:
+                 dtype=np.float32, device=None) -> CSR:
     """Random sparse SPD with power-law row lengths.
 
     Expected off-diagonal degrees w_i follow a discrete power law on [w_min, w_max]
     whose exponent gives mean ``mean_deg``; edges are drawn Chung-Lu style (both ends
     proportional to w, sum(w)/2 draws), symmetrised, de-duplicated, self loops removed,
-    and rows are capped at ``cap`` entries including the diagonal.  Off-diagonal values
-    U(-1, 0) (rounded to float32), diagonal = sum |off| + 1e-2 formed from the rounded
-    off-diagonals and then rounded.  Rows are reverse-Cuthill-McKee reordered."""
-    import scipy.sparse as sp
+    and rows are capped at ``cap`` entries including the diagonal: an undirected edge is
+    dropped when it is not among the first cap - 1 edges of either end, edges of a node
+    being counted in the order (as the smaller end, by the other end), then (as the larger
+    end, by the other end).  Off-diagonal values U(-1, 0) (rounded to float32), diagonal =
+    sum |off| + 1e-2 formed from the rounded off-diagonals and then rounded.  Rows are
+    reverse-Cuthill-McKee reordered.
 
+    Every random number comes from ``default_rng(seed)`` on the host; the integer work (the
+    inverse-CDF lookups, sorting, de-duplication, ranking and the CSR assembly) runs as
+    torch operations on ``device`` (default: the GPU when one is present, else the host).
+    Each of them is exact, so the matrix is the same bit for bit on either device; the
+    floating-point row sums of the diagonal stay on the host (numpy, in entry order)."""
+    import scipy.sparse as sp
+    import torch
+
+    if device is None:
+        device = "cuda" if torch.cuda.is_available() else "cpu"
+    dev = torch.device(device)
     rng = np.random.default_rng(seed)
     g = _powerlaw_exponent(w_min, w_max, mean_deg)
     support = np.arange(w_min, w_max + 1, dtype=np.float64)
@@ -302,37 +326,40 @@ def powerlaw_spd(n: int = 8_000_000, seed: int = 5, w_min: int = 8, w_max: int =
     n_draw = int(round(w.sum() / 2.0))
     cdf = np.cumsum(w)
     cdf /= cdf[-1]
-    u = rng.random(n_draw)
-    a = np.searchsorted(cdf, u, side="right").astype(np.int64)
-    del u
-    u = rng.random(n_draw)
-    b = np.searchsorted(cdf, u, side="right").astype(np.int64)
-    del u
-    np.minimum(a, n - 1, out=a)
-    np.minimum(b, n - 1, out=b)
+    cdf_t = torch.from_numpy(cdf).to(dev)
+
+    def draw():
+        # node of each draw: the first index whose cumulative weight exceeds u
+        u = torch.from_numpy(rng.random(n_draw)).to(dev)
+        return torch.searchsorted(cdf_t, u, right=True).clamp_(max=n - 1)
+
+    a = draw()
+    b = draw()
     keep = a != b
-    lo = np.minimum(a[keep], b[keep])
-    hi = np.maximum(a[keep], b[keep])
-    del a, b, keep
-    key = np.unique(lo * n + hi)
-    del lo, hi
-    lo = key // n
-    hi = key % n
+    a = a[keep]
+    b = b[keep]
+    del keep
+    key = torch.unique(torch.minimum(a, b) * n + torch.maximum(a, b), sorted=True)
+    del a, b
+    lo = torch.div(key, n, rounding_mode="floor")
+    hi = key - lo * n
     del key
-    # cap: drop an undirected edge if it falls beyond the (cap-1)-th entry of either end
+    # cap: rank of every edge among the edges of each of its two ends (see above)
     deg_cap = cap - 1
-    ends = np.concatenate([lo, hi])
-    order = np.argsort(ends, kind="stable")
-    counts = np.bincount(ends, minlength=n)
-    starts = np.zeros(n + 1, dtype=np.int64)
-    np.cumsum(counts, out=starts[1:])
-    rank = np.empty_like(order)
-    rank[order] = np.arange(order.shape[0]) - np.repeat(starts[:-1], counts)
     m_e = lo.shape[0]
-    ok = (rank[:m_e] < deg_cap) & (rank[m_e:] < deg_cap)
-    del ends, order, rank, counts, starts
-    lo = lo[ok]
-    hi = hi[ok]
+    idx = torch.arange(m_e, device=dev)
+    cnt_lo = torch.bincount(lo, minlength=n)
+    rank_lo = idx - (torch.cumsum(cnt_lo, 0) - cnt_lo)[lo]          # lo is sorted
+    hs, order_h = torch.sort(hi, stable=True)
+    cnt_hi = torch.bincount(hi, minlength=n)
+    occ = torch.empty_like(hi)
+    occ[order_h] = idx - (torch.cumsum(cnt_hi, 0) - cnt_hi)[hs]
+    rank_hi = cnt_lo[hi] + occ
+    ok = (rank_lo < deg_cap) & (rank_hi < deg_cap)
+    del idx, cnt_lo, rank_lo, hs, order_h, cnt_hi, occ, rank_hi
+    lo = lo[ok].cpu().numpy()
+    hi = hi[ok].cpu().numpy()
+    del ok
     offv = (-rng.random(lo.shape[0])).astype(np.float32)
     rows = np.concatenate([lo, hi])
     cols = np.concatenate([hi, lo])
@@ -343,15 +370,33 @@ def powerlaw_spd(n: int = 8_000_000, seed: int = 5, w_min: int = 8, w_max: int =
     rows = np.concatenate([rows, np.arange(n, dtype=np.int64)])
     cols = np.concatenate([cols, np.arange(n, dtype=np.int64)])
     vals = np.concatenate([vals, diag])
-    M = sp.csr_matrix((vals, (rows.astype(np.int32), cols.astype(np.int32))), shape=(n, n), dtype=np.float32)
-    del rows, cols, vals
+    del absum, diag
+
+    def assemble(r, c, v):
+        # CSR of the entries (r, c, v) with the columns of every row in increasing order
+        rt = torch.from_numpy(r).to(dev)
+        k = rt * n + torch.from_numpy(c).to(dev)
+        k, order = torch.sort(k)
+        indptr = torch.zeros(n + 1, dtype=torch.int64, device=dev)
+        indptr[1:] = torch.cumsum(torch.bincount(rt, minlength=n), 0)
+        del rt
+        indices = (k - torch.div(k, n, rounding_mode="floor") * n).to(torch.int32)
+        data = torch.from_numpy(v).to(dev)[order]
+        return indptr.cpu().numpy(), indices.cpu().numpy(), data.cpu().numpy()
+
+    indptr, indices, data = assemble(rows, cols, vals)
     if rcm:
         from scipy.sparse.csgraph import reverse_cuthill_mckee
 
+        M = sp.csr_matrix((data, indices, indptr.astype(np.int32)), shape=(n, n))
         perm = reverse_cuthill_mckee(M, symmetric_mode=True)
-        M = M[perm][:, perm].tocsr()
-    M.sort_indices()
-    A = CSR(M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data.astype(dtype))
+        del M, indptr, indices, data
+        iperm = np.empty(n, dtype=np.int64)
+        iperm[perm] = np.arange(n, dtype=np.int64)
+        indptr, indices, data = assemble(iperm[rows], iperm[cols], vals)
+    if indptr[-1] >= 2**31:
+        raise ValueError("nnz exceeds int32 indexing")
+    A = CSR(indptr.astype(np.int32), indices, data.astype(dtype))
     A.meta = {"kind": "powerlaw", "n": n, "exponent": g, "seed": seed}
     return A
 
