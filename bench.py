@@ -3,15 +3,24 @@ diffusion workload (128^3 grid, 7-point stencil, log-normal face coefficients wi
 sigma = 2, b ~ N(0,1) seed 0), mixed precision (FP32 block factors, FP64 CG) against
 all-FP64.
 
-One step = pcg_solve through the C ABI: block extraction + batched block Cholesky/inverse
-(setup) and the CG solve (a CUDA graph with a device-driven loop) to ||r||/||b|| <= 1e-10
-with the true-residual check.  The line also carries the per-kernel breakdown, the roofline
-of the dominant kernel (the SpMV), the FP64-factor comparison, the Lanczos kappa estimates
-before and after preconditioning, the end-to-end figure and the oracle's CPU baseline.
+One step = pcg_solve through the C ABI: the CSR structure check, block extraction + batched
+block Cholesky/inverse (setup) and the CG solve (a CUDA graph with a device-driven loop) to
+||r||/||b|| <= 1e-10 with the true-residual check.  The headline line also carries:
 
-Other workloads (each prints its own line): --workload batched_rgg_512 (512 uneven RGG
-systems set up and solved in one persistent launch) and --workload powerlaw_8m (random SPD
-with power-law rows, FP32 values).
+* the per-kernel breakdown and the roofline of the dominant kernel (the SpMV);
+* the FP64-factor comparison and the block-size sweep (8/16/32/64);
+* the Lanczos kappa estimates before and after preconditioning;
+* the error of every result against the FP64 oracle's solution of the same system;
+* the end-to-end figure (host buffers through the C ABI);
+* the oracle's CPU baseline, single-threaded and on all host cores;
+* sub-objects for the other two throughput workloads (512 uneven RGG systems in one
+  persistent launch; the 8M-row power-law matrix with FP32 values), each with its own
+  roofline, clocks, iterations, residuals and oracle error;
+* the paper's own rows: point Jacobi (block size 1) setup + apply against the oracle, the
+  error of the decoupled per-block solve x = M^-1 b, and the paper-size sweep of kappa and
+  kappa^2 per block size.
+
+Single workloads print their own line: --workload batched_rgg_512, --workload powerlaw_8m.
 
 value   = algorithmic bytes of the step / step time (GB/s), inputs resident in HBM.
           bytes = setup (CSR read + factor writes) + per-solve extras (initial and final
@@ -21,7 +30,8 @@ e2e     = the same metric through the C ABI with host buffers: the CSR and b are
           from pinned host memory to the device and x back inside the timed region.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Under torchrun (N > 1) every rank solves its own replica (weak scaling).
+Under torchrun (N > 1) every rank solves its own replica (weak scaling); the sub-workloads,
+paper rows and oracle comparisons run at N = 1 only.
 """
 from __future__ import annotations
 
@@ -29,6 +39,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import re
 import statistics
 import subprocess
@@ -46,9 +57,13 @@ from paper_2410_02408_gb300 import workloads as W  # noqa: E402
 
 METRIC = "PCG+precond GB/s (% HBM peak), mixed vs FP64, to rel. residual 1e-10"
 FALLBACK_HBM_GBS = 6800.0
+# Launch shape of the batched workload when its autotuner is skipped (the shape the autotuner
+# picks for the 512-system batch in both precisions): CTAs per SM, team limit, slots per CTA,
+# setup shared memory (KB).
+BATCH_SHAPE_DEFAULT = "2,8,4,70"
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -63,7 +78,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-oracle-error", action="store_true", help="skip the full oracle solves (error vs oracle)")
+    ap.add_argument("--no-sub", action="store_true", help="headline: skip the batched and power-law sub-objects")
+    ap.add_argument("--no-paper-rows", action="store_true", help="headline: skip point Jacobi, decoupled solve, sweep")
+    ap.add_argument("--sub-steps", type=int, default=3, help="timed steps of each sub-workload")
     ap.add_argument("--cpu-sample-iters", type=int, default=0, help="oracle CG iterations per sample (0 = auto)")
+    ap.add_argument("--cpu-threads", type=int, default=0, help="oracle threads of the all-cores baseline (0 = all)")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="persistent CG CTAs per SM (0 = occupancy max)")
     ap.add_argument("--workload", default="diffusion3d", choices=["diffusion3d", "batched_rgg_512", "powerlaw_8m"],
                     help="diffusion3d: the headline 128^3 solve; batched_rgg_512: 512 uneven RGG systems "
@@ -86,7 +106,7 @@ def parse():
                     help="batched workload: one extra solve with per-phase device timers (not timed)")
     ap.add_argument("--profile", action="store_true",
                     help="one solve of the workload and nothing else (for ncu captures); prints a short line")
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
     args.bs_given = args.bs is not None
     if args.bs is None:
         args.bs = 16
@@ -280,20 +300,71 @@ def barrier(dist):
 
 
 # ---------------------------------------------------------------- oracle (CPU) timing
-def oracle_sample(A, b, bs, sample_iters):
-    """Oracle setup + a bounded number of CG iterations on the full matrix (single thread)."""
+def host_info():
+    """Host cores and CPU model (the timing host of the CPU baseline)."""
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            txt = f.read()
+        m = re.search(r"^model name\s*:\s*(.+)$", txt, re.M)
+        if m:
+            model = m.group(1).strip()
+        else:
+            parts = [re.search(rf"^{k}\s*:\s*(\S+)", txt, re.M) for k in ("CPU implementer", "CPU part")]
+            if all(parts):
+                model = f"{platform.machine()} implementer {parts[0].group(1)} part {parts[1].group(1)}"
+    except OSError:
+        pass
+    return {"nproc": cores, "cpu_model": model, "machine": platform.machine()}
+
+
+def oracle_threads(args):
+    return args.cpu_threads or host_info()["nproc"]
+
+
+def oracle_step_bytes(A, bs, iters):
+    """Algorithmic bytes of an oracle setup + iters CG iterations (FP64 factors, same B_it)."""
+    vb = 8
+    setup_b = csr_bytes(A.n, A.nnz, vb) + sum(factor_bytes(A.n, bs, 8))
+    _, b_it, _ = step_bytes(A.n, A.nnz, bs, "fp64", 0, vb)
+    return setup_b + iters * b_it
+
+
+def oracle_sample(A, b, bs, sample_iters, threads=1):
+    """Oracle setup + a bounded number of CG iterations on the full matrix."""
     import oracle
 
+    oracle.set_threads(threads)
     t0 = time.perf_counter()
     L, f = oracle.factor(A, bs)
     t1 = time.perf_counter()
     r = oracle.pcg(A, b, bs, 1e-10, max_iter=sample_iters, L=L)
     t2 = time.perf_counter()
+    used = oracle.threads()
+    oracle.set_threads(1)
     it = r["iterations"]
-    setup_b = csr_bytes(A.n, A.nnz, 8) + factor_bytes(A.n, bs, 8)[0] + factor_bytes(A.n, bs, 8)[1]
-    _, b_it, _ = step_bytes(A.n, A.nnz, bs, "fp64", 0)
-    byt = setup_b + it * b_it
-    return byt / (t2 - t0) / 1e9, {"setup_s": t1 - t0, "cg_s": t2 - t1, "iterations": it}
+    return oracle_step_bytes(A, bs, it) / (t2 - t0) / 1e9, {"setup_s": t1 - t0, "cg_s": t2 - t1,
+                                                           "iterations": it, "threads": used}
+
+
+def oracle_full(A, b, bs, threads):
+    """The oracle's complete FP64 setup + PCG to 1e-10 (the reference solution of the
+    error-vs-oracle figures), timed on the host cores."""
+    import oracle
+
+    oracle.set_threads(threads)
+    t0 = time.perf_counter()
+    r = oracle.pcg(A, b, bs, 1e-10)
+    s = time.perf_counter() - t0
+    used = oracle.threads()
+    oracle.set_threads(1)
+    return r, {"seconds": s, "threads": used, "iterations": r["iterations"], "status": r["status"],
+               "GBs": oracle_step_bytes(A, bs, r["iterations"]) / s / 1e9}
+
+
+def rel_err(x, ref):
+    return float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
 
 
 def run_reference(args):
@@ -304,20 +375,25 @@ def run_reference(args):
     args.bs = bs
     b = W.rhs(A.n, 0)
     iters = args.cpu_sample_iters or 8
+    threads = oracle_threads(args)
     vals = []
+    used = 1
     for s in range(args.warmup + args.steps):
-        v, meta = oracle_sample(A, b, args.bs, iters)
+        v, meta = oracle_sample(A, b, args.bs, iters, threads)
+        used = meta["threads"]
         if s >= args.warmup:
             vals.append(v)
     value = statistics.median(vals)
+    host = host_info()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wname, "n": A.n, "nnz": A.nnz,
                    "block_size": args.bs, "prec": "fp64"},
-        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": f"oracle setup + {iters} CG iterations on the full matrix per step"},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": used, "kind": "oracle",
+                         "sample": f"oracle FP64 setup + {iters} CG iterations on the full matrix per step, "
+                                   f"{used} threads", "host": host},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -355,6 +431,66 @@ def kappa_timing(pc, Ad, bd, bs, n, nnz, vb, steps=200):
     return out
 
 
+# ---------------------------------------------------------------- GPU helpers
+def timed_solves(pc, Ad, bd, bs, prec, args, steps, warmup):
+    """warmup + steps setup+solve calls (pcg_solve); returns (x, infos, ms over the timed steps)."""
+    import torch
+
+    st = torch.cuda.current_stream()
+    x = info = None
+    for _ in range(warmup):
+        x, info = pc.pcg(Ad, bd, bs, tol=args.tol, max_iter=args.maxit, prec=prec)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    infos = []
+    e0.record(st)
+    for _ in range(steps):
+        x, info = pc.pcg(Ad, bd, bs, tol=args.tol, max_iter=args.maxit, prec=prec)
+        infos.append(info)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return x, infos, e0.elapsed_time(e1)
+
+
+def kernel_times(pc, Ad, bd, bs, prec, args):
+    """Per-kernel device times of the CG loop: one extra (untimed) solve in profiling mode, where
+    the loop-body kernels are launched one by one with CUDA events around each on the current
+    stream.  Returns (spmv_us, precond_us, update_us, spmv_order)."""
+    os.environ["PC_CG_PROFILE"] = "1"
+    try:
+        hp = pc.setup(Ad, bs, prec=prec)
+        hp.pcg(bd, tol=args.tol, max_iter=args.maxit)
+        kt = hp.trace(8)
+        order = {"binned": hp.row_binned(), "col_segments": hp.col_segments()}
+        hp.destroy()
+    finally:
+        del os.environ["PC_CG_PROFILE"]
+    us = [float(kt[i]) / 1e3 for i in range(3)] if len(kt) >= 3 else [0.0, 0.0, 0.0]
+    return us[0], us[1], us[2], order
+
+
+def kernel_table(n, nnz, vb, bs, prec, spmv_us, prec_us, upd_us, peak, peak_kind, traffic, kernel_name):
+    fb = 4 if prec != "fp64" else 8
+    spmv_bytes = csr_bytes(n, nnz, vb) + 2 * 8 * n                      # CSR, p (read once), q
+    prec_bytes = factor_bytes(n, bs, fb)[0] + 4 * 8 * n                   # M^{-1}, r, q in; r, z out
+    upd_bytes = 5 * 8 * n                                                 # x, p, z in; x, p out
+    gbs = lambda b, us: b / (us * 1e-6) / 1e9 if us > 0 else 0.0        # noqa: E731
+    achieved = gbs(spmv_bytes, spmv_us)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel_name,
+                "algorithmic_bytes_per_launch": spmv_bytes, "avg_launch_us": spmv_us}
+    kernels = {
+        "spmv": {"us": spmv_us, "GBs": achieved, "bytes": spmv_bytes},
+        "precond": {"us": prec_us, "GBs": gbs(prec_bytes, prec_us), "bytes": prec_bytes,
+                    "frac": gbs(prec_bytes, prec_us) / peak},
+        "update": {"us": upd_us, "GBs": gbs(upd_bytes, upd_us), "bytes": upd_bytes,
+                   "frac": gbs(upd_bytes, upd_us) / peak},
+        "note": "profiling-mode launches (events around each kernel), includes per-launch overhead",
+    }
+    return roofline, kernels
+
+
 # ---------------------------------------------------------------- GPU arm
 def run_ours(args):
     import torch
@@ -376,16 +512,12 @@ def run_ours(args):
     Ad = pc.csr(A)
     bd = torch.from_numpy(b).cuda()
     n, nnz = A.n, A.nnz
-
-    def solve(prec):
-        x, info = pc.pcg(Ad, bd, args.bs, tol=args.tol, max_iter=args.maxit, prec=prec)
-        return x, info
+    st = torch.cuda.current_stream()
 
     for _ in range(args.warmup):
-        x, info = solve(args.prec)
+        x, info = pc.pcg(Ad, bd, args.bs, tol=args.tol, max_iter=args.maxit, prec=args.prec)
     torch.cuda.synchronize()
     barrier(dist)
-    st = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     infos = []
@@ -394,7 +526,7 @@ def run_ours(args):
         barrier(dist)
         e0.record(st)
         for _ in range(args.steps):
-            x, info = solve(args.prec)
+            x, info = pc.pcg(Ad, bd, args.bs, tol=args.tol, max_iter=args.maxit, prec=args.prec)
             infos.append(info)
         e1.record(st)
         torch.cuda.synchronize()
@@ -403,48 +535,22 @@ def run_ours(args):
     ms_total = max_over_ranks(ms_total, dist)
     ms_step = ms_total / args.steps
     iters = infos[-1]["iterations"]
-    total_bytes = 0
-    for inf in infos:
-        sb, b_it, kb = step_bytes(n, nnz, args.bs, args.prec, inf["iterations"], vb)
-        total_bytes += sb
+    total_bytes = sum(step_bytes(n, nnz, args.bs, args.prec, inf["iterations"], vb)[0] for inf in infos)
     value = total_bytes * ws / (ms_total / 1e3) / 1e9
     solve_ms = statistics.mean(i["solve_ms"] for i in infos)
     peak, peak_kind = measured_hbm()
     _, b_it, _ = step_bytes(n, nnz, args.bs, args.prec, iters, vb)
-    # Per-kernel times: one extra (untimed) solve in profiling mode, where the loop-body
-    # kernels are launched one by one with CUDA events around each on the current stream.
-    os.environ["PC_CG_PROFILE"] = "1"
-    hp = pc.setup(Ad, args.bs, prec=args.prec)
-    hp.pcg(bd, tol=args.tol, max_iter=args.maxit)
-    kt = hp.trace(8)
-    spmv_order = {"binned": hp.row_binned(), "col_segments": hp.col_segments()}
-    hp.destroy()
-    del os.environ["PC_CG_PROFILE"]
-    spmv_us, prec_us, upd_us = (float(kt[0]) / 1e3, float(kt[1]) / 1e3, float(kt[2]) / 1e3) if len(kt) >= 3 else (0.0, 0.0, 0.0)
-    fb = 4 if args.prec != "fp64" else 8
-    spmv_bytes = csr_bytes(n, nnz, vb) + 2 * 8 * n                      # CSR, p (read once), q
-    prec_bytes = factor_bytes(n, args.bs, fb)[0] + 4 * 8 * n              # M^{-1}, r, q in; r, z out
-    upd_bytes = 5 * 8 * n                                                 # x, p, z in; x, p out
-    # dominant kernel (largest share of the iteration): the SpMV q = A p with the p.q reduction
-    achieved = spmv_bytes / (spmv_us * 1e-6) / 1e9 if spmv_us > 0 else 0.0
+    spmv_us, prec_us, upd_us, spmv_order = kernel_times(pc, Ad, bd, args.bs, args.prec, args)
     traffic = profiled_traffic(args.bs, args.prec) if args.workload == "diffusion3d" else None
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_kind": peak_kind,
-                "kernel": "cg_spmv_kernel (q = A p and p.q; one launch per CG iteration)",
-                "algorithmic_bytes_per_launch": spmv_bytes, "avg_launch_us": spmv_us}
-    kernels = {
-        "spmv": {"us": spmv_us, "GBs": achieved, "bytes": spmv_bytes},
-        "precond": {"us": prec_us, "GBs": prec_bytes / (prec_us * 1e-6) / 1e9 if prec_us > 0 else 0.0,
-                    "bytes": prec_bytes},
-        "update": {"us": upd_us, "GBs": upd_bytes / (upd_us * 1e-6) / 1e9 if upd_us > 0 else 0.0,
-                   "bytes": upd_bytes},
-        "note": "profiling-mode launches (events around each kernel), includes per-launch overhead",
-    }
-    # launches of this library's kernels per step: setup; the row-length statistic (auto row
-    # order) and, when binned, the binning, cost split (3) and segment bounds; per round I1,
-    # I2, arm, T; 3 per iteration
+    kname = ("cg_spmv_bin_pipe_kernel (binned rows; q = A p and p.q; one launch per CG iteration)"
+             if spmv_order["binned"] else "cg_spmv_kernel (q = A p and p.q; one launch per CG iteration)")
+    roofline, kernels = kernel_table(n, nnz, vb, args.bs, args.prec, spmv_us, prec_us, upd_us, peak, peak_kind,
+                                     traffic, kname)
+    # launches of this library's kernels per step: the CSR check, setup; the row-length statistic
+    # (auto row order) and, when binned, the binning, cost split (3) and segment bounds; per
+    # round I1, I2, arm, T; 3 per iteration
     order_launches = (1 if args.row_binning == "auto" else 0) + (5 if spmv_order["binned"] else 0)
-    launches = sum(1 + order_launches + 4 * (i["restarts"] + 1) + 3 * i["iterations"] for i in infos)
+    launches = sum(2 + order_launches + 4 * (i["restarts"] + 1) + 3 * i["iterations"] for i in infos)
     xr = x.cpu().numpy()
     true_res = float(np.linalg.norm(b - A.to_scipy() @ xr) / np.linalg.norm(b))   # report only
 
@@ -467,23 +573,12 @@ def run_ours(args):
         "gpu_launches": launches,
     }
     line["clocks"] = clk.summary()
+    x_fp64 = None
 
     if rank == 0 and not args.no_fp64_compare and args.prec != "fp64":
-        torch.cuda.synchronize()
-        solve("fp64")
-        torch.cuda.synchronize()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(st)
-        reps = 2
-        finf = []
-        for _ in range(reps):
-            _, fi = solve("fp64")
-            finf.append(fi)
-        t1.record(st)
-        torch.cuda.synchronize()
-        fms = t0.elapsed_time(t1) / reps
-        fb = sum(step_bytes(n, nnz, args.bs, "fp64", fi["iterations"], vb)[0] for fi in finf) / reps
+        x_fp64, finf, fms_total = timed_solves(pc, Ad, bd, args.bs, "fp64", args, 2, 1)
+        fms = fms_total / 2
+        fb = sum(step_bytes(n, nnz, args.bs, "fp64", fi["iterations"], vb)[0] for fi in finf) / 2
         line["fp64"] = {"value": fb / (fms / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": fms,
                         "iterations": finf[-1]["iterations"], "solve_ms": finf[-1]["solve_ms"],
                         "setup_ms": finf[-1]["setup_ms"]}
@@ -498,15 +593,8 @@ def run_ours(args):
         for bsz in (8, 16, 32, 64):
             row = {}
             for prec in ("fp32", "fp64"):
-                pc.pcg(Ad, bd, bsz, tol=args.tol, max_iter=args.maxit, prec=prec)
-                torch.cuda.synchronize()
-                t0 = torch.cuda.Event(enable_timing=True)
-                t1 = torch.cuda.Event(enable_timing=True)
-                t0.record(st)
-                _, si = pc.pcg(Ad, bd, bsz, tol=args.tol, max_iter=args.maxit, prec=prec)
-                t1.record(st)
-                torch.cuda.synchronize()
-                sms = t0.elapsed_time(t1)
+                _, si, sms = timed_solves(pc, Ad, bd, bsz, prec, args, 1, 1)
+                si = si[-1]
                 sb = step_bytes(n, nnz, bsz, prec, si["iterations"], vb)[0]
                 row["mixed" if prec == "fp32" else "fp64"] = {
                     "ms": sms, "iterations": si["iterations"], "GBs": sb / (sms / 1e3) / 1e9,
@@ -516,49 +604,235 @@ def run_ours(args):
         line["bs_sweep"] = sweep
 
     if not args.no_e2e:
-        # end to end through the C ABI from pinned host buffers
-        hrp = torch.from_numpy(A.row_ptr).pin_memory()
-        hci = torch.from_numpy(A.col).pin_memory()
-        hva = torch.from_numpy(A.val).pin_memory()
-        hb = torch.from_numpy(b).pin_memory()
-        hx = torch.empty(n, dtype=torch.float64).pin_memory()
-        drp = torch.empty_like(hrp, device="cuda")
-        dci = torch.empty_like(hci, device="cuda")
-        dva = torch.empty_like(hva, device="cuda")
-        db = torch.empty_like(hb, device="cuda")
-        h2d = sum(t.numel() * t.element_size() for t in (hrp, hci, hva, hb))
-        d2h = hx.numel() * hx.element_size()
-        torch.cuda.synchronize()
-        barrier(dist)
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(st)
-        eb = 0
-        ksteps = max(1, min(args.steps, 3))
-        for _ in range(ksteps):
-            drp.copy_(hrp, non_blocking=True)
-            dci.copy_(hci, non_blocking=True)
-            dva.copy_(hva, non_blocking=True)
-            db.copy_(hb, non_blocking=True)
-            xd, ei = pc.pcg(pc.CSR(drp, dci, dva), db, args.bs, tol=args.tol, max_iter=args.maxit, prec=args.prec)
-            hx.copy_(xd, non_blocking=True)
-            eb += step_bytes(n, nnz, args.bs, args.prec, ei["iterations"], vb)[0]
-        t1.record(st)
-        torch.cuda.synchronize()
-        ems = max_over_ranks(t0.elapsed_time(t1), dist)
-        line["e2e"] = {"value": eb * ws / (ems / 1e3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
-                       "d2h_bytes_per_step": d2h, "ms_per_step": ems / ksteps}
+        line["e2e"] = e2e_single(pc, A, b, args, dist, ws)
 
-    if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        sample = args.cpu_sample_iters or 8
-        v, meta = oracle_sample(A, b, args.bs, sample)
-        line["cpu_baseline"] = {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                                "sample": f"oracle FP64 setup + {meta['iterations']} CG iterations on the full "
-                                          f"matrix ({meta['setup_s'] + meta['cg_s']:.1f} s)"}
+    if rank == 0 and ws == 1:
+        host = host_info()
+        modes = {}
+        if not args.no_cpu_baseline:
+            sample = args.cpu_sample_iters or 8
+            v1, m1 = oracle_sample(A, b, args.bs, sample, 1)
+            modes["single"] = {"value": v1, "cores": m1["threads"],
+                               "sample": f"oracle FP64 setup + {m1['iterations']} CG iterations on the full "
+                                         f"matrix ({m1['setup_s'] + m1['cg_s']:.1f} s)"}
+            line["cpu_baseline"] = {"value": v1, "unit": "GB/s", "cores": m1["threads"], "kind": "oracle",
+                                    "sample": modes["single"]["sample"], "host": host, "modes": modes}
+        if not args.no_oracle_error:
+            o, om = oracle_full(A, b, args.bs, oracle_threads(args))
+            modes["all_cores"] = {"value": om["GBs"], "cores": om["threads"],
+                                  "sample": f"oracle FP64 setup + PCG to 1e-10 ({om['iterations']} iterations, "
+                                            f"{om['seconds']:.1f} s)", "seconds_to_solution": om["seconds"]}
+            if "cpu_baseline" in line:
+                line["cpu_baseline"].update({"value": om["GBs"], "cores": om["threads"],
+                                             "sample": modes["all_cores"]["sample"]})
+            errs = {"mixed" if args.prec != "fp64" else "fp64": rel_err(xr, o["x"])}
+            if x_fp64 is not None:
+                errs["fp64"] = rel_err(x_fp64.cpu().numpy(), o["x"])
+            errs["oracle_iterations"] = o["iterations"]
+            errs["note"] = "||x - x_oracle|| / ||x_oracle||, x_oracle = the oracle's FP64 PCG to the same tolerance"
+            line["err_vs_fp64_oracle"] = errs
+            line["speedup_vs_oracle_all_cores"] = om["seconds"] * 1e3 / ms_step
+
+    if rank == 0 and ws == 1 and args.workload == "diffusion3d" and not args.no_paper_rows:
+        line["paper_rows"] = paper_rows(pc, A, b, Ad, bd, args)
+
+    if rank == 0 and ws == 1 and args.workload == "diffusion3d" and not args.no_sub:
+        sub = {}
+        sub["batched_rgg_512"] = batched_result(pc, args, args.sub_steps, 1, tune=False)
+        sub["powerlaw_8m"] = powerlaw_result(pc, args, args.sub_steps, 1)
+        line["sub_workloads"] = sub
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def e2e_single(pc, A, b, args, dist, ws):
+    """End to end through the C ABI from pinned host buffers: CSR and b copied in, x out."""
+    import torch
+
+    st = torch.cuda.current_stream()
+    n, nnz, vb = A.n, A.nnz, A.val.dtype.itemsize
+    hrp = torch.from_numpy(A.row_ptr).pin_memory()
+    hci = torch.from_numpy(A.col).pin_memory()
+    hva = torch.from_numpy(A.val).pin_memory()
+    hb = torch.from_numpy(b).pin_memory()
+    hx = torch.empty(n, dtype=torch.float64).pin_memory()
+    drp = torch.empty_like(hrp, device="cuda")
+    dci = torch.empty_like(hci, device="cuda")
+    dva = torch.empty_like(hva, device="cuda")
+    db = torch.empty_like(hb, device="cuda")
+    h2d = sum(t.numel() * t.element_size() for t in (hrp, hci, hva, hb))
+    d2h = hx.numel() * hx.element_size()
+    torch.cuda.synchronize()
+    barrier(dist)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(st)
+    eb = 0
+    ksteps = max(1, min(args.steps, 3))
+    for _ in range(ksteps):
+        drp.copy_(hrp, non_blocking=True)
+        dci.copy_(hci, non_blocking=True)
+        dva.copy_(hva, non_blocking=True)
+        db.copy_(hb, non_blocking=True)
+        xd, ei = pc.pcg(pc.CSR(drp, dci, dva), db, args.bs, tol=args.tol, max_iter=args.maxit, prec=args.prec)
+        hx.copy_(xd, non_blocking=True)
+        eb += step_bytes(n, nnz, args.bs, args.prec, ei["iterations"], vb)[0]
+    t1.record(st)
+    torch.cuda.synchronize()
+    ems = max_over_ranks(t0.elapsed_time(t1), dist)
+    return {"value": eb * ws / (ems / 1e3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": ems / ksteps}
+
+
+# ---------------------------------------------------------------- the paper's own rows
+def paper_rows(pc, A, b, Ad, bd, args):
+    """Point Jacobi (block size 1: the paper's preconditioner, Sec. 3.3 and its CUDA kernel in
+    Sec. 4.3) setup + apply throughput against the oracle; the error of the paper's decoupled
+    per-block solve x = M^-1 b (Sec. 3.2 and 3.6 solve the blocks independently) against the PCG
+    solution; the paper-size sweep of kappa and kappa^2 (the HHL cost driver of Sec. 3.4) per
+    block size (Sec. 5.1: N in {2^10, 2^12, 2^14})."""
+    out = {}
+    out["point_jacobi_bs1"] = point_jacobi_row(pc, A, b, Ad, bd, args)
+    out["decoupled_solve"] = decoupled_row(pc, args)
+    out["paper_size_sweep"] = paper_sweep(pc)
+    return out
+
+
+def point_jacobi_row(pc, A, b, Ad, bd, args):
+    """GPU setup (CSR check + diagonal extraction + 1x1 'factor') and one application
+    z = D^-1 r, against the oracle's setup + apply on the host cores, FP64 throughout.
+    Bytes: setup = CSR + the two stored factor arrays; apply = factor + 2 vectors."""
+    import torch
+
+    import oracle
+
+    st = torch.cuda.current_stream()
+    n, nnz, vb = A.n, A.nnz, A.val.dtype.itemsize
+    Fm, Fl = factor_bytes(n, 1, 8)
+    setup_b = csr_bytes(n, nnz, vb) + Fm + Fl
+    apply_b = Fm + 16 * n
+    for _ in range(2):
+        pc.setup(Ad, 1, prec="fp64").destroy()
+    torch.cuda.synchronize()
+    reps = 10
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(st)
+    for _ in range(reps):
+        H = pc.setup(Ad, 1, prec="fp64")
+        H.destroy()
+    e1.record(st)
+    torch.cuda.synchronize()
+    H = pc.setup(Ad, 1, prec="fp64")
+    z = torch.empty_like(bd)
+    H.apply("inv", bd, out=z)
+    torch.cuda.synchronize()
+    e1b = torch.cuda.Event(enable_timing=True)
+    e1b.record(st)
+    for _ in range(reps * 5):
+        H.apply("inv", bd, out=z)
+    e2.record(st)
+    torch.cuda.synchronize()
+    setup_ms = e0.elapsed_time(e1) / reps
+    apply_ms = e1b.elapsed_time(e2) / (reps * 5)
+    zr = z.cpu().numpy()
+    H.destroy()
+    row = {"gpu": {"setup_ms": setup_ms, "apply_ms": apply_ms,
+                   "setup_GBs": setup_b / (setup_ms / 1e3) / 1e9, "apply_GBs": apply_b / (apply_ms / 1e3) / 1e9,
+                   "note": "setup = pc_setup + pc_destroy (CSR check, extraction, factor allocation and writes)"}}
+    for mode, threads in (("single", 1), ("all_cores", oracle_threads(args))):
+        oracle.set_threads(threads)
+        t0 = time.perf_counter()
+        L, _ = oracle.factor(A, 1)
+        t1 = time.perf_counter()
+        k = 3
+        for _ in range(k):
+            zo = oracle.apply(A, L, 1, oracle.MODE_INV, b)
+        t2 = time.perf_counter()
+        row[mode] = {"setup_ms": (t1 - t0) * 1e3, "apply_ms": (t2 - t1) * 1e3 / k, "cores": oracle.threads()}
+        oracle.set_threads(1)
+    row["max_abs_diff_vs_oracle"] = float(np.max(np.abs(zr - zo)))
+    for mode in ("single", "all_cores"):
+        row[f"speedup_vs_{mode}"] = {"setup": row[mode]["setup_ms"] / setup_ms,
+                                     "apply": row[mode]["apply_ms"] / apply_ms,
+                                     "setup_plus_apply": (row[mode]["setup_ms"] + row[mode]["apply_ms"]) /
+                                                         (setup_ms + apply_ms)}
+    row["workload"] = "diffusion3d 128^3 sigma 2 (the headline matrix), FP64"
+    row["paper"] = "Sec. 5.3.1 reports up to 15x for its CUDA point-Jacobi preconditioning over CPU (GPU, CPU unstated)"
+    return row
+
+
+def decoupled_row(pc, args):
+    """x_dec = M^-1 b (each block solved on its own, the solution the paper assembles from the
+    blocks) against the PCG solution x of the full system: ||x_dec - x|| / ||x|| and the
+    residual ||b - A x_dec|| / ||b||, per block size, FP64 factors."""
+    import torch
+
+    out = {}
+    for wname, A in (("poisson2d_64", W.poisson2d(64)), ("diffusion3d_128_sigma2", W.diffusion3d(128, 2.0))):
+        b = W.rhs(A.n, 0)
+        Ad = pc.csr(A)
+        bd = torch.from_numpy(b).cuda()
+        Asp = A.to_scipy()
+        rows = {}
+        for bs in (1, 8, 16, 32, 64):
+            H = pc.setup(Ad, bs, prec="fp64")
+            try:
+                xd = H.apply("inv", bd).cpu().numpy()
+                x, info = H.pcg(bd, tol=args.tol, max_iter=args.maxit)
+            finally:
+                H.destroy()
+            x = x.cpu().numpy()
+            rows[str(bs)] = {"err_vs_pcg": rel_err(xd, x),
+                             "rel_residual": float(np.linalg.norm(b - Asp @ xd) / np.linalg.norm(b)),
+                             "pcg_iterations": info["iterations"]}
+        out[wname] = rows
+    return out
+
+
+def paper_sweep(pc):
+    """kappa before and after block-Jacobi preconditioning and the kappa^2 reduction (HHL's cost
+    grows as kappa^2, Sec. 3.4) at the paper's sizes N = 2^10, 2^12, 2^14 (Sec. 5.1): 2D Poisson
+    and random SPD matrices of three densities (power-law recipe, mean off-diagonal degree 4,
+    8, 16).  Lanczos with min(N, 200) steps and CGS2; PCG iterations to 1e-10 per block size."""
+    import torch
+
+    out = {}
+    for N in (1024, 4096, 16384):
+        mats = [(f"poisson2d_{int(round(N ** 0.5))}", W.poisson2d(int(round(N ** 0.5))))]
+        for d in (4, 8, 16):
+            mats.append((f"random_spd_deg{d}", random_spd(N, d)))
+        res = {}
+        for name, A in mats:
+            b = W.rhs(A.n, 0)
+            Ad = pc.csr(A)
+            bd = torch.from_numpy(b).cuda()
+            m = min(A.n, 200)
+            kb = pc.kappa(Ad, bd, 0, max_steps=m)
+            row = {"nnz": A.nnz, "kappa_before": kb["kappa"], "steps": kb["steps"], "by_bs": {}}
+            for bs in (1, 4, 16, 64):
+                H = pc.setup(Ad, bs, prec="fp64")
+                try:
+                    ka = H.kappa(bd, max_steps=m)
+                    _, info = H.pcg(bd, tol=1e-10)
+                finally:
+                    H.destroy()
+                row["by_bs"][str(bs)] = {"kappa_after": ka["kappa"],
+                                         "kappa2_reduction": (kb["kappa"] / ka["kappa"]) ** 2,
+                                         "pcg_iterations": info["iterations"]}
+            res[name] = row
+        out[str(N)] = res
+    return out
+
+
+def random_spd(n, mean_deg, seed=11):
+    """The paper-size random SPD family: the power-law recipe (Chung-Lu edges, U(-1,0)
+    off-diagonals, diagonal = row |sum| + 1e-2, RCM order) with a given mean degree."""
+    w_min = 2
+    w_max = max(mean_deg + 1, min(1999, n // 4))
+    return W.powerlaw_spd(n, seed=seed, w_min=w_min, w_max=w_max, mean_deg=float(mean_deg), cap=min(2000, n),
+                          dtype=np.float64)
 
 
 # ---------------------------------------------------------------- batched workload
@@ -579,12 +853,11 @@ def batch_step_bytes(batch, prec, iters, restarts):
     return total
 
 
-def run_batched(args):
+def batched_result(pc, args, steps, warmup, tune=True):
+    """Setup + PCG of the 512 uneven RGG systems in one persistent launch: the figures of one
+    JSON line (returned as a dict)."""
     import torch
 
-    import paper_2410_02408_gb300 as pc
-
-    pc.load()
     t0 = time.time()
     batch = W.rgg_batch(n_sys=args.n_sys, seed=3)
     gen_s = time.time() - t0
@@ -595,21 +868,22 @@ def run_batched(args):
     st = torch.cuda.current_stream()
     peak, peak_kind = measured_hbm()
     tuning = {}
-    if args.batch_shape:
-        occ, team, split, kb = args.batch_shape.split(",")
+    shape = args.batch_shape or ("" if tune and not args.no_tune else BATCH_SHAPE_DEFAULT)
+    if shape:
+        occ, team, split, kb = shape.split(",")
         pc.batch_set_tuning(int(occ), int(team), float(split))
         pc.binding.lib().pc_batch_set_setup_smem(int(kb))
-        tuning["explicit"] = args.batch_shape
-    elif not args.no_tune:
+        tuning["explicit"] = shape
+    else:
         for prec in ([args.prec, "fp64"] if args.prec != "fp64" and not args.no_fp64_compare else [args.prec]):
             t0 = time.time()
             tms, cfg = pc.batch_autotune(batch, bd, args.tol, args.maxit, prec, args.tune_trials)
             tuning[prec] = {"best_ms": tms, "config": cfg, "tuning_s": time.time() - t0}
 
-    def timed(prec, steps, warmup):
+    def timed(prec, nsteps, nwarm):
         H = pc.Batch(batch, prec)
         x = torch.empty_like(bd)
-        for _ in range(warmup):
+        for _ in range(nwarm):
             H.solve(bd, args.tol, args.maxit, x=x)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -617,7 +891,7 @@ def run_batched(args):
         per = info = None
         kms = []
         e0.record(st)
-        for _ in range(steps):
+        for _ in range(nsteps):
             _, per, info = H.solve(bd, args.tol, args.maxit, x=x)
             kms.append(info["solve_ms"])
         e1.record(st)
@@ -625,20 +899,18 @@ def run_batched(args):
         li = H.launch_info()
         team, _ = H.teams()
         H.destroy()
-        ms = e0.elapsed_time(e1) / steps
+        ms = e0.elapsed_time(e1) / nsteps
         return x, per, info, ms, statistics.mean(kms), li, team
 
     with ClockSampler(0) as clk:
-        x, per, info, ms, kms, li, team = timed(args.prec, args.steps, args.warmup)
+        x, per, info, ms, kms, li, team = timed(args.prec, steps, warmup)
     restarts = np.zeros(batch.n_sys, dtype=np.int64)   # per-system restarts are not exported; bytes omit them
     step_b = batch_step_bytes(batch, args.prec, per["iterations"], restarts)
     value = step_b / (ms / 1e3) / 1e9
     achieved = step_b / (kms / 1e3) / 1e9
     it = per["iterations"]
-    line = {
-        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+    res = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "ms_per_step": ms, "steps": steps, "warmup": warmup,
         "config": {"workload": f"batched_rgg_{batch.n_sys}", "n_sys": batch.n_sys, "rows": n_rows, "nnz": nnz,
                    "block_sizes": "per system from {4,8,16,32,64}",
                    "prec": "mixed (fp32 factors, fp64 CG)" if args.prec != "fp64" else "fp64", "tol": args.tol,
@@ -653,9 +925,10 @@ def run_batched(args):
                      "kernel": "batched_kernel (setup + PCG of every system, one persistent launch)",
                      "algorithmic_bytes_per_launch": step_b, "avg_launch_us": kms * 1e3},
         "launch": li, "teams": {"multi_cta_systems": int((team > 1).sum()), "max_team": int(team.max())},
-        "graph": bool(info["graph"]), "gpu_launches": 2 * args.steps, "generation_s": gen_s, "autotune": tuning,
+        "graph": bool(info["graph"]), "gpu_launches": 2 * steps, "generation_s": gen_s, "autotune": tuning,
     }
-    line["clocks"] = clk.summary()
+    res["clocks"] = clk.summary()
+    x_mixed = x.cpu().numpy()
     if args.phase_profile:
         os.environ["PC_BATCH_PROFILE"] = "1"
         Hp = pc.Batch(batch, args.prec)
@@ -664,13 +937,15 @@ def run_batched(args):
         Hp.destroy()
         del os.environ["PC_BATCH_PROFILE"]
         tot = sum(prof.values()) or 1
-        line["phase_profile"] = {k: {"cta_ms": v / 1e6, "share": v / tot} for k, v in prof.items()}
+        res["phase_profile"] = {k: {"cta_ms": v / 1e6, "share": v / tot} for k, v in prof.items()}
+    x64 = None
     if args.prec != "fp64" and not args.no_fp64_compare:
-        _, per64, info64, ms64, kms64, _, _ = timed("fp64", max(1, min(args.steps, 2)), 1)
+        x64t, per64, info64, ms64, kms64, _, _ = timed("fp64", max(1, min(steps, 2)), 1)
+        x64 = x64t.cpu().numpy()
         b64 = batch_step_bytes(batch, "fp64", per64["iterations"], restarts)
-        line["fp64"] = {"value": b64 / (ms64 / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": ms64,
-                        "iterations_sum": int(per64["iterations"].sum()), "status": info64["status_name"]}
-        line["mixed_speedup_vs_fp64"] = ms64 / ms
+        res["fp64"] = {"value": b64 / (ms64 / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": ms64,
+                       "iterations_sum": int(per64["iterations"].sum()), "status": info64["status_name"]}
+        res["mixed_speedup_vs_fp64"] = ms64 / ms
     if not args.no_e2e:
         hb = torch.from_numpy(b).pin_memory()
         hx = torch.empty(n_rows, dtype=torch.float64).pin_memory()
@@ -684,7 +959,7 @@ def run_batched(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(st)
-        k = max(1, min(args.steps, 3))
+        k = max(1, min(steps, 3))
         for _ in range(k):
             H.row_ptr.copy_(hrp, non_blocking=True)
             H.col.copy_(hci, non_blocking=True)
@@ -697,32 +972,112 @@ def run_batched(args):
         H.destroy()
         ems = e0.elapsed_time(e1) / k
         h2d = sum(t.numel() * t.element_size() for t in (hrp, hci, hva, hb))
-        line["e2e"] = {"value": step_b / (ems / 1e3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
-                       "d2h_bytes_per_step": hx.numel() * 8, "ms_per_step": ems}
-    if not args.no_cpu_baseline:
+        res["e2e"] = {"value": step_b / (ems / 1e3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
+                      "d2h_bytes_per_step": hx.numel() * 8, "ms_per_step": ems}
+    if not args.no_cpu_baseline or not args.no_oracle_error:
         import oracle
 
-        # systems in increasing size until about 10 s of CPU work
-        order = np.argsort([A.n for A in batch.systems])
-        t0 = time.perf_counter()
+        # oracle PCG of sampled systems (smallest, median and largest sizes) on all host cores:
+        # the error of each result against it, and the oracle's throughput on that sample
+        threads = oracle_threads(args)
+        oracle.set_threads(threads)
+        sizes = np.array([A.n for A in batch.systems])
+        order = np.argsort(sizes)
+        sample = list(order[:4]) + list(order[len(order) // 2 - 2:len(order) // 2 + 2]) + list(order[-2:])
+        errs_m, errs_64 = [], []
         sb = 0
-        done = 0
-        for s in order:
-            if time.perf_counter() - t0 > 10.0:
-                break
-            done += 1
+        t0 = time.perf_counter()
+        for s in sample:
             A = batch.systems[s]
             sl = slice(int(batch.sys_row[s]), int(batch.sys_row[s + 1]))
             r = oracle.pcg(A, b[sl], int(batch.bs[s]), args.tol)
+            errs_m.append(rel_err(x_mixed[sl], r["x"]))
+            if x64 is not None:
+                errs_64.append(rel_err(x64[sl], r["x"]))
             n_s, nnz_s, bs_s = A.n, A.nnz, int(batch.bs[s])
             C = csr_bytes(n_s, nnz_s, 8)
             Fm, _ = factor_bytes(n_s, bs_s, 8)
             v = 8 * n_s
             sb += (C + Fm) + (Fm + 5 * v) + r["iterations"] * (C + Fm + 11 * v) + (r["restarts"] + 1) * (C + 3 * v)
         cs = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": sb / cs / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                                "sample": f"oracle FP64 setup + PCG of the {done} smallest systems ({cs:.1f} s)"}
+        used = oracle.threads()
+        oracle.set_threads(1)
+        res["err_vs_fp64_oracle"] = {"mixed_max": max(errs_m), "fp64_max": max(errs_64) if errs_64 else None,
+                                     "systems": [int(s) for s in sample],
+                                     "note": "max over sampled systems of ||x_s - x_oracle,s|| / ||x_oracle,s||"}
+        res["cpu_baseline"] = {"value": sb / cs / 1e9, "unit": "GB/s", "cores": used, "kind": "oracle",
+                               "sample": f"oracle FP64 setup + PCG of {len(sample)} sampled systems ({cs:.1f} s)"}
+    return res
+
+
+def run_batched(args):
+    import paper_2410_02408_gb300 as pc
+
+    pc.load()
+    res = batched_result(pc, args, args.steps, args.warmup, tune=True)
+    line = {"n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic"}
+    line.update(res)
     print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- power-law workload
+def powerlaw_result(pc, args, steps, warmup):
+    """The 8M-row power-law matrix (FP32 values, bs 32): mixed and FP64-factor setup + solve,
+    the binned SpMV's roofline, and the error against the oracle's FP64 PCG."""
+    import torch
+
+    t0 = time.time()
+    A = W.powerlaw_spd(args.pl_n, seed=5)
+    gen_s = time.time() - t0
+    bs = 32
+    b = W.rhs(A.n, 0)
+    Ad = pc.csr(A)
+    bd = torch.from_numpy(b).cuda()
+    n, nnz, vb = A.n, A.nnz, A.val.dtype.itemsize
+    peak, peak_kind = measured_hbm()
+    with ClockSampler(0) as clk:
+        x, infos, ms_total = timed_solves(pc, Ad, bd, bs, args.prec, args, steps, warmup)
+    ms = ms_total / steps
+    byt = sum(step_bytes(n, nnz, bs, args.prec, i["iterations"], vb)[0] for i in infos)
+    value = byt / (ms_total / 1e3) / 1e9
+    spmv_us, prec_us, upd_us, order = kernel_times(pc, Ad, bd, bs, args.prec, args)
+    kname = ("cg_spmv_bin_pipe_kernel (binned rows; q = A p and p.q; one launch per CG iteration)"
+             if order["binned"] else "cg_spmv_kernel (q = A p and p.q; one launch per CG iteration)")
+    roofline, kernels = kernel_table(n, nnz, vb, bs, args.prec, spmv_us, prec_us, upd_us, peak, peak_kind, None,
+                                     kname)
+    info = infos[-1]
+    res = {"metric": METRIC, "value": value, "unit": "GB/s", "ms_per_step": ms, "steps": steps, "warmup": warmup,
+           "config": {"workload": f"powerlaw_{n}_fp32vals", "n": n, "nnz": nnz, "block_size": bs,
+                      "prec": "mixed (fp32 factors, fp64 CG)" if args.prec != "fp64" else "fp64",
+                      "csr_values": "fp32" if vb == 4 else "fp64", "tol": args.tol,
+                      "l2": "inputs larger than L2 (CSR %.0f MB + factor)" % (csr_bytes(n, nnz, vb) / 1e6)},
+           "iterations": info["iterations"], "true_rel_residual": info["true_rel_residual"],
+           "setup_ms": statistics.mean(i["setup_ms"] for i in infos),
+           "solve_ms": statistics.mean(i["solve_ms"] for i in infos),
+           "frac_of_hbm_peak": value / peak, "roofline": roofline, "kernels": kernels, "spmv_order": order,
+           "generation_s": gen_s,
+           "gpu_launches": sum(2 + 6 + 4 * (i["restarts"] + 1) + 3 * i["iterations"] for i in infos)}
+    res["clocks"] = clk.summary()
+    x64 = None
+    if args.prec != "fp64" and not args.no_fp64_compare:
+        x64t, finf, fms_total = timed_solves(pc, Ad, bd, bs, "fp64", args, 1, 1)
+        x64 = x64t.cpu().numpy()
+        fb = step_bytes(n, nnz, bs, "fp64", finf[-1]["iterations"], vb)[0]
+        res["fp64"] = {"value": fb / (fms_total / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": fms_total,
+                       "iterations": finf[-1]["iterations"]}
+        res["mixed_speedup_vs_fp64"] = fms_total / ms
+    if not args.no_oracle_error:
+        o, om = oracle_full(A, b, bs, oracle_threads(args))
+        errs = {"mixed" if args.prec != "fp64" else "fp64": rel_err(x.cpu().numpy(), o["x"])}
+        if x64 is not None:
+            errs["fp64"] = rel_err(x64, o["x"])
+        errs["oracle_iterations"] = o["iterations"]
+        res["err_vs_fp64_oracle"] = errs
+        res["cpu_baseline"] = {"value": om["GBs"], "unit": "GB/s", "cores": om["threads"], "kind": "oracle",
+                               "sample": f"oracle FP64 setup + PCG to 1e-10 ({om['iterations']} iterations, "
+                                         f"{om['seconds']:.1f} s)", "seconds_to_solution": om["seconds"]}
+    return res
 
 
 def main():

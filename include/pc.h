@@ -26,7 +26,12 @@
  *   - No call aborts, prints or traps.  Every failure is a pc_status; details are in the
  *     info structs.  Device-side waits are bounded (PC_ERR_TIMEOUT).
  *   - CSR: square, int32 indices, column indices sorted and unique in each row, explicit
- *     diagonal.  n < 2^31, nnz < 2^31.
+ *     diagonal.  n < 2^31, nnz < 2^31.  Every entry point that takes a CSR without a handle
+ *     (pc_setup, hence pcg_solve and kappa_estimate with block_size > 0; kappa_estimate and
+ *     kappa_estimate_h without a handle; pcg_solve_noalloc; pc_spmv; pc_extract_blocks;
+ *     pc_grad_val) first runs an O(nnz) structure check on the device (pc_csr_check) and
+ *     returns PC_ERR_INVALID_ARG before any other kernel reads the matrix when it fails; the
+ *     check reads only row_ptr[0..n] and col_idx[0..nnz) and synchronises the stream.
  *   - Block partition: block k covers rows [k*bs, min(n, (k+1)*bs)); the last block may
  *     be shorter and is padded with the identity internally (the result is unchanged).
  *     1 <= block_size <= 64.
@@ -133,6 +138,18 @@ typedef struct {
 pc_status pc_setup(const pc_csr *A, int32_t block_size, double tol, int32_t prec, void *stream,
                    pc_handle **out);
 
+/* pc_csr_check - the O(nnz) structure check that the CSR entry points run: row_ptr[0] = 0,
+ * row ranges non-decreasing and inside [0, nnz], row_ptr[n] = nnz, every column index in
+ * [0, n), columns strictly increasing within each row, and the diagonal entry stored in every
+ * row (Sec. 3.1 takes A sparse and Hermitian positive definite; these are the storage rules
+ * this library's kernels rely on).  One device thread per row reads only row_ptr[0..n] and
+ * col_idx[0..nnz); no value is read and nothing is gathered through a column index.
+ *   flags  (host, may be NULL) receives the OR of the violations found: 1 row pointers,
+ *          2 a column out of range, 4 columns not strictly increasing, 8 a missing diagonal.
+ * Returns PC_OK or PC_ERR_INVALID_ARG (also for a malformed descriptor: n <= 0, null
+ * pointers, bad dtype).  Synchronises the stream. */
+pc_status pc_csr_check(const pc_csr *A, uint32_t *flags, void *stream);
+
 /* First failing block of the last pc_setup on h (-1 if none). */
 int64_t pc_handle_failed_block(const pc_handle *h);
 
@@ -165,6 +182,15 @@ pc_status pc_spmv(const pc_csr *A, const double *x, double *y, void *stream);
 
 /* pc_dot - *result = x . y (device scalar), fixed-order reduction (bit-reproducible). */
 pc_status pc_dot(int64_t n, const double *x, const double *y, double *result, void *stream);
+
+/* pc_debug_convert - the float <-> double conversions that the mixed-precision kernels
+ * (FP32 factors applied to FP64 vectors, FP32 CSR values in FP64 products) perform on the
+ * integer pipe instead of the FP64 pipe, exposed element by element so that they can be
+ * checked against IEEE-754 conversion: out_f[i] = in_d[i] rounded to float (round to nearest,
+ * ties to even; overflow to infinity), out_d[i] = in_f[i] widened exactly.  Support call; the
+ * paper has no counterpart.  Device arrays of n elements.  Stream-ordered, no synchronisation. */
+pc_status pc_debug_convert(int64_t n, const double *in_d, float *out_f, const float *in_f, double *out_d,
+                           void *stream);
 
 /* ---------------------------------------------------------------------------------
  * kappa_estimate - Lanczos estimate of kappa (Sec. 3.1) for A (block_size == 0) or for
@@ -205,27 +231,29 @@ pc_status pcg_solve_h(pc_handle *h, const double *b, double *x, double tol, int3
                       pc_solve_info *info, void *stream);
 
 /* pcg_solve_noalloc - the same solve as pcg_solve with the persistent engine
- * (pc_set_cg_engine(1): same kernels, same results), for callers that cannot allocate
- * device memory.  The paper has no counterpart; this is a
- * deployment variant.  Examples of such callers: code that runs while a stream is being
- * captured into a CUDA graph (cudaMalloc/cudaFree are not stream-ordered and cudaFree
- * synchronises the device), plug-ins hosted by a framework whose caching allocator owns
- * the device memory, and latency-critical loops that must not enter the driver's
- * allocator.  The caller passes only inputs and outputs (A, b, x as in pcg_solve); every
- * byte of scratch (block factors, four CG vectors, reduction partials, barrier words)
- * comes from one fixed device array of PC_NOALLOC_SCRATCH_BYTES that the library defines
- * statically, so every GPU that loads libpc holds that much memory until the process exits.
+ * (pc_set_cg_engine(1): same kernels, same grid, same wait budget, same results), for
+ * callers that cannot allocate device memory.  The paper has no counterpart; this is a
+ * deployment variant.  Examples of such callers: plug-ins hosted by a framework whose
+ * caching allocator owns the device memory (a cudaMalloc behind its back can fail or fragment
+ * the pool it manages), and latency-critical loops that must not enter the driver's allocator
+ * (cudaMalloc and cudaFree can block and synchronise the device).  The caller passes only
+ * inputs and outputs (A, b, x as in pcg_solve); every byte of scratch (block factors, four CG
+ * vectors, reduction partials, barrier and status words) comes from one fixed device array of
+ * PC_NOALLOC_SCRATCH_BYTES that the library defines statically, so every GPU that loads libpc
+ * holds that much memory until the process exits.
  *   Limit: the problem must fit, i.e. roughly (K+1 + bs) * n * e + 32 n bytes plus a few KB
  *   for factors of element size e (8 for PC_PREC_FP64, 4 otherwise), K = bs/2, with the
- *   factor arrays padded to whole 32-row warp units; larger problems return
- *   PC_ERR_INVALID_ARG before any work is enqueued.
+ *   factor arrays padded to whole 32-row warp units and the vectors to multiples of 32 rows;
+ *   larger problems return PC_ERR_INVALID_ARG before any work is enqueued.
+ *   The call runs the CSR structure check (pc_csr_check), then setup, then the solve, and
+ *   synchronises the stream after each of them (and after the FP64 refactorisation that
+ *   follows an FP32 pivot breakdown, as in pc_setup) to read their status words back.
  *   The first call on each device looks up the array's device address (cudaGetSymbolAddress
- *   with that device current) and caches it; make that first call before any stream
- *   capture.  All calls share the one array and it keeps the previous call's contents (the
- *   call clears what must start at zero): calls that overlap on the GPU (different
- *   streams or threads on the same device) race and must be serialised by the caller.
- *   No cudaMalloc, cudaFree or allocating library routine is called; info->solve_ms and
- *   info->setup_ms are not measured (0). */
+ *   with that device current) and caches it.  All calls share the one array and it keeps the
+ *   previous call's contents (the call clears what must start at zero): calls that overlap on
+ *   the GPU (different streams or threads on the same device) race and must be serialised by
+ *   the caller.  No cudaMalloc, cudaFree or allocating library routine is called;
+ *   info->solve_ms and info->setup_ms are not measured (0). */
 #define PC_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
 pc_status pcg_solve_noalloc(const pc_csr *A, int32_t block_size, const double *b, double *x,
                             double tol, int32_t max_iter, int32_t prec, pc_solve_info *info,
@@ -287,7 +315,8 @@ typedef struct {
 typedef struct pc_batch_handle pc_batch_handle;
 
 /* pc_batch_create - validate the batch (an O(nnz) device pass: row pointers
- * non-decreasing, local columns inside their system), schedule the teams and allocate the
+ * non-decreasing, local columns inside their system, strictly increasing within each row,
+ * diagonal stored), schedule the teams and allocate the
  * library-owned workspace (4 FP64 vectors of n_rows, the M^{-1} factors, team counters).
  * prec: PC_PREC_FP64, or PC_PREC_FP32 / PC_PREC_TF32 (FP32 factors applied in FP32, FP64
  * CG).  pivot_tol: a Cholesky pivot <= pivot_tol * (largest diagonal entry of its block)

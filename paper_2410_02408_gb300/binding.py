@@ -79,12 +79,16 @@ def lib():
     sig = {
         "pc_setup": (_I32, [ctypes.POINTER(pc_csr), _I32, _D, _I32, _P, ctypes.POINTER(_P)]),
         "pc_handle_failed_block": (_I64, [_P]),
+        "pc_csr_check": (_I32, [ctypes.POINTER(pc_csr), ctypes.POINTER(ctypes.c_uint32), _P]),
+        "pcg_solve_noalloc": (_I32, [ctypes.POINTER(pc_csr), _I32, _P, _P, _D, _I32, _I32,
+                                     ctypes.POINTER(pc_solve_info), _P]),
         "pc_apply": (_I32, [_P, _I32, _P, _P, _P]),
         "pc_get_factor": (_I32, [_P, _I32, _P, _P]),
         "pc_destroy": (_I32, [_P]),
         "pc_extract_blocks": (_I32, [ctypes.POINTER(pc_csr), _I32, _P, _P]),
         "pc_spmv": (_I32, [ctypes.POINTER(pc_csr), _P, _P, _P]),
         "pc_dot": (_I32, [_I64, _P, _P, _P, _P]),
+        "pc_debug_convert": (_I32, [_I64, _P, _P, _P, _P, _P]),
         "kappa_estimate": (_I32, [ctypes.POINTER(pc_csr), _I32, _I32, _D, _P, _I32,
                                   ctypes.POINTER(pc_kappa_info), _P]),
         "kappa_estimate_h": (_I32, [_P, ctypes.POINTER(pc_csr), _I32, _D, _P, _I32,
@@ -330,6 +334,18 @@ def pcg(A, b, block_size: int, tol: float = 1e-10, max_iter: int = 100000, prec:
     return x, info.to_dict()
 
 
+CSR_FLAGS = {1: "row_ptr", 2: "column_range", 4: "column_order", 8: "missing_diagonal"}
+
+
+def csr_check(A):
+    """The library's O(nnz) CSR structure check: (status, set of violated rules)."""
+    A = _as_csr(A)
+    d = A.desc()
+    flags = ctypes.c_uint32(0)
+    st = int(lib().pc_csr_check(ctypes.byref(d), ctypes.byref(flags), _stream()))
+    return st, {name for bit, name in CSR_FLAGS.items() if flags.value & bit}
+
+
 def spmv(A, x, out=None):
     torch = _torch()
     A = _as_csr(A)
@@ -338,6 +354,21 @@ def spmv(A, x, out=None):
     d = A.desc()
     _check(lib().pc_spmv(ctypes.byref(d), _ptr(x), _ptr(out), _stream()), "pc_spmv")
     return out
+
+
+def debug_convert(d, f):
+    """The library's integer-pipe conversions: (float32 of the float64 tensor d, float64 of the
+    float32 tensor f), element by element (pc_debug_convert)."""
+    torch = _torch()
+    d = _dev(d, torch.float64)
+    f = _dev(f, torch.float32)
+    out_f = torch.empty(d.shape[0], dtype=torch.float32, device="cuda")
+    out_d = torch.empty(f.shape[0], dtype=torch.float64, device="cuda")
+    if d.shape[0] != f.shape[0]:
+        raise ValueError("d and f must have the same length")
+    _check(lib().pc_debug_convert(d.shape[0], _ptr(d), _ptr(out_f), _ptr(f), _ptr(out_d), _stream()),
+           "pc_debug_convert")
+    return out_f, out_d
 
 
 def dot(x, y) -> float:

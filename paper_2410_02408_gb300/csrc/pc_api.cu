@@ -7,15 +7,12 @@
 
 #include <mutex>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pc.h"
 #include "pc_kernels.cuh"
 
 using pc::Layout;
-
-namespace pc {
-// pc_setup.cu: FP64 arithmetic with FP32 stored factors (fallback of the FP32 setup).
-cudaError_t launch_setup_f64_store_f32(const SetupArgs& a, bool val_f32, cudaStream_t st);
-}  // namespace pc
 
 struct pc_handle {
   pc_csr A;
@@ -83,6 +80,15 @@ long long wait_budget() {
   return kDefaultBudget;
 }
 
+// NVTX range around an entry point (visible in profilers that collect NVTX; the header-only
+// NVTX library does nothing when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 pc_status from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return PC_OK;
   cudaGetLastError();
@@ -137,7 +143,62 @@ int64_t vec_stride(int64_t n) { return (n + 31) & ~(int64_t)31; }
 std::mutex g_mu;
 double* g_dot_scratch[64] = {nullptr};
 
+// Per-device result word of the CSR structure check for calls without a handle; the mutex is
+// held from the check's launch until its result has been read.
+std::mutex g_check_mu;
+unsigned* g_check_word[64] = {nullptr};
+
+// O(nnz) structure check of A on the device (row_ptr[0] = 0, non-decreasing row ranges inside
+// [0, nnz], row_ptr[n] = nnz, columns in [0, n), strictly increasing within each row, diagonal
+// stored).  word: one device unsigned.  Synchronises the stream; *flags (may be null) receives
+// the pc::CSR_BAD_* bits found.
+pc_status check_csr_with(const pc_csr* A, unsigned* word, cudaStream_t st, unsigned* flags) {
+  unsigned f = 0u;
+  cudaError_t e = pc::launch_validate_csr(A->n, A->nnz, A->row_ptr, A->col_idx, word, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&f, word, sizeof(f), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return from_cuda(e);
+  if (flags) *flags = f;
+  return f ? PC_ERR_INVALID_ARG : PC_OK;
+}
+
+pc_status check_csr(const pc_csr* A, cudaStream_t st, unsigned* flags) {
+  int dev = 0;
+  PC_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return PC_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_check_mu);
+  if (!g_check_word[dev]) {
+    pc_status s = dalloc(&g_check_word[dev], 256);
+    if (s != PC_OK) return s;
+  }
+  return check_csr_with(A, g_check_word[dev], st, flags);
+}
+
 }  // namespace
+
+namespace pc {
+// Settings shared with the allocation-free solve (pc_static.cu), so that it runs the persistent
+// engine with the same grid and wait budget as pcg_solve_h.
+long long wait_budget_cycles() { return wait_budget(); }
+
+// Grid of the persistent CG kernel for this matrix: resident CTAs per SM (capped by
+// pc_set_ctas_per_sm) times the SM count, at most one CTA per 8 warp units.
+cudaError_t persistent_grid(const Layout& L, int64_t nnz, bool val_f32, bool fac_f32, int* grid) {
+  PcgArgs plan;
+  plan.lay = L;
+  pcg_plan(plan, nnz, val_f32, fac_f32);
+  int per_sm = 0;
+  cudaError_t e = pcg_occupancy(L, val_f32, fac_f32, PCG_BLOCK, plan.sp.total, &per_sm);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  if (g_ctas_per_sm > 0 && g_ctas_per_sm < per_sm) per_sm = g_ctas_per_sm;
+  int g = per_sm * sm_count();
+  const int64_t max_useful = (L.n_units + 7) / 8;   // at least 8 warp units per CTA
+  if (g > max_useful) g = (int)(max_useful > 0 ? max_useful : 1);
+  *grid = g;
+  return cudaSuccess;
+}
+}  // namespace pc
 
 extern "C" {
 
@@ -213,9 +274,20 @@ int32_t pc_get_trace(const pc_handle* h, int64_t* out, int32_t max_entries) {
 
 int64_t pc_handle_failed_block(const pc_handle* h) { return h ? h->failed_block : -1; }
 
+pc_status pc_csr_check(const pc_csr* A, uint32_t* flags, void* stream) {
+  NvtxRange nv("pc_csr_check");
+  if (flags) *flags = 0u;
+  if (!csr_ok(A)) return PC_ERR_INVALID_ARG;
+  unsigned f = 0u;
+  const pc_status s = check_csr(A, (cudaStream_t)stream, &f);
+  if (flags) *flags = f;
+  return s;
+}
+
 int32_t pc_handle_refactored_fp64(const pc_handle* h) { return h ? h->refactored_fp64 : 0; }
 
 pc_status pc_setup(const pc_csr* A, int32_t block_size, double tol, int32_t prec, void* stream, pc_handle** out) {
+  NvtxRange nv("pc_setup");
   if (!out) return PC_ERR_INVALID_ARG;
   *out = nullptr;
   if (!csr_ok(A) || block_size < 1 || block_size > 64 || !(tol >= 0.0)) return PC_ERR_INVALID_ARG;
@@ -236,6 +308,12 @@ pc_status pc_setup(const pc_csr* A, int32_t block_size, double tol, int32_t prec
   if (s == PC_OK) s = dalloc(&h->linv, es * (size_t)(h->L.n_units * pc::unit_elems_linv(h->L)));
   if (s == PC_OK) s = dalloc(&h->tmp, sizeof(double) * (size_t)A->n);
   if (s == PC_OK) s = dalloc(&h->failed_d, sizeof(unsigned long long));
+  if (s != PC_OK) {
+    pc_destroy(h);
+    return s;
+  }
+  // the CSR structure is checked before any kernel reads it through its indices
+  s = check_csr_with(A, reinterpret_cast<unsigned*>(h->failed_d), st, nullptr);
   if (s != PC_OK) {
     pc_destroy(h);
     return s;
@@ -276,6 +354,7 @@ pc_status pc_setup(const pc_csr* A, int32_t block_size, double tol, int32_t prec
 }
 
 pc_status pc_apply(pc_handle* h, int32_t mode, const double* in, double* out, void* stream) {
+  NvtxRange nv("pc_apply");
   if (!h || !in || !out || in == out) return PC_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   switch (mode) {
@@ -307,14 +386,25 @@ pc_status pc_get_factor(const pc_handle* h, int32_t which, double* out, void* st
 
 pc_status pc_extract_blocks(const pc_csr* A, int32_t block_size, double* out, void* stream) {
   if (!csr_ok(A) || block_size < 1 || !out) return PC_ERR_INVALID_ARG;
+  const pc_status s = check_csr(A, (cudaStream_t)stream, nullptr);
+  if (s != PC_OK) return s;
   return from_cuda(pc::launch_extract(A->n, A->row_ptr, A->col_idx, A->val, A->dtype == PC_F32, block_size, out,
                                       (cudaStream_t)stream));
 }
 
 pc_status pc_spmv(const pc_csr* A, const double* x, double* y, void* stream) {
   if (!csr_ok(A) || !x || !y || x == y) return PC_ERR_INVALID_ARG;
+  const pc_status s = check_csr(A, (cudaStream_t)stream, nullptr);
+  if (s != PC_OK) return s;
   return from_cuda(pc::launch_spmv(A->n, A->row_ptr, A->col_idx, A->val, A->dtype == PC_F32, x, y,
                                    (cudaStream_t)stream));
+}
+
+pc_status pc_debug_convert(int64_t n, const double* in_d, float* out_f, const float* in_f, double* out_d,
+                           void* stream) {
+  if (n < 0 || (n > 0 && (!in_d || !out_f || !in_f || !out_d))) return PC_ERR_INVALID_ARG;
+  if (n == 0) return PC_OK;
+  return from_cuda(pc::launch_convert(n, in_d, out_f, in_f, out_d, (cudaStream_t)stream));
 }
 
 pc_status pc_dot(int64_t n, const double* x, const double* y, double* result, void* stream) {
@@ -336,6 +426,8 @@ pc_status pc_dot(int64_t n, const double* x, const double* y, double* result, vo
 
 pc_status pc_grad_val(const pc_csr* A, const double* lambda, const double* x, double* grad_val, void* stream) {
   if (!csr_ok(A) || !lambda || !x || !grad_val) return PC_ERR_INVALID_ARG;
+  const pc_status s = check_csr(A, (cudaStream_t)stream, nullptr);
+  if (s != PC_OK) return s;
   return from_cuda(pc::launch_grad_val(A->n, A->row_ptr, A->col_idx, lambda, x, grad_val, (cudaStream_t)stream));
 }
 
@@ -350,16 +442,8 @@ pc_status pc_grad_edges(int64_t n_edges, const int32_t* p, const int32_t* q, con
 // ------------------------------------------------------------------ PCG
 static pc_status ensure_cg_workspace(pc_handle* h, cudaStream_t st) {
   const int block = pc::PCG_BLOCK;
-  int per_sm = 0;
-  pc::PcgArgs plan;
-  plan.lay = h->L;
-  pc::pcg_plan(plan, h->A.nnz, h->val_f32, h->fac_f32);
-  PC_TRY(pc::pcg_occupancy(h->L, h->val_f32, h->fac_f32, block, plan.sp.total, &per_sm));
-  if (per_sm < 1) return PC_ERR_CUDA;
-  if (g_ctas_per_sm > 0 && g_ctas_per_sm < per_sm) per_sm = g_ctas_per_sm;
-  int grid = per_sm * sm_count();
-  const int64_t max_useful = (h->L.n_units + 7) / 8;   // at least 8 warp units per CTA
-  if (grid > max_useful) grid = (int)(max_useful > 0 ? max_useful : 1);
+  int grid = 0;
+  PC_TRY(pc::persistent_grid(h->L, h->A.nnz, h->val_f32, h->fac_f32, &grid));
   if (h->cg && h->grid == grid) return PC_OK;
   dfree(h->part);
   dfree(h->split);
@@ -530,6 +614,7 @@ static pc_status pcg_solve_graph(pc_handle* h, const double* b, double* x, doubl
 
 pc_status pcg_solve_h(pc_handle* h, const double* b, double* x, double tol, int32_t max_iter, pc_solve_info* info,
                       void* stream) {
+  NvtxRange nv("pcg_solve_h");
   if (info) {
     memset(info, 0, sizeof(*info));
     info->failed_block = -1;
@@ -616,6 +701,7 @@ pc_status pcg_solve_h(pc_handle* h, const double* b, double* x, double tol, int3
 
 pc_status pcg_solve(const pc_csr* A, int32_t block_size, const double* b, double* x, double tol, int32_t max_iter,
                     int32_t prec, pc_solve_info* info, void* stream) {
+  NvtxRange nv("pcg_solve");
   if (info) {
     memset(info, 0, sizeof(*info));
     info->failed_block = -1;
@@ -655,6 +741,7 @@ pc_status pcg_solve(const pc_csr* A, int32_t block_size, const double* b, double
 // ------------------------------------------------------------------ Lanczos
 pc_status kappa_estimate_h(pc_handle* h, const pc_csr* A, int32_t max_steps, double tol, const double* v0,
                            int32_t reorth, pc_kappa_info* info, void* stream) {
+  NvtxRange nv("kappa_estimate");
   double* ha = info ? info->alpha : nullptr;
   double* hb = info ? info->beta : nullptr;
   if (info) {
@@ -666,6 +753,10 @@ pc_status kappa_estimate_h(pc_handle* h, const pc_csr* A, int32_t max_steps, dou
   if (!csr_ok(M) || !v0 || max_steps < 1 || max_steps > 256 || !(tol >= 0.0) || (reorth != 0 && reorth != 1))
     return PC_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
+  if (!h) {   // a handle's CSR was checked by pc_setup
+    const pc_status cs = check_csr(M, st, nullptr);
+    if (cs != PC_OK) return cs;
+  }
   const int64_t n = M->n;
   const int m = max_steps;
   const int G = pc::lanczos_grid();

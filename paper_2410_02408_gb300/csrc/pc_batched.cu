@@ -23,6 +23,8 @@
 #include <cmath>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pc.h"
 #include "pc_kernels.cuh"
 #include "pc_setup_unit.cuh"
@@ -609,7 +611,8 @@ __global__ void batched_reset(unsigned* queue, int* err, unsigned* cnt, unsigned
 }
 
 // CSR checks of the concatenated batch: row pointers non-decreasing and inside [0, nnz],
-// every local column index inside its system.  bad[0] counts violations.
+// every local column index inside its system, columns strictly increasing within a row and
+// the diagonal stored.  bad[0] counts violations.
 __global__ void batched_validate(const int64_t* __restrict__ sys_row, int n_sys, const int32_t* __restrict__ rp,
                                  const int32_t* __restrict__ ci, int64_t nnz, unsigned* bad) {
   const int s = blockIdx.x;
@@ -623,10 +626,16 @@ __global__ void batched_validate(const int64_t* __restrict__ sys_row, int n_sys,
       ++nbad;
       continue;
     }
+    const int32_t lr = (int32_t)(row - r0);   // the row's local index (its diagonal column)
+    int32_t prev = -1;
+    bool diag = false;
     for (int32_t e = e0; e < e1; ++e) {
       const int32_t c = ci[e];
-      if (c < 0 || c >= n) ++nbad;
+      if (c < 0 || c >= n || c <= prev) ++nbad;   // out of range, or not strictly increasing
+      diag = diag || c == lr;
+      prev = c;
     }
+    if (!diag) ++nbad;
   }
   if (nbad) atomicAdd(bad, nbad);
 }
@@ -1019,8 +1028,21 @@ static cudaError_t batch_capture(pc_batch_handle* h, cudaStream_t st) {
   return e;
 }
 
+static pc_status batch_solve_impl(pc_batch_handle* h, const double* b, double* x, double tol, int32_t max_iter,
+                                  int32_t* iters, int32_t* status, double* relres, pc_solve_info* info,
+                                  void* stream);
+
 pc_status pc_batch_solve(pc_batch_handle* h, const double* b, double* x, double tol, int32_t max_iter,
                          int32_t* iters, int32_t* status, double* relres, pc_solve_info* info, void* stream) {
+  nvtxRangePushA("pc_batch_solve");
+  const pc_status ret = batch_solve_impl(h, b, x, tol, max_iter, iters, status, relres, info, stream);
+  nvtxRangePop();
+  return ret;
+}
+
+static pc_status batch_solve_impl(pc_batch_handle* h, const double* b, double* x, double tol, int32_t max_iter,
+                                  int32_t* iters, int32_t* status, double* relres, pc_solve_info* info,
+                                  void* stream) {
   if (info) {
     memset(info, 0, sizeof(*info));
     info->failed_block = -1;

@@ -102,6 +102,16 @@ cudaError_t launch_get_factor(const Layout& L, const void* fac, bool fac_f32, in
                               cudaStream_t st);
 
 // pc_ops.cu
+// CSR structure check (sets *flags to the OR of the CSR_BAD_* bits found; 0 = valid).
+constexpr unsigned CSR_BAD_ROW_PTR = 1u;   // row_ptr[0] != 0, row_ptr[n] != nnz, or a row range outside [0, nnz]
+constexpr unsigned CSR_BAD_COLUMN = 2u;    // a column index outside [0, n)
+constexpr unsigned CSR_BAD_ORDER = 4u;     // columns of a row not strictly increasing
+constexpr unsigned CSR_NO_DIAGONAL = 8u;   // a row without its diagonal entry
+cudaError_t launch_validate_csr(int64_t n, int64_t nnz, const int32_t* rp, const int32_t* ci, unsigned* flags,
+                                cudaStream_t st);
+// out_f[i] = d2f(in_d[i]), out_d[i] = f2d(in_f[i]) (the conversions of pc_common.cuh)
+cudaError_t launch_convert(int64_t n, const double* in_d, float* out_f, const float* in_f, double* out_d,
+                           cudaStream_t st);
 cudaError_t launch_spmv(int64_t n, const int32_t* rp, const int32_t* ci, const void* va, bool val_f32,
                         const double* x, double* y, cudaStream_t st);
 cudaError_t launch_dot(int64_t n, const double* x, const double* y, double* result, double* part,
@@ -134,6 +144,12 @@ cudaError_t launch_grad_val(int64_t n, const int32_t* rp, const int32_t* ci, con
                             double* g, cudaStream_t st);
 cudaError_t launch_grad_edges(int64_t n_edges, const int32_t* ep, const int32_t* eq, const double* lam,
                               const double* x, int64_t n, double* g, cudaStream_t st);
+
+// pc_api.cu: settings of the persistent engine (wait budget in cycles; grid for a matrix).
+long long wait_budget_cycles();
+cudaError_t persistent_grid(const Layout& L, int64_t nnz, bool val_f32, bool fac_f32, int* grid);
+// pc_setup.cu: FP64 arithmetic with FP32 stored factors (fallback of the FP32 setup).
+cudaError_t launch_setup_f64_store_f32(const SetupArgs& a, bool val_f32, cudaStream_t st);
 
 // pc_pcg_*.cu
 cudaError_t launch_pcg(const PcgArgs& a, bool val_f32, bool fac_f32, int grid, int block, cudaStream_t st);

@@ -1,10 +1,77 @@
 // Stand-alone operators: CSR SpMV, fixed-order dot product, block preconditioner
 // application (M^{-1}, L^{-1}, L^{-T}), the second phase of the symmetric operator
 // L^{-1} A L^{-T} (SpMV with a fused per-unit L^{-1} epilogue), the SpMV row split of
-// the persistent CG kernel, and the adjoint gradient on the sparsity pattern.
+// the persistent CG kernel, the adjoint gradient on the sparsity pattern, and the O(nnz)
+// structure check of a CSR matrix.
 #include "pc_kernels.cuh"
 
 namespace pc {
+
+// CSR structure check, one thread per row: the row's range must lie inside [0, nnz] and not
+// decrease, and its columns must lie in [0, n), increase strictly and include the row
+// itself.  Only row_ptr[0..n] and col[0..nnz) are read; nothing is gathered through a
+// column index.  Violations are OR-ed into *flags (CSR_BAD_* bits).
+__global__ void __launch_bounds__(256) validate_csr_kernel(int64_t n, int64_t nnz, const int32_t* __restrict__ rp,
+                                                           const int32_t* __restrict__ ci, unsigned* flags) {
+  unsigned f = 0u;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t e0 = __ldg(rp + i), e1 = __ldg(rp + i + 1);
+    if (e0 < 0 || e1 < e0 || (int64_t)e1 > nnz) {
+      f |= CSR_BAD_ROW_PTR;
+      continue;
+    }
+    int64_t prev = -1;
+    bool diag = false;
+    for (int32_t e = e0; e < e1; ++e) {
+      const int64_t c = __ldg(ci + e);
+      if (c < 0 || c >= n) f |= CSR_BAD_COLUMN;
+      if (c <= prev) f |= CSR_BAD_ORDER;
+      diag = diag || c == i;
+      prev = c;
+    }
+    if (!diag) f |= CSR_NO_DIAGONAL;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (__ldg(rp) != 0 || (int64_t)__ldg(rp + n) != nnz)) f |= CSR_BAD_ROW_PTR;
+  f = __reduce_or_sync(FULL, f);
+  if ((threadIdx.x & 31) == 0 && f) atomicOr(flags, f);
+}
+
+// The integer-pipe float <-> double conversions of the mixed-precision kernels, element by
+// element (full warps: the helpers vote on their rare hardware fallback).
+__global__ void __launch_bounds__(256) convert_kernel(int64_t n, const double* __restrict__ in_d,
+                                                      float* __restrict__ out_f, const float* __restrict__ in_f,
+                                                      double* __restrict__ out_d) {
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const bool ok = i < n;
+    const float f = d2f(ok ? in_d[i] : 0.0);
+    const double d = f2d(ok ? in_f[i] : 0.0f);
+    if (ok) {
+      out_f[i] = f;
+      out_d[i] = d;
+    }
+  }
+}
+
+cudaError_t launch_convert(int64_t n, const double* in_d, float* out_f, const float* in_f, double* out_d,
+                           cudaStream_t st) {
+  const int64_t want = (n + 255) / 256;
+  convert_kernel<<<(int)(want < 1024 ? (want > 0 ? want : 1) : 1024), 256, 0, st>>>(n, in_d, out_f, in_f, out_d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate_csr(int64_t n, int64_t nnz, const int32_t* rp, const int32_t* ci, unsigned* flags,
+                                cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (n + 255) / 256;
+  const int grid = (int)(want < (int64_t)(sms > 0 ? sms : 1) * 8 ? want : (int64_t)(sms > 0 ? sms : 1) * 8);
+  cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  validate_csr_kernel<<<grid > 0 ? grid : 1, 256, 0, st>>>(n, nnz, rp, ci, flags);
+  return cudaGetLastError();
+}
 
 template <typename VT>
 __global__ void __launch_bounds__(256) spmv_kernel(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,

@@ -73,27 +73,24 @@ extern "C" pc_status pcg_solve_noalloc(const pc_csr* A, int32_t block_size, cons
   const bool fac_f32 = prec != PC_PREC_FP64;
   const size_t es = fac_f32 ? 4 : 8;
 
-  // persistent grid, as in pcg_solve
+  // persistent grid and wait budget exactly as pcg_solve_h computes them
   const int block = pc::PCG_BLOCK;
-  int per_sm = 0, dev = 0, sms = 0;
   pc::PcgArgs a;
   a.lay = L;
   pc::pcg_plan(a, A->nnz, val_f32, fac_f32);
-  cudaError_t e = pc::pcg_occupancy(L, val_f32, fac_f32, block, a.sp.total, &per_sm);
-  if (e == cudaSuccess) e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int grid = 0;
+  cudaError_t e = pc::persistent_grid(L, A->nnz, val_f32, fac_f32, &grid);
   if (e != cudaSuccess) return to_status(e);
-  if (per_sm < 1 || sms < 1) return PC_ERR_CUDA;
-  int grid = per_sm * sms;
-  const int64_t max_useful = (L.n_units + 7) / 8;
-  if (grid > max_useful) grid = (int)(max_useful > 0 ? max_useful : 1);
 
-  // carve the scratch: sizes first, so an oversized problem is rejected before any work
+  // carve the scratch: sizes first, so an oversized problem is rejected before any work.
+  // The CG vectors sit at a stride of a multiple of 32 doubles (every vector and every
+  // bulk-copied row window starts 16-byte aligned), with 64 doubles of tail padding.
   const size_t n = (size_t)A->n;
+  const size_t vs = (n + 31) & ~(size_t)31;
   const size_t sz_minv = round256(es * (size_t)(L.n_units * pc::unit_elems_minv(L)));
   const size_t sz_linv = round256(es * (size_t)(L.n_units * pc::unit_elems_linv(L)));
   const size_t sz_fail = 256;
-  const size_t sz_vec = round256(sizeof(double) * 4 * n);
+  const size_t sz_vec = round256(sizeof(double) * (4 * vs + 64));
   const size_t sz_part = round256(sizeof(double) * 4 * (size_t)grid);
   const size_t sz_split = round256(sizeof(int64_t) * (size_t)(grid + 1));
   const size_t sz_ctl = round256(sizeof(pc::GridSync) + sizeof(pc::PcgOut));
@@ -118,6 +115,14 @@ extern "C" pc_status pcg_solve_noalloc(const pc_csr* A, int32_t block_size, cons
   cur += sz_split;
   unsigned char* ctl = cur;
 
+  // CSR structure check (the word is cleared by the launcher) before anything reads the matrix
+  unsigned bad = 0u;
+  e = pc::launch_validate_csr(A->n, A->nnz, A->row_ptr, A->col_idx, reinterpret_cast<unsigned*>(failed_d), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, failed_d, sizeof(bad), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return to_status(e);
+  if (bad) return PC_ERR_INVALID_ARG;
+
   // setup: the failure word must start at all ones (the scratch keeps old contents)
   e = cudaMemsetAsync(failed_d, 0xff, sizeof(unsigned long long), st);
   pc::SetupArgs sa;
@@ -133,6 +138,14 @@ extern "C" pc_status pcg_solve_noalloc(const pc_csr* A, int32_t block_size, cons
   unsigned long long failed = ~0ull;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&failed, failed_d, sizeof(failed), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && failed != ~0ull && fac_f32) {
+    // as in pc_setup: an FP32 pivot broke down, so every block is factored again in FP64
+    // arithmetic (factors stored in FP32); NOT_SPD only if that fails too
+    e = cudaMemsetAsync(failed_d, 0xff, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = pc::launch_setup_f64_store_f32(sa, val_f32, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&failed, failed_d, sizeof(failed), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
   if (e != cudaSuccess) return to_status(e);
   if (failed != ~0ull) {
     if (info) {
@@ -152,9 +165,9 @@ extern "C" pc_status pcg_solve_noalloc(const pc_csr* A, int32_t block_size, cons
   a.b = b;
   a.x = x;
   a.r = vec;
-  a.z = vec + n;
-  a.p = vec + 2 * n;
-  a.q = vec + 3 * n;
+  a.z = vec + vs;
+  a.p = vec + 2 * vs;
+  a.q = vec + 3 * vs;
   a.part = part;
   a.split = split;
   a.gs = reinterpret_cast<pc::GridSync*>(ctl);
@@ -162,7 +175,7 @@ extern "C" pc_status pcg_solve_noalloc(const pc_csr* A, int32_t block_size, cons
   a.tol = tol;
   a.max_iter = max_iter;
   a.max_restarts = 3;
-  a.budget = 4000000000LL;
+  a.budget = pc::wait_budget_cycles();
   a.trace = nullptr;
   a.trace_len = 0;
   if (e == cudaSuccess) e = pc::launch_pcg(a, val_f32, fac_f32, grid, block, st);

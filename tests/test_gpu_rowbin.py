@@ -99,9 +99,10 @@ def test_default_is_whole_rows(pc, powerlaw):
     assert binned and nseg == 1
 
 
-def test_unsorted_columns_are_swept_whole(pc, powerlaw):
-    """Rows stored with their columns in decreasing order are the same matrix: segments need
-    increasing columns, so the handle falls back to one sweep and still solves correctly."""
+def test_unsorted_columns_are_rejected(pc, powerlaw):
+    """Rows stored with their columns in decreasing order break the CSR convention (columns
+    strictly increasing within a row); the structure check at setup rejects them before any
+    kernel reads the matrix, and the same rows stored in increasing order solve."""
     A = powerlaw
     col = A.col.copy()
     val = A.val.copy()
@@ -110,8 +111,13 @@ def test_unsorted_columns_are_swept_whole(pc, powerlaw):
         col[s:e] = col[s:e][::-1]
         val[s:e] = val[s:e][::-1]
     Ar = W.CSR(A.row_ptr, col, val)
-    x, info, binned, nseg = _solve(pc, Ar, 32, "on", segs=3, want_segs=True)
-    assert binned and nseg == 1
+    st, bad = pc.csr_check(Ar)
+    assert st == 1 and bad == {"column_order"}
+    with pytest.raises(pc.PcError) as ei:
+        pc.setup(Ar, 32, prec="fp32")
+    assert ei.value.name == "invalid_arg"
+    x, info, binned, nseg = _solve(pc, A, 32, "on", segs=3, want_segs=True)
+    assert binned and nseg == 3
     r = oracle.pcg(A, W.rhs(A.n, 0), 32, 1e-10)
     assert np.linalg.norm(x - r["x"]) <= 1e-10 * np.linalg.norm(r["x"])
 
