@@ -590,15 +590,16 @@ def run_ours(args):
     if rank == 0 and not args.no_bs_sweep and args.workload == "diffusion3d":
         # one timed setup+solve per block size and precision (after one untimed solve)
         sweep = {}
+        names = {"fp32": "mixed", "tf32": "mixed_tf32", "fp64": "fp64"}
         for bsz in (8, 16, 32, 64):
             row = {}
-            for prec in ("fp32", "fp64"):
+            for prec in ("fp32", "tf32", "fp64"):
                 _, si, sms = timed_solves(pc, Ad, bd, bsz, prec, args, 1, 1)
                 si = si[-1]
                 sb = step_bytes(n, nnz, bsz, prec, si["iterations"], vb)[0]
-                row["mixed" if prec == "fp32" else "fp64"] = {
+                row[names[prec]] = {
                     "ms": sms, "iterations": si["iterations"], "GBs": sb / (sms / 1e3) / 1e9,
-                    "true_rel_residual": si["true_rel_residual"]}
+                    "setup_ms": si["setup_ms"], "true_rel_residual": si["true_rel_residual"]}
             row["mixed_speedup_vs_fp64"] = row["fp64"]["ms"] / row["mixed"]["ms"]
             sweep[str(bsz)] = row
         line["bs_sweep"] = sweep
@@ -802,7 +803,7 @@ def paper_sweep(pc):
     for N in (1024, 4096, 16384):
         mats = [(f"poisson2d_{int(round(N ** 0.5))}", W.poisson2d(int(round(N ** 0.5))))]
         for d in (4, 8, 16):
-            mats.append((f"random_spd_deg{d}", random_spd(N, d)))
+            mats.append((f"random_spd_deg{d}", W.random_spd(N, d)))
         res = {}
         for name, A in mats:
             b = W.rhs(A.n, 0)
@@ -824,15 +825,6 @@ def paper_sweep(pc):
             res[name] = row
         out[str(N)] = res
     return out
-
-
-def random_spd(n, mean_deg, seed=11):
-    """The paper-size random SPD family: the power-law recipe (Chung-Lu edges, U(-1,0)
-    off-diagonals, diagonal = row |sum| + 1e-2, RCM order) with a given mean degree."""
-    w_min = 2
-    w_max = max(mean_deg + 1, min(1999, n // 4))
-    return W.powerlaw_spd(n, seed=seed, w_min=w_min, w_max=w_max, mean_deg=float(mean_deg), cap=min(2000, n),
-                          dtype=np.float64)
 
 
 # ---------------------------------------------------------------- batched workload

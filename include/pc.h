@@ -72,8 +72,10 @@ typedef enum { PC_F64 = 0, PC_F32 = 1 } pc_dtype; /* type of the CSR values */
 /* Precision of the block factors and of their application.  PC_PREC_FP64: factor and
  * apply in FP64.  PC_PREC_FP32: factor and apply in FP32 (FP32 accumulation); CG vectors,
  * residual update, dot products and scalars stay FP64, so the outer FP64 CG is the
- * iterative refinement that recovers full accuracy.  PC_PREC_TF32 is accepted as the
- * FP32 path (same arithmetic). */
+ * iterative refinement that recovers full accuracy.  PC_PREC_TF32: as PC_PREC_FP32, except
+ * that M_k^{-1} = L_k^{-T} L_k^{-1} is formed on the tensor cores (mma.sync m16n8k8) from
+ * L_k^{-1} rounded to TF32 (round to nearest, ties away from zero) with FP32 accumulation;
+ * the Cholesky factor and L_k^{-1} are FP32, and the stored M_k^{-1} is exactly symmetric. */
 typedef enum { PC_PREC_FP64 = 0, PC_PREC_FP32 = 1, PC_PREC_TF32 = 2 } pc_prec;
 
 /* pc_apply modes (L_k is the Cholesky factor of the diagonal block A_kk):
@@ -191,6 +193,12 @@ pc_status pc_dot(int64_t n, const double *x, const double *y, double *result, vo
  * paper has no counterpart.  Device arrays of n elements.  Stream-ordered, no synchronisation. */
 pc_status pc_debug_convert(int64_t n, const double *in_d, float *out_f, const float *in_f, double *out_d,
                            void *stream);
+
+/* pc_debug_mma_tf32 - one tensor-core product as PC_PREC_TF32's setup issues it: d = a b with
+ * a 16 x 8 and b 8 x 8 (device, row-major FP32), both rounded to TF32 (round to nearest, ties
+ * away from zero), FP32 accumulation; d is 16 x 8 row-major.  Support call for checking the
+ * fragment mapping; the paper has no counterpart.  Stream-ordered, no synchronisation. */
+pc_status pc_debug_mma_tf32(const float *a, const float *b, float *d, void *stream);
 
 /* ---------------------------------------------------------------------------------
  * kappa_estimate - Lanczos estimate of kappa (Sec. 3.1) for A (block_size == 0) or for

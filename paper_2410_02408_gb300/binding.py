@@ -89,6 +89,7 @@ def lib():
         "pc_spmv": (_I32, [ctypes.POINTER(pc_csr), _P, _P, _P]),
         "pc_dot": (_I32, [_I64, _P, _P, _P, _P]),
         "pc_debug_convert": (_I32, [_I64, _P, _P, _P, _P, _P]),
+        "pc_debug_mma_tf32": (_I32, [_P, _P, _P, _P]),
         "kappa_estimate": (_I32, [ctypes.POINTER(pc_csr), _I32, _I32, _D, _P, _I32,
                                   ctypes.POINTER(pc_kappa_info), _P]),
         "kappa_estimate_h": (_I32, [_P, ctypes.POINTER(pc_csr), _I32, _D, _P, _I32,
@@ -369,6 +370,19 @@ def debug_convert(d, f):
     _check(lib().pc_debug_convert(d.shape[0], _ptr(d), _ptr(out_f), _ptr(f), _ptr(out_d), _stream()),
            "pc_debug_convert")
     return out_f, out_d
+
+
+def debug_mma_tf32(a, b):
+    """One tensor-core product d = a b (a 16x8, b 8x8, FP32 in, TF32 operands, FP32 accumulate),
+    as the TF32 setup issues it (pc_debug_mma_tf32)."""
+    torch = _torch()
+    a = _dev(a, torch.float32)
+    b = _dev(b, torch.float32)
+    if tuple(a.shape) != (16, 8) or tuple(b.shape) != (8, 8):
+        raise ValueError("a must be 16x8 and b 8x8")
+    d = torch.empty((16, 8), dtype=torch.float32, device="cuda")
+    _check(lib().pc_debug_mma_tf32(_ptr(a), _ptr(b), _ptr(d), _stream()), "pc_debug_mma_tf32")
+    return d
 
 
 def dot(x, y) -> float:

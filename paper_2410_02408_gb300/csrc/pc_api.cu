@@ -328,7 +328,8 @@ pc_status pc_setup(const pc_csr* A, int32_t block_size, double tol, int32_t prec
   a.minv = h->minv;
   a.linv = h->linv;
   a.failed = h->failed_d;
-  if (e == cudaSuccess) e = pc::launch_setup(a, h->val_f32, h->fac_f32, st);
+  if (e == cudaSuccess)
+    e = prec == PC_PREC_TF32 ? pc::launch_setup_tf32(a, h->val_f32, st) : pc::launch_setup(a, h->val_f32, h->fac_f32, st);
   unsigned long long failed = ~0ull;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&failed, h->failed_d, sizeof(failed), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -405,6 +406,11 @@ pc_status pc_debug_convert(int64_t n, const double* in_d, float* out_f, const fl
   if (n < 0 || (n > 0 && (!in_d || !out_f || !in_f || !out_d))) return PC_ERR_INVALID_ARG;
   if (n == 0) return PC_OK;
   return from_cuda(pc::launch_convert(n, in_d, out_f, in_f, out_d, (cudaStream_t)stream));
+}
+
+pc_status pc_debug_mma_tf32(const float* a, const float* b, float* d, void* stream) {
+  if (!a || !b || !d) return PC_ERR_INVALID_ARG;
+  return from_cuda(pc::launch_mma_tf32_check(a, b, d, (cudaStream_t)stream));
 }
 
 pc_status pc_dot(int64_t n, const double* x, const double* y, double* result, void* stream) {

@@ -71,6 +71,7 @@ struct BArgs {
   int32_t slot_bytes;        // shared memory per setup slot
   unsigned long long* prof;  // null, or PH_N phase accumulators (profiling mode)
   int32_t smem_bytes;        // dynamic shared memory of a CTA
+  int32_t tc;                // FP32 factors: M^{-1} formed on the tensor cores (PC_PREC_TF32)
 };
 
 struct Team {
@@ -94,6 +95,7 @@ struct Env {
   int32_t max_iter, max_restarts;
   int32_t setup_warps, slot_bytes, smem_bytes;
   unsigned long long* prof;   // null, or per-phase nanoseconds summed over CTAs (profiling mode)
+  int32_t tc;                 // FP32 factors: M^{-1} formed on the tensor cores (PC_PREC_TF32)
 };
 
 // Profiling mode: thread 0 of every CTA adds the time since its previous mark to a phase
@@ -291,6 +293,14 @@ __device__ __noinline__ void phase_setup(const Env& e, const SysCtx& c, unsigned
   FT* Xs = As + (size_t)L.U * (L.bs + 1);
   FT* Mf = reinterpret_cast<FT*>(const_cast<void*>(c.Mf));
   const int64_t uM = unit_elems_minv(L);
+  if constexpr (sizeof(FT) == 4) {
+    if (e.tc) {
+      for (int64_t u = c.u0 + warp; u < c.u1; u += nw)
+        setup_unit<double, FT, FT, true>(L, u, c.rp, e.ci, e.va, e.pivot_tol, Mf + u * uM, nullptr, As, Xs,
+                                         threadIdx.x & 31, &e.fail[c.s]);
+      return;
+    }
+  }
   for (int64_t u = c.u0 + warp; u < c.u1; u += nw)
     setup_unit<double, FT, FT>(L, u, c.rp, e.ci, e.va, e.pivot_tol, Mf + u * uM, nullptr, As, Xs, threadIdx.x & 31,
                            &e.fail[c.s]);
@@ -538,6 +548,7 @@ __global__ void __launch_bounds__(BT, 2) batched_kernel(const __grid_constant__ 
     env.slot_bytes = a.slot_bytes;
     env.prof = a.prof;
     env.smem_bytes = a.smem_bytes;
+    env.tc = a.tc;
   }
   unsigned long long idle_from = a.prof != nullptr && threadIdx.x == 0 ? globaltimer_ns() : 0ull;
   for (;;) {
@@ -965,6 +976,7 @@ pc_status pc_batch_create(const pc_batch* B, int32_t prec, double pivot_tol, voi
   a.o_restarts = h->o_restarts;
   a.o_relres = h->d_relres;
   a.pivot_tol = pivot_tol;
+  a.tc = prec == PC_PREC_TF32 ? 1 : 0;
   a.max_restarts = 3;
   a.budget = batch_budget();
   a.setup_warps = setup_warps;

@@ -96,6 +96,8 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 
 // pc_setup.cu
 cudaError_t launch_setup(const SetupArgs& a, bool val_f32, bool fac_f32, cudaStream_t st);
+// PC_PREC_TF32: FP32 factorisation, M^{-1} formed on the tensor cores (TF32 operands, FP32 accumulation).
+cudaError_t launch_setup_tf32(const SetupArgs& a, bool val_f32, cudaStream_t st);
 cudaError_t launch_extract(int64_t n, const int32_t* rp, const int32_t* ci, const void* va, bool val_f32,
                            int32_t bs, double* out, cudaStream_t st);
 cudaError_t launch_get_factor(const Layout& L, const void* fac, bool fac_f32, int which, double* out,
@@ -109,6 +111,8 @@ constexpr unsigned CSR_BAD_ORDER = 4u;     // columns of a row not strictly incr
 constexpr unsigned CSR_NO_DIAGONAL = 8u;   // a row without its diagonal entry
 cudaError_t launch_validate_csr(int64_t n, int64_t nnz, const int32_t* rp, const int32_t* ci, unsigned* flags,
                                 cudaStream_t st);
+// D (16x8) = A (16x8) B (8x8), row-major, on the tensor cores with TF32 operands (one warp)
+cudaError_t launch_mma_tf32_check(const float* A, const float* B, float* D, cudaStream_t st);
 // out_f[i] = d2f(in_d[i]), out_d[i] = f2d(in_f[i]) (the conversions of pc_common.cuh)
 cudaError_t launch_convert(int64_t n, const double* in_d, float* out_f, const float* in_f, double* out_d,
                            cudaStream_t st);

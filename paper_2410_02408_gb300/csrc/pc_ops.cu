@@ -4,8 +4,34 @@
 // the persistent CG kernel, the adjoint gradient on the sparsity pattern, and the O(nnz)
 // structure check of a CSR matrix.
 #include "pc_kernels.cuh"
+#include "pc_setup_unit.cuh"
 
 namespace pc {
+
+// One tensor-core product D = A B (A 16x8, B 8x8, row-major in global memory), operands
+// rounded to TF32, FP32 accumulation: the fragment mapping of mma_tf32_m16n8k8, for checks.
+__global__ void mma_tf32_check_kernel(const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ D) {
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  uint32_t a[4], b[2];
+  a[0] = tf32_rna(A[g * 8 + t]);
+  a[1] = tf32_rna(A[(g + 8) * 8 + t]);
+  a[2] = tf32_rna(A[g * 8 + t + 4]);
+  a[3] = tf32_rna(A[(g + 8) * 8 + t + 4]);
+  b[0] = tf32_rna(B[t * 8 + g]);
+  b[1] = tf32_rna(B[(t + 4) * 8 + g]);
+  float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  mma_tf32_m16n8k8(d, a, b);
+  D[g * 8 + 2 * t] = d[0];
+  D[g * 8 + 2 * t + 1] = d[1];
+  D[(g + 8) * 8 + 2 * t] = d[2];
+  D[(g + 8) * 8 + 2 * t + 1] = d[3];
+}
+
+cudaError_t launch_mma_tf32_check(const float* A, const float* B, float* D, cudaStream_t st) {
+  mma_tf32_check_kernel<<<1, 32, 0, st>>>(A, B, D);
+  return cudaGetLastError();
+}
 
 // CSR structure check, one thread per row: the row's range must lie inside [0, nnz] and not
 // decrease, and its columns must lie in [0, n), increase strictly and include the row

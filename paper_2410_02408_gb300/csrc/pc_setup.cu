@@ -6,7 +6,7 @@
 
 namespace pc {
 
-template <typename VT, typename FT, typename ST = FT>
+template <typename VT, typename FT, typename ST = FT, bool TC = false>
 __global__ void __launch_bounds__(128) setup_kernel(SetupArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Layout L = a.lay;
@@ -20,8 +20,8 @@ __global__ void __launch_bounds__(128) setup_kernel(SetupArgs a) {
   ST* Lo = reinterpret_cast<ST*>(a.linv);
   const int64_t uM = unit_elems_minv(L), uL = unit_elems_linv(L);
   for (int64_t u = (int64_t)blockIdx.x * nw + warp; u < L.n_units; u += (int64_t)gridDim.x * nw)
-    setup_unit<VT, FT, ST>(L, u, a.row_ptr, a.col, va, a.tol, Mo + u * uM, Lo ? Lo + u * uL : nullptr, As, Xs, lane,
-                           a.failed);
+    setup_unit<VT, FT, ST, TC>(L, u, a.row_ptr, a.col, va, a.tol, Mo + u * uM, Lo ? Lo + u * uL : nullptr, As, Xs,
+                               lane, a.failed);
 }
 
 // Dense copy of the diagonal blocks (bit-exact value copy; rows past n are zero).
@@ -81,27 +81,28 @@ __global__ void get_factor_kernel(Layout L, const FT* __restrict__ fac, int whic
 }
 
 // ------------------------------------------------------------------ launchers
-template <typename VT, typename FT, typename ST = FT>
+template <typename VT, typename FT, typename ST = FT, bool TC = false>
 static cudaError_t launch_setup_t(const SetupArgs& a, cudaStream_t st) {
   const Layout& L = a.lay;
   const size_t per_warp = (size_t)2 * L.U * (L.bs + 1) * sizeof(FT);
   int warps = 4;
   while (warps > 1 && per_warp * warps > 200 * 1024) --warps;
   const size_t smem = per_warp * warps;
-  cudaError_t e = cudaFuncSetAttribute(setup_kernel<VT, FT, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e =
+      cudaFuncSetAttribute(setup_kernel<VT, FT, ST, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, setup_kernel<VT, FT, ST>, warps * 32, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, setup_kernel<VT, FT, ST, TC>, warps * 32, smem);
   if (e != cudaSuccess) return e;
   if (occ < 1) occ = 1;
   int64_t need = (L.n_units + warps - 1) / warps;
   int64_t grid = (int64_t)sms * occ * 4;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-  setup_kernel<VT, FT, ST><<<(unsigned)grid, warps * 32, smem, st>>>(a);
+  setup_kernel<VT, FT, ST, TC><<<(unsigned)grid, warps * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -110,6 +111,13 @@ cudaError_t launch_setup(const SetupArgs& a, bool val_f32, bool fac_f32, cudaStr
   if (!val_f32 && fac_f32) return launch_setup_t<double, float>(a, st);
   if (val_f32 && fac_f32) return launch_setup_t<float, float>(a, st);
   return launch_setup_t<float, double>(a, st);
+}
+
+// FP32 arithmetic with M^{-1} = L^{-T} L^{-1} formed on the tensor cores (TF32 operands, FP32
+// accumulation): the PC_PREC_TF32 setup.
+cudaError_t launch_setup_tf32(const SetupArgs& a, bool val_f32, cudaStream_t st) {
+  if (val_f32) return launch_setup_t<float, float, float, true>(a, st);
+  return launch_setup_t<double, float, float, true>(a, st);
 }
 
 // FP64 arithmetic, FP32 stored factors: the fallback for blocks whose FP32 factorisation

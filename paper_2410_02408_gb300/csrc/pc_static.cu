@@ -134,7 +134,8 @@ extern "C" pc_status pcg_solve_noalloc(const pc_csr* A, int32_t block_size, cons
   sa.minv = minv;
   sa.linv = linv;
   sa.failed = failed_d;
-  if (e == cudaSuccess) e = pc::launch_setup(sa, val_f32, fac_f32, st);
+  if (e == cudaSuccess)
+    e = prec == PC_PREC_TF32 ? pc::launch_setup_tf32(sa, val_f32, st) : pc::launch_setup(sa, val_f32, fac_f32, st);
   unsigned long long failed = ~0ull;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&failed, failed_d, sizeof(failed), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -401,6 +401,18 @@ def powerlaw_spd(n: int = 8_000_000, seed: int = 5, w_min: int = 8, w_max: int =
     return A
 
 
+def random_spd(n: int, mean_deg: float, seed: int = 11, dtype=np.float64) -> CSR:
+    """The paper-size random SPD family (the paper draws "sparse, Hermitian, positive-definite
+    matrices" of N = 2^10, 2^12, 2^14 with varying sparsity, Sec. 4.2 and 5.1, without a recipe):
+    the power-law recipe of ``powerlaw_spd`` (Chung-Lu edges, U(-1, 0) off-diagonals, diagonal
+    = row |sum| + 1e-2, reverse Cuthill-McKee order) with expected degrees on
+    [2, max(mean_deg + 1, min(1999, n // 4))] and mean ``mean_deg``."""
+    w_max = int(max(mean_deg + 1, min(1999, n // 4)))
+    A = powerlaw_spd(n, seed=seed, w_min=2, w_max=w_max, mean_deg=float(mean_deg), cap=min(2000, n), dtype=dtype)
+    A.meta.update({"kind": "random_spd", "mean_deg": mean_deg})
+    return A
+
+
 # ---------------------------------------------------------------------------
 # Named workloads
 # ---------------------------------------------------------------------------
