@@ -294,3 +294,135 @@ def grad_edges(p: np.ndarray, q: np.ndarray, lam: np.ndarray, x: np.ndarray) -> 
     g = np.zeros(p.shape[0])
     lib().or_grad_edges(p.shape[0], _ptr(p), _ptr(q), _ptr(lam), _ptr(x), _ptr(g))
     return g
+
+
+# ---------------------------------------------------------------- complex Hermitian (Sec. 3.1)
+def _zdeclare(L):
+    L.zor_dotc.restype = None
+    L.zor_dotc.argtypes = [_i64, _p, _p, _p]
+    L.zor_spmv.restype = None
+    L.zor_spmv.argtypes = [_i64, _p, _p, _p, _p, _p]
+    L.zor_extract_blocks.restype = None
+    L.zor_extract_blocks.argtypes = [_i64, _p, _p, _p, _i32, _p]
+    L.zor_cholesky.restype = _i32
+    L.zor_cholesky.argtypes = [_i32, _i32, _p, _p, _dbl]
+    L.zor_cholesky_blocks.restype = _i64
+    L.zor_cholesky_blocks.argtypes = [_i64, _i32, _p, _p, _dbl]
+    L.zor_block_apply.restype = None
+    L.zor_block_apply.argtypes = [_i64, _i32, _p, _i32, _p, _p]
+    L.zor_pcg.restype = _i32
+    L.zor_pcg.argtypes = [_i64, _p, _p, _p, _i32, _p, _p, _p, _dbl, _i32, _i32, _p]
+    L.zor_lanczos.restype = _i32
+    L.zor_lanczos.argtypes = [_i64, _p, _p, _p, _i32, _p, _p, _i32, _dbl, _i32, _p, _p, _p]
+
+
+def zlib():
+    L = lib()
+    if not getattr(L, "_z_declared", False):
+        _zdeclare(L)
+        L._z_declared = True
+    return L
+
+
+@dataclass
+class ZMatrix:
+    """Complex CSR: int32 indices, complex128 values."""
+
+    row_ptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+
+    @property
+    def n(self):
+        return self.row_ptr.shape[0] - 1
+
+
+def as_zmatrix(A) -> ZMatrix:
+    return ZMatrix(np.ascontiguousarray(A.row_ptr, dtype=np.int32), np.ascontiguousarray(A.col, dtype=np.int32),
+                   np.ascontiguousarray(A.val, dtype=np.complex128))
+
+
+def zdot(x, y) -> complex:
+    """x^H y."""
+    x = np.ascontiguousarray(x, dtype=np.complex128)
+    y = np.ascontiguousarray(y, dtype=np.complex128)
+    out = np.zeros(2)
+    zlib().zor_dotc(x.shape[0], _ptr(x), _ptr(y), _ptr(out))
+    return complex(out[0], out[1])
+
+
+def zspmv(A, x):
+    M = as_zmatrix(A)
+    x = np.ascontiguousarray(x, dtype=np.complex128)
+    y = np.zeros(M.n, dtype=np.complex128)
+    zlib().zor_spmv(M.n, _ptr(M.row_ptr), _ptr(M.col), _ptr(M.val), _ptr(x), _ptr(y))
+    return y
+
+
+def zextract_blocks(A, bs: int):
+    M = as_zmatrix(A)
+    out = np.zeros((num_blocks(M.n, bs), bs, bs), dtype=np.complex128)
+    zlib().zor_extract_blocks(M.n, _ptr(M.row_ptr), _ptr(M.col), _ptr(M.val), bs, _ptr(out))
+    return out
+
+
+def zcholesky(D, tol: float = 0.0):
+    """A = L L^H of one dense Hermitian PD matrix; returns (L, failing column or -1)."""
+    D = np.ascontiguousarray(D, dtype=np.complex128)
+    L = np.zeros_like(D)
+    f = zlib().zor_cholesky(D.shape[0], D.shape[0], _ptr(D), _ptr(L), tol)
+    return L, int(f)
+
+
+def zfactor(A, bs: int, tol: float = 0.0):
+    """Block factors L_k (A_kk = L_k L_k^H): (L blocks, failing block or -1)."""
+    M = as_zmatrix(A)
+    D = zextract_blocks(M, bs)
+    L = np.zeros_like(D)
+    f = zlib().zor_cholesky_blocks(M.n, bs, _ptr(D), _ptr(L), tol)
+    return L, int(f)
+
+
+def zapply(L, n: int, bs: int, mode: int, v):
+    """mode 0: M^{-1} v = L^{-H} L^{-1} v; 2: L^{-1} v; 3: L^{-H} v."""
+    L = np.ascontiguousarray(L, dtype=np.complex128)
+    v = np.ascontiguousarray(v, dtype=np.complex128)
+    out = np.zeros(n, dtype=np.complex128)
+    zlib().zor_block_apply(n, bs, _ptr(L), mode, _ptr(v), _ptr(out))
+    return out
+
+
+def zpcg(A, b, bs: int = 0, tol: float = 1e-10, max_iter: int = 100000, x0=None, max_restarts: int = 3, L=None):
+    """Block-Jacobi PCG for Hermitian PD A (bs == 0: unpreconditioned)."""
+    M = as_zmatrix(A)
+    if bs > 0 and L is None:
+        L, f = zfactor(M, bs)
+        if f >= 0:
+            return {"status": "not_spd", "failed_block": f, "x": None}
+    b = np.ascontiguousarray(b, dtype=np.complex128)
+    x = np.zeros(M.n, dtype=np.complex128) if x0 is None else np.array(x0, dtype=np.complex128)
+    out = np.zeros(4)
+    st = zlib().zor_pcg(M.n, _ptr(M.row_ptr), _ptr(M.col), _ptr(M.val), bs, _ptr(L) if bs > 0 else None, _ptr(b),
+                        _ptr(x), tol, max_iter, max_restarts, _ptr(out))
+    return {"status": STATUS[int(st)], "x": x, "iterations": int(out[0]), "rel_residual": float(out[1]),
+            "true_rel_residual": float(out[2]), "restarts": int(out[3])}
+
+
+def zkappa(A, v0, m: int = 200, bs: int = 0, tol: float = 1e-12, reorth: bool = True):
+    """Lanczos estimate of kappa for Hermitian PD A (bs == 0) or L^{-1} A L^{-H}."""
+    M = as_zmatrix(A)
+    L = None
+    if bs > 0:
+        L, f = zfactor(M, bs)
+        if f >= 0:
+            raise ValueError(f"block {f} is not HPD")
+    v0 = np.ascontiguousarray(v0, dtype=np.complex128)
+    alpha = np.zeros(m)
+    beta = np.zeros(m)
+    basis = np.zeros((m, M.n), dtype=np.complex128)
+    k = zlib().zor_lanczos(M.n, _ptr(M.row_ptr), _ptr(M.col), _ptr(M.val), bs, _ptr(L) if bs > 0 else None,
+                           _ptr(v0), m, tol, int(reorth), _ptr(alpha), _ptr(beta), _ptr(basis))
+    alpha, beta = alpha[:k].copy(), beta[:k].copy()
+    lo = tridiag_eig(alpha, beta[:k - 1], 0)
+    hi = tridiag_eig(alpha, beta[:k - 1], k - 1)
+    return {"kappa": hi / lo, "lambda_min": lo, "lambda_max": hi, "steps": k, "alpha": alpha, "beta": beta}

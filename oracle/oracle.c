@@ -25,6 +25,9 @@
  *   or_grad_val        - adjoint gradient dL/dA_ij = -lambda_i x_j on the pattern
  *   or_grad_edges      - the same adjoint for a matrix assembled from edge coefficients,
  *                        A = sum_e c_e (e_p - e_q)(e_p - e_q)^T + sum_f c_f e_p e_p^T
+ *   zor_*              - the same for complex Hermitian positive definite A (Sec. 3.1):
+ *                        A_k = L L^H, M^{-1} = L^{-H} L^{-1}, PCG with conjugate dots,
+ *                        Lanczos with a complex basis and a real tridiagonal
  *
  * Condition number (Sec. 3.1): for the SPD operators here kappa = lambda_max/lambda_min.
  *
@@ -519,4 +522,300 @@ void or_grad_edges(int64_t n_edges, const int32_t *p, const int32_t *q, const do
     else
       gc[e] = -(lambda[p[e]] - lambda[q[e]]) * (x[p[e]] - x[q[e]]);
   }
+}
+
+/* ========================================================================= */
+/* Complex Hermitian positive definite systems (Sec. 3.1: A is Hermitian PD).
+ * Values are C99 double complex (interleaved re, im in memory).  Same algorithms as the real
+ * routines above with the Hermitian transpose: A_k = L L^H (real positive diagonal),
+ * M^{-1} = L^{-H} L^{-1}, conjugate dot products, and Lanczos with a real tridiagonal. */
+#include <complex.h>
+
+typedef double complex zdbl;
+
+static zdbl zdot_chunk(int64_t lo, int64_t hi, const zdbl *x, const zdbl *y) {
+  zdbl s = 0.0;
+  for (int64_t i = lo; i < hi; ++i) s += conj(x[i]) * y[i];
+  return s;
+}
+
+/* x^H y: terms added in index order within chunks of OR_CHUNK, then the chunk sums in order. */
+static zdbl zdot_serial(int64_t n, const zdbl *x, const zdbl *y) {
+  zdbl s = 0.0;
+  for (int64_t lo = 0; lo < n; lo += OR_CHUNK)
+    s += zdot_chunk(lo, lo + OR_CHUNK < n ? lo + OR_CHUNK : n, x, y);
+  return s;
+}
+
+static zdbl zdot(int64_t n, const zdbl *x, const zdbl *y) {
+  if (n < OR_PAR_MIN) return zdot_serial(n, x, y);
+  int64_t nc = (n + OR_CHUNK - 1) / OR_CHUNK;
+  zdbl *part = (zdbl *)malloc(sizeof(zdbl) * nc);
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < nc; ++c) {
+    int64_t lo = c * OR_CHUNK;
+    part[c] = zdot_chunk(lo, lo + OR_CHUNK < n ? lo + OR_CHUNK : n, x, y);
+  }
+  zdbl s = 0.0;
+  for (int64_t c = 0; c < nc; ++c) s += part[c];
+  free(part);
+  return s;
+}
+
+/* x^H y written to out[0] (re), out[1] (im). */
+void zor_dotc(int64_t n, const zdbl *x, const zdbl *y, double *out) {
+  zdbl s = zdot(n, x, y);
+  out[0] = creal(s);
+  out[1] = cimag(s);
+}
+
+void zor_spmv(int64_t n, const int32_t *row_ptr, const int32_t *col, const zdbl *val, const zdbl *x,
+              zdbl *y) {
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
+  for (int64_t i = 0; i < n; ++i) {
+    zdbl s = 0.0;
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) s += val[e] * x[col[e]];
+    y[i] = s;
+  }
+}
+
+void zor_extract_blocks(int64_t n, const int32_t *row_ptr, const int32_t *col, const zdbl *val,
+                        int32_t bs, zdbl *out) {
+  int64_t nb = or_num_blocks(n, bs);
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
+  for (int64_t k = 0; k < nb; ++k) {
+    zdbl *D = out + k * (int64_t)bs * bs;
+    int64_t s = k * (int64_t)bs;
+    int32_t b = block_rows(n, bs, k);
+    for (int64_t t = 0; t < (int64_t)bs * bs; ++t) D[t] = 0.0;
+    for (int32_t i = 0; i < b; ++i) {
+      int64_t row = s + i;
+      for (int64_t e = row_ptr[row]; e < row_ptr[row + 1]; ++e) {
+        int64_t c = col[e];
+        if (c >= s && c < s + b) D[(int64_t)i * bs + (c - s)] = val[e];
+      }
+    }
+  }
+}
+
+/* Column Cholesky A = L L^H of the b x b corner (stride ld): v(j:b) = A(j:b, j) -
+ * sum_{k<j} L(j:b, k) conj(L(j, k)); the pivot is the real part of v(j), which must exceed
+ * tol * max_i Re A_ii (and be finite); returns the failing column or -1. */
+int32_t zor_cholesky(int32_t b, int32_t ld, const zdbl *D, zdbl *L, double tol) {
+  double dmax = 0.0;
+  for (int32_t i = 0; i < b; ++i)
+    if (creal(D[(int64_t)i * ld + i]) > dmax) dmax = creal(D[(int64_t)i * ld + i]);
+  for (int32_t i = 0; i < b; ++i)
+    for (int32_t j = 0; j < ld; ++j) L[(int64_t)i * ld + j] = 0.0;
+  zdbl *v = (zdbl *)malloc(sizeof(zdbl) * (b > 0 ? b : 1));
+  int32_t fail = -1;
+  for (int32_t j = 0; j < b && fail < 0; ++j) {
+    for (int32_t i = j; i < b; ++i) {
+      zdbl s = D[(int64_t)i * ld + j];
+      for (int32_t k = 0; k < j; ++k) s -= L[(int64_t)i * ld + k] * conj(L[(int64_t)j * ld + k]);
+      v[i] = s;
+    }
+    double piv = creal(v[j]);
+    if (!(piv > tol * dmax) || !isfinite(piv)) {
+      fail = j;
+      break;
+    }
+    double d = sqrt(piv);
+    L[(int64_t)j * ld + j] = d;
+    for (int32_t i = j + 1; i < b; ++i) L[(int64_t)i * ld + j] = v[i] / d;
+  }
+  free(v);
+  return fail;
+}
+
+int64_t zor_cholesky_blocks(int64_t n, int32_t bs, const zdbl *D, zdbl *L, double tol) {
+  int64_t nb = or_num_blocks(n, bs);
+  for (int64_t k = 0; k < nb; ++k) {
+    int32_t f = zor_cholesky(block_rows(n, bs, k), bs, D + k * (int64_t)bs * bs, L + k * (int64_t)bs * bs, tol);
+    if (f >= 0) return k;
+  }
+  return -1;
+}
+
+/* mode 0: z = L^{-H} L^{-1} r;  2: z = L^{-1} r;  3: z = L^{-H} r. */
+static void zforward(int32_t b, int32_t ld, const zdbl *L, const zdbl *r, zdbl *y) {
+  for (int32_t i = 0; i < b; ++i) {
+    zdbl s = r[i];
+    for (int32_t k = 0; k < i; ++k) s -= L[(int64_t)i * ld + k] * y[k];
+    y[i] = s / creal(L[(int64_t)i * ld + i]);
+  }
+}
+
+static void zbackward(int32_t b, int32_t ld, const zdbl *L, const zdbl *y, zdbl *z) {
+  for (int32_t i = b - 1; i >= 0; --i) {
+    zdbl s = y[i];
+    for (int32_t k = i + 1; k < b; ++k) s -= conj(L[(int64_t)k * ld + i]) * z[k];
+    z[i] = s / creal(L[(int64_t)i * ld + i]);
+  }
+}
+
+void zor_block_apply(int64_t n, int32_t bs, const zdbl *L, int32_t mode, const zdbl *r, zdbl *z) {
+  int64_t nb = or_num_blocks(n, bs);
+#pragma omp parallel if (n >= OR_PAR_MIN)
+  {
+    zdbl *y = (zdbl *)malloc(sizeof(zdbl) * bs);
+#pragma omp for schedule(static)
+    for (int64_t k = 0; k < nb; ++k) {
+      int64_t s = k * (int64_t)bs;
+      int32_t b = block_rows(n, bs, k);
+      const zdbl *Lk = L + k * (int64_t)bs * bs;
+      if (mode == 0) {
+        zforward(b, bs, Lk, r + s, y);
+        zbackward(b, bs, Lk, y, z + s);
+      } else if (mode == 2) {
+        zforward(b, bs, Lk, r + s, z + s);
+      } else {
+        zbackward(b, bs, Lk, r + s, z + s);
+      }
+    }
+    free(y);
+  }
+}
+
+/* Preconditioned CG for Hermitian PD A with M = blockdiag(L_k L_k^H), x0 given (x in/out):
+ *   r = b - A x;  z = M^{-1} r;  p = z;  rho = r^H z (real)
+ *   loop: q = A p;  alpha = rho / Re(p^H q);  x += alpha p;  r -= alpha q;  stop at ||r|| <= tol ||b||
+ *         z = M^{-1} r;  rho' = Re(r^H z);  beta = rho'/rho;  p = z + beta p
+ * with the same true-residual restarts as or_pcg.  out: iterations, recurrence and true
+ * relative residuals, restarts. */
+int32_t zor_pcg(int64_t n, const int32_t *row_ptr, const int32_t *col, const zdbl *val, int32_t bs,
+                const zdbl *L, const zdbl *b, zdbl *x, double tol, int32_t max_iter,
+                int32_t max_restarts, double *out) {
+  zdbl *r = (zdbl *)malloc(sizeof(zdbl) * n);
+  zdbl *z = (zdbl *)malloc(sizeof(zdbl) * n);
+  zdbl *p = (zdbl *)malloc(sizeof(zdbl) * n);
+  zdbl *q = (zdbl *)malloc(sizeof(zdbl) * n);
+  int32_t status = OR_OK;
+  int32_t it = 0, restarts = 0;
+  double bnorm = sqrt(creal(zdot(n, b, b)));
+  double rnorm = 0.0, tnorm = 0.0;
+  if (bnorm == 0.0) {
+    for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+    goto done;
+  }
+  for (;;) {
+    zor_spmv(n, row_ptr, col, val, x, q);
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
+    if (L) zor_block_apply(n, bs, L, 0, r, z);
+    else memcpy(z, r, sizeof(zdbl) * n);
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
+    for (int64_t i = 0; i < n; ++i) p[i] = z[i];
+    double rho = creal(zdot(n, r, z));
+    rnorm = sqrt(creal(zdot(n, r, r)));
+    int converged = rnorm <= tol * bnorm;
+    while (!converged) {
+      if (it >= max_iter) { status = OR_NO_CONVERGENCE; goto done; }
+      if (!(rho > 0.0) || !isfinite(rho)) { status = OR_BREAKDOWN; goto done; }
+      zor_spmv(n, row_ptr, col, val, p, q);
+      double pq = creal(zdot(n, p, q));
+      if (!(pq > 0.0) || !isfinite(pq)) { status = OR_BREAKDOWN; goto done; }
+      double alpha = rho / pq;
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
+      for (int64_t i = 0; i < n; ++i) x[i] += alpha * p[i];
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
+      for (int64_t i = 0; i < n; ++i) r[i] -= alpha * q[i];
+      ++it;
+      rnorm = sqrt(creal(zdot(n, r, r)));
+      if (rnorm <= tol * bnorm) { converged = 1; break; }
+      if (L) zor_block_apply(n, bs, L, 0, r, z);
+      else memcpy(z, r, sizeof(zdbl) * n);
+      double rho_new = creal(zdot(n, r, z));
+      double beta = rho_new / rho;
+      rho = rho_new;
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
+      for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+    }
+    zor_spmv(n, row_ptr, col, val, x, q);
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
+    tnorm = sqrt(creal(zdot(n, r, r)));
+    if (tnorm <= tol * bnorm) break;
+    if (restarts >= max_restarts) { status = OR_NO_CONVERGENCE; goto done; }
+    ++restarts;
+  }
+done:
+  if (out) {
+    out[0] = (double)it;
+    out[1] = bnorm > 0.0 ? rnorm / bnorm : 0.0;
+    if (bnorm > 0.0) {
+      zor_spmv(n, row_ptr, col, val, x, q);
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
+      for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
+      out[2] = sqrt(creal(zdot(n, r, r))) / bnorm;
+    } else {
+      out[2] = 0.0;
+    }
+    out[3] = (double)restarts;
+  }
+  free(r); free(z); free(p); free(q);
+  return status;
+}
+
+/* Hermitian Lanczos on Op = A (L == NULL) or L^{-1} A L^{-H}, complex basis, real tridiagonal:
+ *   q_1 = v0/||v0|| (L^{-1} v0 normalised when preconditioned)
+ *   w = Op q_j - beta_{j-1} q_{j-1};  alpha_j = Re(q_j^H w);  w -= alpha_j q_j
+ *   reorth: twice { c_l = q_l^H w for l <= j;  w -= sum_l c_l q_l }
+ *   beta_j = ||w||; stop as or_lanczos.  basis: m * n complex workspace. */
+int32_t zor_lanczos(int64_t n, const int32_t *row_ptr, const int32_t *col, const zdbl *val, int32_t bs,
+                    const zdbl *L, const zdbl *v0, int32_t m, double tol, int32_t reorth, double *alpha,
+                    double *beta, zdbl *basis) {
+  zdbl *w = (zdbl *)malloc(sizeof(zdbl) * n);
+  zdbl *t1 = (zdbl *)malloc(sizeof(zdbl) * n);
+  zdbl *t2 = (zdbl *)malloc(sizeof(zdbl) * n);
+  zdbl *c = (zdbl *)malloc(sizeof(zdbl) * (m > 0 ? m : 1));
+  zdbl *q0 = basis;
+  if (L) zor_block_apply(n, bs, L, 2, v0, q0);
+  else memcpy(q0, v0, sizeof(zdbl) * n);
+  double nrm = sqrt(creal(zdot(n, q0, q0)));
+  for (int64_t i = 0; i < n; ++i) q0[i] = q0[i] / nrm;
+  double tnorm = 0.0;
+  int32_t steps = 0;
+  for (int32_t j = 0; j < m; ++j) {
+    zdbl *qj = basis + (int64_t)j * n;
+    if (L) {
+      zor_block_apply(n, bs, L, 3, qj, t1);
+      zor_spmv(n, row_ptr, col, val, t1, t2);
+      zor_block_apply(n, bs, L, 2, t2, w);
+    } else {
+      zor_spmv(n, row_ptr, col, val, qj, w);
+    }
+    if (j > 0) {
+      zdbl *qp = basis + (int64_t)(j - 1) * n;
+      for (int64_t i = 0; i < n; ++i) w[i] -= beta[j - 1] * qp[i];
+    }
+    double a = creal(zdot(n, qj, w));
+    alpha[j] = a;
+    for (int64_t i = 0; i < n; ++i) w[i] -= a * qj[i];
+    if (reorth) {
+      for (int pass = 0; pass < 2; ++pass) {
+#pragma omp parallel for schedule(dynamic, 1) if (n >= OR_PAR_MIN)
+        for (int32_t l = 0; l <= j; ++l) c[l] = zdot_serial(n, basis + (int64_t)l * n, w);
+#pragma omp parallel for schedule(static) if (n >= OR_PAR_MIN)
+        for (int64_t lo = 0; lo < n; lo += OR_CHUNK) {
+          int64_t hi = lo + OR_CHUNK < n ? lo + OR_CHUNK : n;
+          for (int32_t l = 0; l <= j; ++l) {
+            const zdbl *ql = basis + (int64_t)l * n;
+            for (int64_t i = lo; i < hi; ++i) w[i] -= c[l] * ql[i];
+          }
+        }
+      }
+    }
+    double bj = sqrt(creal(zdot(n, w, w)));
+    beta[j] = bj;
+    steps = j + 1;
+    if (fabs(a) > tnorm) tnorm = fabs(a);
+    if (bj > tnorm) tnorm = bj;
+    if (bj <= tol * tnorm || j + 1 == m) break;
+    if ((int64_t)(j + 1) >= n) break;
+    zdbl *qn = basis + (int64_t)(j + 1) * n;
+    for (int64_t i = 0; i < n; ++i) qn[i] = w[i] / bj;
+  }
+  free(w); free(t1); free(t2); free(c);
+  return steps;
 }

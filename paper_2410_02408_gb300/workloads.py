@@ -46,7 +46,7 @@ class CSR:
         return sp.csr_matrix((self.val, self.col, self.row_ptr), shape=(self.n, self.n))
 
     def to_dense(self) -> np.ndarray:
-        d = np.zeros((self.n, self.n), dtype=np.float64)
+        d = np.zeros((self.n, self.n), dtype=np.complex128 if np.iscomplexobj(self.val) else np.float64)
         rows = np.repeat(np.arange(self.n), np.diff(self.row_ptr))
         d[rows, self.col] = self.val
         return d
@@ -411,6 +411,82 @@ def random_spd(n: int, mean_deg: float, seed: int = 11, dtype=np.float64) -> CSR
     A = powerlaw_spd(n, seed=seed, w_min=2, w_max=w_max, mean_deg=float(mean_deg), cap=min(2000, n), dtype=dtype)
     A.meta.update({"kind": "random_spd", "mean_deg": mean_deg})
     return A
+
+
+# ---------------------------------------------------------------------------
+# Complex Hermitian positive definite (Sec. 3.1 allows Hermitian A)
+# ---------------------------------------------------------------------------
+def magnetic_laplacian_1d(n: int, theta: float) -> CSR:
+    """Path graph with a constant vector potential: A_ii = 2, A_{i,i+1} = -e^{i theta},
+    A_{i+1,i} = -e^{-i theta}, Dirichlet ends (complex128 values).  It is unitarily similar to
+    tridiag(-1, 2, -1) (gauge transform diag(e^{i k theta})), so its eigenvalues are
+    2 - 2 cos(k pi / (n + 1))."""
+    p = np.arange(n, dtype=np.int64)
+    cols = np.stack([p - 1, p, p + 1], axis=1)
+    mask = np.stack([p > 0, np.ones(n, bool), p < n - 1], axis=1)
+    e = np.exp(1j * theta)
+    vals = np.broadcast_to(np.array([-np.conj(e), 2.0 + 0j, -e]), (n, 3)).copy()
+    A = _csr_from_padded(cols, vals, mask)
+    A.meta = {"kind": "magnetic1d", "n": n, "theta": theta}
+    return A
+
+
+def magnetic_laplacian_2d(n: int, flux: float) -> CSR:
+    """Magnetic 5-point Laplacian on an n x n grid (Dirichlet boundary) in the Landau gauge:
+    hops along x carry no phase, a hop from (i, j) to (i, j+1) carries e^{2 pi i flux i}, so every
+    plaquette encloses the flux `flux` (in flux quanta).  A_pp = 4, A_pq = -(hop phase), A_qp =
+    conj(A_pq); Hermitian positive definite (complex128 values)."""
+    N = n * n
+    p = np.arange(N, dtype=np.int64)
+    i = p % n
+    j = p // n
+    ph = np.exp(2j * np.pi * flux * i)          # phase of the hop p -> p + n (j -> j + 1)
+    cols = np.stack([p - n, p - 1, p, p + 1, p + n], axis=1)
+    mask = np.stack([j > 0, i > 0, np.ones(N, bool), i < n - 1, j < n - 1], axis=1)
+    vals = np.stack([-np.conj(ph), -np.ones(N), 4.0 * np.ones(N), -np.ones(N), -ph], axis=1).astype(np.complex128)
+    A = _csr_from_padded(cols, vals, mask)
+    A.meta = {"kind": "magnetic2d", "n": n, "flux": flux}
+    return A
+
+
+def hermitian_diffusion3d(n: int, sigma: float, seed: int = 1, phase_seed: int = 2) -> CSR:
+    """The 3D variable-coefficient diffusion stencil of ``diffusion3d`` (same face coefficients)
+    with a random U(1) phase on every interior face: A_pq = -c_f e^{i phi_f}, A_qp = conj(A_pq)
+    for p < q, phi_f ~ U(-pi, pi) from ``default_rng(phase_seed)`` (drawn for the faces in the
+    order cx, cy, cz), A_pp = sum of the coefficients of the six faces of p (Dirichlet faces on
+    the diagonal only).  Hermitian positive definite (complex128 values)."""
+    cx, cy, cz = diffusion3d_faces(n, sigma, seed)
+    rng = np.random.default_rng(phase_seed)
+    px = np.exp(1j * rng.uniform(-np.pi, np.pi, cx.shape))
+    py = np.exp(1j * rng.uniform(-np.pi, np.pi, cy.shape))
+    pz = np.exp(1j * rng.uniform(-np.pi, np.pi, cz.shape))
+    N = n ** 3
+    cxm, cxp = cx[:, :, :n].reshape(N), cx[:, :, 1:].reshape(N)
+    cym, cyp = cy[:, :n, :].reshape(N), cy[:, 1:, :].reshape(N)
+    czm, czp = cz[:n, :, :].reshape(N), cz[1:, :, :].reshape(N)
+    # phase of the face on each side, seen from the lower-index cell of the pair
+    pxm, pxp = px[:, :, :n].reshape(N), px[:, :, 1:].reshape(N)
+    pym, pyp = py[:, :n, :].reshape(N), py[:, 1:, :].reshape(N)
+    pzm, pzp = pz[:n, :, :].reshape(N), pz[1:, :, :].reshape(N)
+    p = np.arange(N, dtype=np.int64)
+    i = p % n
+    j = (p // n) % n
+    k = p // (n * n)
+    diag = ((((cxm + cxp) + cym) + cyp) + czm) + czp
+    # entry (p, q) for q > p is -c e^{i phi}; for q < p it is the conjugate of entry (q, p)
+    cols = np.stack([p - n * n, p - n, p - 1, p, p + 1, p + n, p + n * n], axis=1)
+    vals = np.stack([-czm * np.conj(pzm), -cym * np.conj(pym), -cxm * np.conj(pxm), diag + 0j,
+                     -cxp * pxp, -cyp * pyp, -czp * pzp], axis=1)
+    mask = np.stack([k > 0, j > 0, i > 0, np.ones(N, bool), i < n - 1, j < n - 1, k < n - 1], axis=1)
+    A = _csr_from_padded(cols, vals, mask)
+    A.meta = {"kind": "hermitian_diffusion3d", "n": n, "sigma": sigma, "seed": seed, "phase_seed": phase_seed}
+    return A
+
+
+def rhs_complex(n: int, seed: int = 0) -> np.ndarray:
+    """b with independent N(0, 1) real and imaginary parts: ``default_rng(seed).standard_normal(2n)``
+    taken as interleaved (re, im) pairs."""
+    return np.random.default_rng(seed).standard_normal(2 * n).view(np.complex128).copy()
 
 
 # ---------------------------------------------------------------------------

@@ -521,3 +521,105 @@ def test_grad_edges_agrees_with_entry_gradient_chain():
     chain = np.concatenate([a.ravel() for a in _face_grad_chain(n, gfn)])
     g = oracle.grad_edges(p, q, lam, x)
     np.testing.assert_allclose(g, chain, rtol=1e-9, atol=1e-12 * np.abs(chain).max())
+
+
+# ---------------------------------------------------------------- complex Hermitian (Sec. 3.1)
+def _hpd_dense(n, seed):
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    return G @ G.conj().T + n * np.eye(n)
+
+
+def test_zdot_and_zspmv_match_numpy():
+    A = W.hermitian_diffusion3d(6, 1.0)
+    x = W.rhs_complex(A.n, 3)
+    y = W.rhs_complex(A.n, 4)
+    assert abs(oracle.zdot(x, y) - np.vdot(x, y)) <= 1e-13 * np.abs(x * y).sum()
+    assert np.allclose(oracle.zspmv(A, x), A.to_dense() @ x, rtol=1e-14, atol=1e-13)
+
+
+def test_zcholesky_matches_lapack():
+    D = _hpd_dense(12, 5)
+    L, f = oracle.zcholesky(D)
+    assert f == -1
+    assert np.allclose(L, np.linalg.cholesky(D), rtol=1e-13, atol=1e-13)
+    assert np.allclose(np.diag(L).imag, 0.0) and (np.diag(L).real > 0).all()
+    assert np.linalg.norm(L @ L.conj().T - D) <= 1e-14 * np.linalg.norm(D) * 10
+    D[3, 3] = -1.0                   # not positive definite: the pivot of column 3 fails
+    assert oracle.zcholesky(D)[1] == 3
+
+
+@pytest.mark.parametrize("bs", [1, 4, 7, 16])
+def test_zapply_is_the_block_diagonal_solve(bs):
+    A = W.hermitian_diffusion3d(5, 1.5)
+    n = A.n
+    L, f = oracle.zfactor(A, bs)
+    assert f == -1
+    v = W.rhs_complex(n, 6)
+    D = A.to_dense()
+    M = np.zeros_like(D)
+    for k in range(0, n, bs):
+        e = min(n, k + bs)
+        M[k:e, k:e] = D[k:e, k:e]
+    assert np.allclose(oracle.zapply(L, n, bs, 0, v), np.linalg.solve(M, v), rtol=1e-12, atol=1e-13)
+    Lf = np.zeros_like(D)
+    for k in range(0, n, bs):
+        e = min(n, k + bs)
+        Lf[k:e, k:e] = L[k // bs, :e - k, :e - k]
+    assert np.allclose(oracle.zapply(L, n, bs, 2, v), np.linalg.solve(Lf, v), rtol=1e-12, atol=1e-13)
+    assert np.allclose(oracle.zapply(L, n, bs, 3, v), np.linalg.solve(Lf.conj().T, v), rtol=1e-12, atol=1e-13)
+
+
+def test_zkappa_magnetic_path_closed_form():
+    # a constant vector potential on a path is a gauge transform of tridiag(-1, 2, -1):
+    # kappa = cot^2(pi / (2 (n + 1))), point Jacobi leaves it unchanged (constant diagonal)
+    n = 30
+    A = W.magnetic_laplacian_1d(n, 0.7)
+    ref = 1.0 / math.tan(math.pi / (2 * (n + 1))) ** 2
+    b = W.rhs_complex(n, 0)
+    assert oracle.zkappa(A, b, 60, 0)["kappa"] == pytest.approx(ref, rel=1e-10)
+    assert oracle.zkappa(A, b, 60, 1)["kappa"] == pytest.approx(ref, rel=1e-10)
+
+
+@pytest.mark.parametrize("bs", [0, 4, 12])
+def test_zkappa_matches_dense_eigenvalues(bs):
+    A = W.magnetic_laplacian_2d(12, 0.13)      # N = 144 <= 200 steps: Lanczos is exact
+    D = A.to_dense()
+    if bs:
+        L, f = oracle.zfactor(A, bs)
+        assert f == -1
+        Lf = np.zeros_like(D)
+        for k in range(0, A.n, bs):
+            e = min(A.n, k + bs)
+            Lf[k:e, k:e] = L[k // bs, :e - k, :e - k]
+        Li = np.linalg.inv(Lf)
+        D = Li @ D @ Li.conj().T
+    ev = np.linalg.eigvalsh(D)
+    k = oracle.zkappa(A, W.rhs_complex(A.n, 0), 200, bs)
+    assert k["kappa"] == pytest.approx(ev[-1] / ev[0], rel=1e-9)
+
+
+@pytest.mark.parametrize("bs", [0, 1, 8, 27])
+def test_zpcg_matches_dense_solve(bs):
+    A = W.hermitian_diffusion3d(6, 1.5)
+    b = W.rhs_complex(A.n, 0)
+    r = oracle.zpcg(A, b, bs, 1e-12)
+    assert r["status"] == "ok"
+    D = A.to_dense()
+    x_ref = np.linalg.solve(D, b)
+    res = np.linalg.norm(D @ r["x"] - b) / np.linalg.norm(b)
+    assert res <= 1e-12 and r["true_rel_residual"] == pytest.approx(res, rel=1e-6)
+    ev = np.linalg.eigvalsh(D)
+    assert np.linalg.norm(r["x"] - x_ref) <= 1e-12 * ev[-1] / ev[0] * np.linalg.norm(x_ref)
+
+
+def test_complex_routines_reduce_to_the_real_ones_on_real_matrices():
+    A = W.poisson2d(16)
+    Az = W.CSR(A.row_ptr, A.col, A.val.astype(np.complex128))
+    b = W.rhs(A.n, 0)
+    rz = oracle.zpcg(Az, b.astype(np.complex128), 8, 1e-10)
+    rr = oracle.pcg(A, b, 8, 1e-10)
+    assert rz["iterations"] == rr["iterations"]
+    assert np.allclose(rz["x"].real, rr["x"], rtol=1e-13, atol=1e-15) and not rz["x"].imag.any()
+    kz = oracle.zkappa(Az, b.astype(np.complex128), 200, 8)["kappa"]
+    assert kz == pytest.approx(oracle.kappa(A, b, 200, 8)["kappa"], rel=1e-12)
