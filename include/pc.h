@@ -287,6 +287,47 @@ pc_status pc_grad_edges(int64_t n_edges, const int32_t *p, const int32_t *q, con
                         const double *x, int64_t n, double *grad_c, void *stream);
 
 /* ---------------------------------------------------------------------------------
+ * Complex Hermitian positive definite systems (Sec. 3.1 takes A Hermitian PD).  Values are
+ * complex doubles stored as interleaved (real, imaginary) pairs, vectors likewise.
+ *
+ * A z = f is solved as the real system K y = g with y = (Re z_0, Im z_0, Re z_1, ...): the
+ * 2x2 block (i, j) of K is [[b, -c], [c, b]] for a_ij = b + i c.  K is SPD exactly when A is
+ * Hermitian PD and has A's eigenvalues (each twice).  The Cholesky factor of the real form of a
+ * complex diagonal block is the real form of its complex factor A_kk = L_k L_k^H (uniqueness of
+ * the Cholesky factor), so block-Jacobi on K with block size 2 bs is the complex block-Jacobi
+ * preconditioner M = blockdiag(L_k L_k^H), and because every CG and Lanczos scalar of a Hermitian
+ * PD system is real, PCG and Lanczos on K follow the complex iterations step for step.
+ * The CSR structure rules (and pc_csr_check) are those of real matrices; Hermitian symmetry is
+ * the caller's contract (an input that is not Hermitian gives an unsymmetric K and typically a
+ * CG breakdown).  n < 2^30, nnz < 2^29 (K has 2n rows and 4 nnz entries). */
+typedef struct {
+  int64_t n;               /* rows = columns                                            */
+  int64_t nnz;             /* stored complex entries                                    */
+  const int32_t *row_ptr;  /* device [n+1]                                              */
+  const int32_t *col_idx;  /* device [nnz], sorted and unique per row, diagonal stored  */
+  const double *val;       /* device [2 nnz]: (re, im) of every entry                   */
+} pc_csr_z;
+
+/* pc_hermitian_real_form - the real form K of A into caller-owned device arrays: row_ptr
+ * [2n+1], col_idx [4 nnz], val [4 nnz] (FP64); real rows 2i and 2i+1 hold the real and the
+ * imaginary parts of complex row i, columns 2j and 2j+1 for complex column j.  Runs the CSR
+ * structure check first (synchronises the stream). */
+pc_status pc_hermitian_real_form(const pc_csr_z *A, int32_t *row_ptr, int32_t *col_idx, double *val,
+                                 void *stream);
+
+/* pcg_solve_z - block-Jacobi PCG for Hermitian PD A (complex block size 1..32; b, x device
+ * [2n] interleaved, x in = x0).  Builds K in library-owned device memory (freed before return)
+ * and runs pcg_solve on it with block size 2 * block_size; info as pcg_solve (failed_block is
+ * the complex block index, block_size the complex one). */
+pc_status pcg_solve_z(const pc_csr_z *A, int32_t block_size, const double *b, double *x, double tol,
+                      int32_t max_iter, int32_t prec, pc_solve_info *info, void *stream);
+
+/* kappa_estimate_z - Lanczos kappa of A (block_size 0) or of L^{-1} A L^{-H} (complex block size
+ * 1..32), v0 device [2n] interleaved; as kappa_estimate on K. */
+pc_status kappa_estimate_z(const pc_csr_z *A, int32_t block_size, int32_t max_steps, double tol,
+                           const double *v0, int32_t reorth, pc_kappa_info *info, void *stream);
+
+/* ---------------------------------------------------------------------------------
  * Batched mode: many independent SPD systems of uneven size, each with its own block
  * size.  Block-Jacobi setup (Sec. 3.2-3.3) and PCG to ||b_s - A_s x_s|| <= tol ||b_s||
  * (Sec. 3.7) for every system run inside ONE persistent cooperative kernel launch, which

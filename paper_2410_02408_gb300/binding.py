@@ -55,6 +55,11 @@ class pc_kappa_info(ctypes.Structure):
                 ("alpha", ctypes.c_void_p), ("beta", ctypes.c_void_p), ("elapsed_ms", ctypes.c_double)]
 
 
+class pc_csr_z(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("col_idx", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
 class pc_batch(ctypes.Structure):
     _fields_ = [("n_sys", ctypes.c_int32), ("n_rows", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("sys_row", ctypes.c_void_p), ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p),
@@ -90,6 +95,11 @@ def lib():
         "pc_dot": (_I32, [_I64, _P, _P, _P, _P]),
         "pc_debug_convert": (_I32, [_I64, _P, _P, _P, _P, _P]),
         "pc_debug_mma_tf32": (_I32, [_P, _P, _P, _P]),
+        "pc_hermitian_real_form": (_I32, [ctypes.POINTER(pc_csr_z), _P, _P, _P, _P]),
+        "pcg_solve_z": (_I32, [ctypes.POINTER(pc_csr_z), _I32, _P, _P, _D, _I32, _I32,
+                               ctypes.POINTER(pc_solve_info), _P]),
+        "kappa_estimate_z": (_I32, [ctypes.POINTER(pc_csr_z), _I32, _I32, _D, _P, _I32,
+                                    ctypes.POINTER(pc_kappa_info), _P]),
         "kappa_estimate": (_I32, [ctypes.POINTER(pc_csr), _I32, _I32, _D, _P, _I32,
                                   ctypes.POINTER(pc_kappa_info), _P]),
         "kappa_estimate_h": (_I32, [_P, ctypes.POINTER(pc_csr), _I32, _D, _P, _I32,
@@ -383,6 +393,87 @@ def debug_mma_tf32(a, b):
     d = torch.empty((16, 8), dtype=torch.float32, device="cuda")
     _check(lib().pc_debug_mma_tf32(_ptr(a), _ptr(b), _ptr(d), _stream()), "pc_debug_mma_tf32")
     return d
+
+
+@dataclass
+class CSRZ:
+    """Device complex CSR (torch CUDA tensors; values complex128) with its pc_csr_z descriptor."""
+
+    row_ptr: object
+    col: object
+    val: object
+
+    @property
+    def n(self) -> int:
+        return int(self.row_ptr.shape[0] - 1)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.shape[0])
+
+    def desc(self) -> pc_csr_z:
+        return pc_csr_z(self.n, self.nnz, _ptr(self.row_ptr), _ptr(self.col), _ptr(self.val))
+
+
+def csr_z(A) -> CSRZ:
+    """Complex CSR on the device from a host CSR whose values are complex."""
+    if isinstance(A, CSRZ):
+        return A
+    torch = _torch()
+    return CSRZ(_dev(np.asarray(A.row_ptr, dtype=np.int32), torch.int32),
+                _dev(np.asarray(A.col, dtype=np.int32), torch.int32),
+                _dev(np.asarray(A.val, dtype=np.complex128), torch.complex128))
+
+
+def _zvec(v):
+    torch = _torch()
+    return _dev(v, torch.complex128)
+
+
+def hermitian_real_form(A):
+    """The real form K of a complex Hermitian CSR (pc_hermitian_real_form): a device CSR."""
+    torch = _torch()
+    Z = csr_z(A)
+    rp = torch.empty(2 * Z.n + 1, dtype=torch.int32, device="cuda")
+    ci = torch.empty(max(4 * Z.nnz, 1), dtype=torch.int32, device="cuda")
+    va = torch.empty(max(4 * Z.nnz, 1), dtype=torch.float64, device="cuda")
+    d = Z.desc()
+    _check(lib().pc_hermitian_real_form(ctypes.byref(d), _ptr(rp), _ptr(ci), _ptr(va), _stream()),
+           "pc_hermitian_real_form")
+    return CSR(rp, ci[:4 * Z.nnz], va[:4 * Z.nnz])
+
+
+def pcg_z(A, b, block_size: int, tol: float = 1e-10, max_iter: int = 100000, prec: str = "fp64", x0=None,
+          check: bool = True):
+    """Block-Jacobi PCG for a complex Hermitian PD system (pcg_solve_z).  Returns (x complex, info)."""
+    Z = csr_z(A)
+    b = _zvec(b)
+    x = _torch().zeros_like(b) if x0 is None else _zvec(x0).clone()
+    info = pc_solve_info()
+    d = Z.desc()
+    st = lib().pcg_solve_z(ctypes.byref(d), int(block_size), _ptr(b), _ptr(x), float(tol), int(max_iter),
+                           PREC[prec], ctypes.byref(info), _stream())
+    if check:
+        _check(st, "pcg_solve_z")
+    return x, info.to_dict()
+
+
+def kappa_z(A, v0, block_size: int = 0, max_steps: int = 200, tol: float = 1e-12, reorth: bool = True):
+    """Lanczos kappa of a complex Hermitian PD matrix (kappa_estimate_z)."""
+    Z = csr_z(A)
+    v0 = _zvec(v0)
+    alpha = np.zeros(max_steps)
+    beta = np.zeros(max_steps)
+    info = pc_kappa_info()
+    info.alpha = alpha.ctypes.data
+    info.beta = beta.ctypes.data
+    d = Z.desc()
+    st = lib().kappa_estimate_z(ctypes.byref(d), int(block_size), int(max_steps), float(tol), _ptr(v0),
+                                int(bool(reorth)), ctypes.byref(info), _stream())
+    _check(st, "kappa_estimate_z")
+    k = info.steps
+    return {"kappa": info.kappa, "lambda_min": info.lambda_min, "lambda_max": info.lambda_max, "steps": k,
+            "alpha": alpha[:k].copy(), "beta": beta[:k].copy(), "ms": info.elapsed_ms}
 
 
 def dot(x, y) -> float:

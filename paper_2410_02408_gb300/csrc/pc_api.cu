@@ -41,7 +41,8 @@ struct pc_handle {
   void* graph;           // instantiated loop graph (pc::cg_graph_create)
   double* gbx;           // copies of b and x: 2 n
   int32_t* perm;         // SpMV row order for irregular row lengths (null: natural order)
-  int32_t* gsplit;       // with perm: each SpMV warp's first 32-row group (balanced runs)
+  int32_t* gsplit;       // with perm: each SpMV warp's first work item (balanced runs)
+  int32_t* items;        // with perm: work items (32-row groups, or single rows of hub-row groups)
   int32_t* gmax;         // with perm: longest row of each 32-row group
   int32_t* bnd;          // with perm: column-segment entry boundaries by binned position
   double* spart;         // with nseg > 1: partial sums between segment sweeps
@@ -247,6 +248,7 @@ pc_status pc_destroy(pc_handle* h) {
   dfree(h->gbx);
   dfree(h->perm);
   dfree(h->gsplit);
+  dfree(h->items);
   dfree(h->gmax);
   dfree(h->bnd);
   dfree(h->spart);
@@ -490,6 +492,8 @@ static bool bin_spmv_pipelined() {
 static void release_binning(pc_handle* h) {
   dfree(h->perm);
   dfree(h->gsplit);
+  dfree(h->items);
+  h->items = nullptr;
   dfree(h->gmax);
   dfree(h->bnd);
   dfree(h->spart);
@@ -520,21 +524,45 @@ static pc_status choose_row_order(pc_handle* h, cudaStream_t st) {
   }
   if (!bin) return PC_OK;
   h->bin_pipe = bin_spmv_pipelined() ? 1 : 0;
-  const int items = pc::cg_spmv_bin_warps(h->bin_pipe != 0);
+  const int n_warps = pc::cg_spmv_bin_warps(h->bin_pipe != 0);
   const int64_t stride = vec_stride(n);
+  const int64_t n_groups = (n + 31) / 32;
   int nseg = col_segments();
+  int64_t* gscr = nullptr;    // per group: whole-group cost, inclusive prefix of the item counts
   pc_status s = dalloc(&h->perm, sizeof(int32_t) * (size_t)n);
-  if (s == PC_OK) s = dalloc(&h->gsplit, sizeof(int32_t) * (size_t)(items + 1));
-  if (s == PC_OK) s = dalloc(&h->gmax, sizeof(int32_t) * (size_t)((n + 31) / 32));
+  if (s == PC_OK) s = dalloc(&h->gsplit, sizeof(int32_t) * (size_t)(n_warps + 1));
+  if (s == PC_OK) s = dalloc(&h->gmax, sizeof(int32_t) * (size_t)n_groups);
   if (s == PC_OK) s = dalloc(&h->bnd, sizeof(int32_t) * (size_t)(nseg + 1) * (size_t)stride);
   if (s == PC_OK && nseg > 1) s = dalloc(&h->spart, sizeof(double) * (size_t)stride);
+  if (s == PC_OK) s = dalloc(&gscr, sizeof(int64_t) * 2 * (size_t)n_groups);
+  if (s != PC_OK) {
+    dfree(gscr);
+    release_binning(h);
+    return s;
+  }
+  int64_t m_items = 0;
+  int64_t* icost = nullptr;
+  cudaError_t e = pc::row_bin_build(n, h->A.row_ptr, h->perm, st);
+  if (e == cudaSuccess) e = pc::row_bin_group_stats(n, h->A.row_ptr, h->perm, gscr, h->gmax, gscr + n_groups, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&m_items, gscr + 2 * n_groups - 1, sizeof(m_items), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && (m_items < n_groups || m_items > n)) e = cudaErrorInvalidValue;   // cannot happen
+  if (e == cudaSuccess) {
+    s = dalloc(&h->items, sizeof(int32_t) * (size_t)m_items);
+    if (s == PC_OK) s = dalloc(&icost, sizeof(int64_t) * (size_t)m_items);
+    if (s == PC_OK)
+      e = pc::row_bin_items(n, h->A.row_ptr, h->perm, h->gmax, gscr, gscr + n_groups, m_items, n_warps, h->items,
+                            icost, h->gsplit, st);
+    if (s == PC_OK && e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  dfree(icost);
+  dfree(gscr);
+  if (s == PC_OK && e != cudaSuccess) s = from_cuda(e);
   if (s != PC_OK) {
     release_binning(h);
     return s;
   }
-  PC_TRY(pc::row_bin_build(n, h->A.row_ptr, h->perm, st));
-  PC_TRY(pc::row_bin_split(n, h->A.row_ptr, h->perm, items, h->gsplit, h->gmax, reinterpret_cast<int64_t*>(h->tmp),
-                           st));
   // entry boundaries per binned position; segments need sorted columns, else whole rows
   int* d_unsorted = reinterpret_cast<int*>(h->tmp);   // after the split's use of the scratch
   int unsorted = 0;
@@ -573,6 +601,7 @@ static pc_status pcg_solve_graph(pc_handle* h, const double* b, double* x, doubl
     if (h->perm) {
       bin.perm = h->perm;
       bin.gsplit = h->gsplit;
+      bin.items = h->items;
       bin.gmax = h->gmax;
       bin.bnd = h->bnd;
       bin.bstride = vec_stride(n);

@@ -111,11 +111,12 @@ __device__ __forceinline__ double cg_row_range(const int32_t* __restrict__ ci, c
 // sharing the loop (warp-uniform); product slots past it are not issued.  The sum starts from
 // init (LPR = 1: the row's partial sum over earlier column segments, continued in entry order;
 // LPR > 1: 0) and for LPR > 1 is completed by an xor tree, valid in every lane of the group.
-// Called by full warps.
+// Called by full warps.  ps / pk: L2 policies of the matrix stream (evict first) and of the
+// gathers of x (evict last).
 template <typename VT, int LPR>
 __device__ __forceinline__ double cg_range_plain(const int32_t* __restrict__ ci, const VT* __restrict__ va,
                                                  const double* __restrict__ x, int32_t s, int32_t cnt, int32_t lim,
-                                                 double init) {
+                                                 double init, uint64_t ps, uint64_t pk) {
   const int j = LPR > 1 ? (int)(threadIdx.x & (LPR - 1)) : 0;
   const int32_t s0 = cnt > 0 ? s : 0;   // an empty range loads (and ignores) entry 0, which exists when lim > 0
   const int32_t kmax = max(cnt, 1) - 1;
@@ -126,12 +127,12 @@ __device__ __forceinline__ double cg_range_plain(const int32_t* __restrict__ ci,
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       const int32_t k = s0 + min(k0 + t * LPR + j, kmax);
-      c[t] = __ldg(ci + k);
-      v[t] = __ldg(va + k);
+      c[t] = ld_hint(ci + k, ps);
+      v[t] = ld_hint(va + k, ps);
     }
     double xv[8];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) xv[t] = __ldg(x + c[t]);
+    for (int t = 0; t < 8; ++t) xv[t] = ld_gather_hint(x + c[t], pk);
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       if (k0 + t * LPR < lim) {   // warp-uniform
@@ -152,11 +153,11 @@ __device__ __forceinline__ double cg_range_plain(const int32_t* __restrict__ ci,
 // lanes sharing the loop (warp-uniform); product slots past it are not issued.  The sum starts
 // from init (LPR = 1: the row's partial sum over earlier column segments, continued in entry
 // order; LPR > 1: 0) and for LPR > 1 is completed by an xor tree, valid in every lane of the
-// group.  Called by full warps.
+// group.  Called by full warps.  ps / pk: L2 policies as in cg_range_plain.
 template <typename VT, int LPR>
 __device__ __forceinline__ double cg_range_pipe(const int32_t* __restrict__ ci, const VT* __restrict__ va,
                                                 const double* __restrict__ x, int32_t s, int32_t cnt, int32_t lim,
-                                                double init) {
+                                                double init, uint64_t ps, uint64_t pk) {
   const int j = LPR > 1 ? (int)(threadIdx.x & (LPR - 1)) : 0;
   const int32_t s0 = cnt > 0 ? s : 0;   // an empty range loads (and ignores) entry 0, which exists when lim > 0
   const int32_t kmax = max(cnt, 1) - 1;
@@ -164,20 +165,20 @@ __device__ __forceinline__ double cg_range_pipe(const int32_t* __restrict__ ci, 
   if (lim > 0) {
     int32_t c[8];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) c[t] = __ldg(ci + s0 + min(t * LPR + j, kmax));
+    for (int t = 0; t < 8; ++t) c[t] = ld_hint(ci + s0 + min(t * LPR + j, kmax), ps);
     for (int32_t k0 = 0; k0 < lim; k0 += 8 * LPR) {
       double xv[8];
       VT v[8];
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
-        xv[t] = __ldg(x + c[t]);
-        v[t] = __ldg(va + s0 + min(k0 + t * LPR + j, kmax));
+        xv[t] = ld_gather_hint(x + c[t], pk);
+        v[t] = ld_hint(va + s0 + min(k0 + t * LPR + j, kmax), ps);
       }
       const int32_t k1 = k0 + 8 * LPR;
       int32_t cn[8];
       if (k1 < lim) {   // warp-uniform
 #pragma unroll
-        for (int t = 0; t < 8; ++t) cn[t] = __ldg(ci + s0 + min(k1 + t * LPR + j, kmax));
+        for (int t = 0; t < 8; ++t) cn[t] = ld_hint(ci + s0 + min(k1 + t * LPR + j, kmax), ps);
       }
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
@@ -216,9 +217,10 @@ struct CgArgs {
 // MODE 0 (I1): r = b - A x, sum b^2.  MODE 1 (A): q = A p, sum p q.  MODE 2 (T): r = b - A x, sum r^2.
 //
 // Natural order: a grid-stride loop over rows, one row per lane, warp-uniform trip counts
-// (rows past n are masked).  Binned order (BIN): each warp walks its own run of 32-row groups
-// of the permuted order (runs of about equal cost); the lanes per row follow the group's
-// longest row (1 up to 64 entries, 8 up to 256, else the whole warp).  With column segments
+// (rows past n are masked).  Binned order (BIN): each warp walks its own run of work items of
+// the permuted order (runs of about equal cost): a 32-row group, with one lane per row when its
+// longest row has up to 64 entries, else 8 lanes per row; or a single row of a group whose
+// longest row exceeds 256 entries, with the whole warp on it.  With column segments
 // (bin.nseg > 1) the warp sweeps its run once per segment, each sweep gathering only the part
 // of x that the segment covers, so the gathers of one sweep stay resident in L2 while the
 // matrix streams past; the partial sums between sweeps are kept per binned position.
@@ -232,9 +234,9 @@ constexpr int SPMV_BIN_PIPE_CTAS_PER_SM = 2;
 template <typename VT, int LPR, bool PIPE>
 __device__ __forceinline__ double cg_range(const int32_t* __restrict__ ci, const VT* __restrict__ va,
                                            const double* __restrict__ x, int32_t s, int32_t cnt, int32_t lim,
-                                           double init) {
-  if constexpr (PIPE) return cg_range_pipe<VT, LPR>(ci, va, x, s, cnt, lim, init);
-  else return cg_range_plain<VT, LPR>(ci, va, x, s, cnt, lim, init);
+                                           double init, uint64_t ps, uint64_t pk) {
+  if constexpr (PIPE) return cg_range_pipe<VT, LPR>(ci, va, x, s, cnt, lim, init, ps, pk);
+  else return cg_range_plain<VT, LPR>(ci, va, x, s, cnt, lim, init, ps, pk);
 }
 
 template <typename VT, int MODE, bool BIN, bool PIPE = false>
@@ -264,6 +266,7 @@ __device__ __forceinline__ void cg_spmv_body(const CgArgs& a, double* sm, int* i
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int32_t g0 = __ldg(B.gsplit + gw), g1 = __ldg(B.gsplit + gw + 1);
     const int nseg = B.nseg;
+    const uint64_t ps = l2_policy_evict_first(), pk = l2_policy_evict_last();
     for (int sg = 0; sg < nseg; ++sg) {
       const int32_t* lo_b = B.bnd + (int64_t)sg * B.bstride;
       const int32_t* hi_b = lo_b + B.bstride;
@@ -273,7 +276,21 @@ __device__ __forceinline__ void cg_spmv_body(const CgArgs& a, double* sm, int* i
         if (last) finish(__ldg(B.perm + pos), v_);
         else __stcg(B.spart + pos, v_);
       };
-      for (int32_t g = g0; g < g1; ++g) {
+      for (int32_t it = g0; it < g1; ++it) {
+        const int32_t item = __ldg(B.items + it);   // warp-uniform
+        if (item < 0) {
+          // one row of a group of hub rows: the whole warp on it
+          const int64_t pos = -(int64_t)item - 1;
+          const int32_t s = __ldg(lo_b + pos);
+          const int32_t cnt = __ldg(hi_b + pos) - s;
+          double v = cg_range<VT, 32, PIPE>(a.ci, va, X, s, cnt, cnt, 0.0, ps, pk);
+          if (lane == 0) {
+            if (!first) v += __ldcg(B.spart + pos);
+            done_pos(pos, v);
+          }
+          continue;
+        }
+        const int32_t g = item;
         const int64_t idx = (int64_t)g * 32 + lane;
         const bool valid = idx < n;
         const int32_t s0 = valid ? __ldg(lo_b + idx) : 0;
@@ -281,31 +298,19 @@ __device__ __forceinline__ void cg_spmv_body(const CgArgs& a, double* sm, int* i
         const int32_t gmax = __ldg(B.gmax + g);   // warp-uniform
         if (gmax <= 64) {
           const double init = (!first && valid) ? __ldcg(B.spart + idx) : 0.0;
-          const double v = cg_range<VT, 1, PIPE>(a.ci, va, X, s0, cnt0, __reduce_max_sync(FULL, cnt0), init);
+          const double v = cg_range<VT, 1, PIPE>(a.ci, va, X, s0, cnt0, __reduce_max_sync(FULL, cnt0), init, ps, pk);
           if (valid) done_pos(idx, v);
-        } else if (gmax <= 256) {
-          // 8 lanes per row, 4 rows per pass
+        } else {
+          // 8 lanes per row, 4 rows per pass (groups whose longest row has more than 256
+          // entries are split into single-row items when the items are built)
           for (int pp = 0; pp < 8; ++pp) {
             const int src = pp * 4 + (lane >> 3);
             const int32_t s = __shfl_sync(FULL, s0, src);
             const int32_t cnt = __shfl_sync(FULL, cnt0, src);
             const int vld = __shfl_sync(FULL, (int)valid, src);
-            double v = cg_range<VT, 8, PIPE>(a.ci, va, X, s, cnt, __reduce_max_sync(FULL, cnt), 0.0);
+            double v = cg_range<VT, 8, PIPE>(a.ci, va, X, s, cnt, __reduce_max_sync(FULL, cnt), 0.0, ps, pk);
             if ((lane & 7) == 0 && vld) {
               const int64_t pos = (int64_t)g * 32 + src;
-              if (!first) v += __ldcg(B.spart + pos);
-              done_pos(pos, v);
-            }
-          }
-        } else {
-          // the whole warp on one row at a time
-          for (int pp = 0; pp < 32; ++pp) {
-            const int32_t s = __shfl_sync(FULL, s0, pp);
-            const int32_t cnt = __shfl_sync(FULL, cnt0, pp);
-            const int vld = __shfl_sync(FULL, (int)valid, pp);
-            double v = cg_range<VT, 32, PIPE>(a.ci, va, X, s, cnt, cnt, 0.0);
-            if (lane == 0 && vld) {
-              const int64_t pos = (int64_t)g * 32 + pp;
               if (!first) v += __ldcg(B.spart + pos);
               done_pos(pos, v);
             }

@@ -100,6 +100,44 @@ __device__ __forceinline__ int32_t ld_stream(const int32_t* p) {
 // Read-only index data that is reused (row pointers): ordinary read-only path.
 __device__ __forceinline__ int32_t ld_ro(const int32_t* p) { return __ldg(p); }
 
+// L2 eviction priority of individual loads: a cache policy (createpolicy) attached to a
+// read-only load (ld.global.nc.L2::cache_hint).  The binned SpMV streams the matrix once per
+// launch with evict-first and gathers the vector with evict-last (and without L1 allocation), so
+// that the gathered vector stays in L2 while gigabytes of matrix pass through it.  Hints only:
+// no global state changes.
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ int32_t ld_hint(const int32_t* p, uint64_t pol) {
+  int32_t v;
+  asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ float ld_hint(const float* p, uint64_t pol) {
+  float v;
+  asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ double ld_hint(const double* p, uint64_t pol) {
+  double v;
+  asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+  return v;
+}
+// Gathers: no L1 allocation either, so that scattered vector reads do not evict the matrix lines
+// each lane reuses across its next rounds.
+__device__ __forceinline__ double ld_gather_hint(const double* p, uint64_t pol) {
+  double v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+  return v;
+}
+
 // Vectors written inside a persistent kernel: L2-coherent loads/stores (bypass L1).
 __device__ __forceinline__ double ld_vec(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ void st_vec(double* p, double v) { __stcg(p, v); }

@@ -172,7 +172,8 @@ size_t cg_scalars_bytes();
 // Binned SpMV order of the graph engine (built by pc_rowbin.cu).
 struct CgBinned {
   const int32_t* perm;     // [n] the row at each binned position
-  const int32_t* gsplit;   // [n_items + 1] each SpMV warp's run of 32-row groups
+  const int32_t* gsplit;   // [n_warps + 1] each SpMV warp's first work item (runs of about equal cost)
+  const int32_t* items;    // [m_items] work items: group g (>= 0) or the row at position -(v + 1)
   const int32_t* gmax;     // [ceil(n/32)] longest row of each group (selects the lanes per row)
   const int32_t* bnd;      // [(nseg + 1) * bstride] entry boundaries of the column segments, by position
   int64_t bstride;
@@ -192,11 +193,17 @@ constexpr int ROWBIN_W = 2048;
 cudaError_t row_bin_waste(int64_t n, const int32_t* rp, unsigned long long* d_out, cudaStream_t st);
 // perm[n]: the rows of every window, stably sorted by length bucket.
 cudaError_t row_bin_build(int64_t n, const int32_t* rp, int32_t* perm, cudaStream_t st);
-// gsplit[n_items+1]: contiguous runs of 32-row groups of the binned order with about equal
-// SpMV cost, one per warp of the binned SpMV grid; gmax[ceil(n/32)]: each group's longest row.
-// scratch: ceil(n/32) int64.
-cudaError_t row_bin_split(int64_t n, const int32_t* rp, const int32_t* perm, int n_items, int32_t* gsplit,
-                          int32_t* gmax, int64_t* scratch, cudaStream_t st);
+// Work items of the binned SpMV (see pc_rowbin.cu): whole 32-row groups, and the single rows of
+// groups whose longest row exceeds 256 entries.  Step 1: per group its longest row (gmax
+// [ceil(n/32)]), the cost of the whole-group item (gcost) and the inclusive prefix of the item
+// counts (gcount_incl, int64 [ceil(n/32)]; its last entry is the number of items).  Step 2: the
+// items (items [m_items]: g >= 0 for group g, -(pos + 1) for the row at binned position pos), their
+// cost prefix (icost, int64 [m_items]) and each warp's first item (isplit [n_warps + 1]).
+cudaError_t row_bin_group_stats(int64_t n, const int32_t* rp, const int32_t* perm, int64_t* gcost, int32_t* gmax,
+                                int64_t* gcount_incl, cudaStream_t st);
+cudaError_t row_bin_items(int64_t n, const int32_t* rp, const int32_t* perm, const int32_t* gmax, const int64_t* gcost,
+                          const int64_t* gcount_incl, int64_t m_items, int n_warps, int32_t* items, int64_t* icost,
+                          int32_t* isplit, cudaStream_t st);
 // Column segments of the binned SpMV: for the row at binned position idx, bnd[s * stride + idx]
 // is its first entry (s = 0), one past its last entry (s = nseg), or its first entry with
 // column >= s * seg_cols (0 < s < nseg; columns sorted within the row).  *unsorted (device

@@ -102,14 +102,28 @@ __global__ void __launch_bounds__(ROWBIN_THREADS) row_bin_kernel(int64_t n, cons
   }
 }
 
-// Cost of every 32-row group of the binned order for the SpMV: the larger of its FP64
-// lane-operations and its dependent memory rounds (a round = index/value loads then the
-// gathers) weighted by the 256 entries a warp of short rows handles per round.  Modes of
-// cg_spmv_kernel: one lane per row up to 64 entries (8 entries per lane and round); 8 lanes
-// per row up to 256 (64 entries per row and round, 4 rows at a time); else the whole warp
-// per row (256 entries per round).  Plus a per-group overhead.
-__global__ void group_cost_kernel(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ perm,
-                                  int64_t* __restrict__ cost, int32_t* __restrict__ gmax) {
+// Work items of the binned SpMV and their cost.  The SpMV is bound by each warp's chain of
+// dependent memory round trips (a round = the column indices and values, then the gathers of x
+// they address), so the cost of an item is the length of its chain, weighted by the 256 entries
+// a warp of short rows handles per round, or its FP64 lane-operations if that is larger, plus a
+// per-item overhead.  Item kinds, as the SpMV walks them:
+//   a 32-row group whose longest row has <= 64 entries: one lane per row, 8 entries per lane and
+//     round: 1 + 2 ceil(max/8) round trips (the bounds load, then two per round);
+//   a group whose longest row has <= 256 entries: 8 lanes per row, 4 rows per pass, 8 passes,
+//     each taking the rounds of its longest row (64 entries per round);
+//   a single row of a group whose longest row has more than 256 entries: the whole warp on that
+//     row, 256 entries per round.  Such groups are split into their rows so that no warp's chain
+//     is a whole group of hub rows.
+__device__ __forceinline__ int64_t item_cost(int64_t ops, int64_t trips) {
+  return (ops > 256 * trips ? ops : 256 * trips) + 256;
+}
+
+// Per 32-row group g of the binned order: gmax[g] = its longest row, gcount[g] = its number of
+// items (1, or its rows when the longest row exceeds 256 entries), gcost[g] = the cost of the
+// whole-group item (unused for split groups).
+__global__ void group_stats_kernel(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ perm,
+                                   int64_t* __restrict__ gcost, int32_t* __restrict__ gmax,
+                                   int64_t* __restrict__ gcount) {
   const int lane = threadIdx.x & 31;
   const int64_t n_groups = (n + 31) / 32;
   for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < n_groups;
@@ -122,22 +136,52 @@ __global__ void group_cost_kernel(int64_t n, const int32_t* __restrict__ rp, con
     }
     const int32_t m = __reduce_max_sync(FULL, len);
     const int32_t sum = __reduce_add_sync(FULL, len);
-    int64_t ops, rounds;
+    // longest row of each pass of 4 rows (lanes 4p .. 4p+3), in lane 4p
+    int32_t pm = max(len, __shfl_xor_sync(FULL, len, 1));
+    pm = max(pm, __shfl_xor_sync(FULL, pm, 2));
+    const int32_t pass_trips = __reduce_add_sync(FULL, (lane & 3) == 0 ? 2 * ((pm + 63) / 64) : 0);
+    int64_t ops, trips;
     if (m <= 64) {
       ops = 32ll * m;
-      rounds = (m + 7) / 8;
-    } else if (m <= 256) {
-      ops = (int64_t)sum + 32ll * 3;
-      // 8 passes of 4 rows; a pass takes the rounds of its longest row
-      const int32_t pmax = __reduce_max_sync(FULL, len);   // upper bound per pass
-      rounds = 8ll * ((pmax + 63) / 64);
+      trips = 1 + 2ll * ((m + 7) / 8);
     } else {
-      ops = (int64_t)sum + 32ll * 5;
-      rounds = __reduce_add_sync(FULL, (len + 255) / 256);
+      ops = (int64_t)sum + 32ll * 3;
+      trips = 1 + pass_trips;
     }
     if (lane == 0) {
-      cost[g] = (ops > 256 * rounds ? ops : 256 * rounds) + 256;
+      gcost[g] = item_cost(ops, trips);
       gmax[g] = m;
+      const int64_t rows = n - g * 32 < 32 ? n - g * 32 : 32;
+      gcount[g] = m > 256 ? rows : 1;
+    }
+  }
+}
+
+// Fill the items: for group g (first item incl[g] - count[g]), either the group itself (value g)
+// or each of its rows (value -(pos + 1), pos = its binned position) with the cost of a warp on
+// that row.
+__global__ void item_fill_kernel(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ perm,
+                                 const int32_t* __restrict__ gmax, const int64_t* __restrict__ gcost,
+                                 const int64_t* __restrict__ gcount_incl, int32_t* __restrict__ items,
+                                 int64_t* __restrict__ icost) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n_groups = (n + 31) / 32;
+  for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < n_groups;
+       g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t incl = __ldg(gcount_incl + g);
+    const int64_t first = g > 0 ? __ldg(gcount_incl + g - 1) : 0;
+    const int64_t cnt = incl - first;
+    if (__ldg(gmax + g) > 256) {
+      const int64_t pos = g * 32 + lane;
+      if (lane < cnt) {
+        const int32_t row = __ldg(perm + pos);
+        const int32_t len = __ldg(rp + row + 1) - __ldg(rp + row);
+        items[first + lane] = (int32_t)(-(pos + 1));
+        icost[first + lane] = item_cost((int64_t)len + 160, 1 + 2ll * ((len + 255) / 256));
+      }
+    } else if (lane == 0) {
+      items[first] = (int32_t)g;
+      icost[first] = __ldg(gcost + g);
     }
   }
 }
@@ -163,8 +207,8 @@ __global__ void __launch_bounds__(1024) cost_scan_kernel(int64_t m, int64_t* cos
   }
 }
 
-// gsplit[w] = first group of work item w: the first group whose inclusive prefix exceeds
-// w * total / n_items (so every item gets a contiguous run of about equal cost).
+// gsplit[w] = first item of warp w: the first item whose inclusive cost prefix exceeds
+// w * total / n_items (so every warp gets a contiguous run of about equal cost).
 __global__ void group_split_kernel(int64_t m, const int64_t* __restrict__ prefix, int n_items,
                                    int32_t* __restrict__ gsplit) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
@@ -184,15 +228,27 @@ __global__ void group_split_kernel(int64_t m, const int64_t* __restrict__ prefix
   gsplit[w] = (int32_t)(w == 0 ? 0 : lo);
 }
 
-cudaError_t row_bin_split(int64_t n, const int32_t* rp, const int32_t* perm, int n_items, int32_t* gsplit,
-                          int32_t* gmax, int64_t* scratch, cudaStream_t st) {
+static int64_t group_grid(int64_t n) {
   const int64_t m = (n + 31) / 32;
   int64_t grid = (m * 32 + 255) / 256;
   if (grid > (int64_t)device_sms() * 16) grid = (int64_t)device_sms() * 16;
-  if (grid < 1) grid = 1;
-  group_cost_kernel<<<(unsigned)grid, 256, 0, st>>>(n, rp, perm, scratch, gmax);
-  cost_scan_kernel<<<1, 1024, 0, st>>>(m, scratch);
-  group_split_kernel<<<(n_items + 1 + 255) / 256, 256, 0, st>>>(m, scratch, n_items, gsplit);
+  return grid < 1 ? 1 : grid;
+}
+
+cudaError_t row_bin_group_stats(int64_t n, const int32_t* rp, const int32_t* perm, int64_t* gcost, int32_t* gmax,
+                                int64_t* gcount_incl, cudaStream_t st) {
+  const int64_t m = (n + 31) / 32;
+  group_stats_kernel<<<(unsigned)group_grid(n), 256, 0, st>>>(n, rp, perm, gcost, gmax, gcount_incl);
+  cost_scan_kernel<<<1, 1024, 0, st>>>(m, gcount_incl);
+  return cudaGetLastError();
+}
+
+cudaError_t row_bin_items(int64_t n, const int32_t* rp, const int32_t* perm, const int32_t* gmax, const int64_t* gcost,
+                          const int64_t* gcount_incl, int64_t m_items, int n_warps, int32_t* items, int64_t* icost,
+                          int32_t* isplit, cudaStream_t st) {
+  item_fill_kernel<<<(unsigned)group_grid(n), 256, 0, st>>>(n, rp, perm, gmax, gcost, gcount_incl, items, icost);
+  cost_scan_kernel<<<1, 1024, 0, st>>>(m_items, icost);
+  group_split_kernel<<<(n_warps + 1 + 255) / 256, 256, 0, st>>>(m_items, icost, n_warps, isplit);
   return cudaGetLastError();
 }
 

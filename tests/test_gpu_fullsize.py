@@ -119,9 +119,11 @@ def test_batched_rgg_512(pc):
         assert res <= 1.0000001e-10, (s, res)
     # FP64 factors, sampled systems (smallest, mid-size and largest) against the oracle:
     # converged small systems by the oracle's solution at the same stopping rule; every sampled
-    # system by the iterate after the same number of iterations (the batch cut at 100
-    # iterations, the oracle run for exactly that many): near the stopping point a restart on
-    # one side only (the true residual just above tol) can change the iteration count.
+    # system by the iterate after the same number of iterations (the batch cut at 20 iterations,
+    # the oracle run for exactly that many).  Later iterates are not comparable on every system:
+    # on some of these graphs CG amplifies rounding differences (a 1e-15 relative change of b
+    # moves the oracle's own 100th iterate by 1.7e-4), and near the stopping point a restart on
+    # one side only can change the iteration count.
     x64, per64, info64 = pc.pcg_batched(batch, b, tol=1e-10, prec="fp64")
     assert info64["status_name"] == "ok"
     x64 = x64.cpu().numpy()
@@ -132,7 +134,7 @@ def test_batched_rgg_512(pc):
         sl = slice(int(batch.sys_row[s]), int(batch.sys_row[s + 1]))
         r = oracle.pcg(A, b[sl], int(batch.bs[s]), 1e-10)
         assert np.linalg.norm(x64[sl] - r["x"]) <= 1e-10 * np.linalg.norm(r["x"]), s
-    kcap = 100
+    kcap = 20
     xk, perk, infok = pc.pcg_batched(batch, b, tol=1e-10, max_iter=kcap, prec="fp64", check=False)
     xk = xk.cpu().numpy()
     for s in list(order[250:253]) + list(order[-3:]):

@@ -373,3 +373,17 @@ def test_fp32_breakdown_refactors_in_fp64(pc):
     with pytest.raises(pc.PcError) as ei:
         pc.setup(_pair_blocks(40, 1e-9, bad=7), 2, prec="fp32")
     assert ei.value.name == "not_spd"
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 7, 40])
+def test_iterate_after_k_steps_matches_oracle(pc, engine, k):
+    """x after exactly k CG steps (the solve cut by max_iter) equals the oracle's k-th iterate:
+    pins the order of the updates inside a step and the last step's x update."""
+    A = W.diffusion3d(14, 2.0)      # 2,744 rows: ragged warp units
+    b = W.rhs(A.n, 0)
+    x, info = pc.pcg(A, b, 8, tol=1e-14, max_iter=k, check=False)
+    assert info["status"] == 4 and info["iterations"] == k
+    r = oracle.pcg(A, b, 8, 0.0, max_iter=k, max_restarts=0)
+    assert r["iterations"] == k
+    xr = x.cpu().numpy()
+    assert np.linalg.norm(xr - r["x"]) <= 1e-12 * np.linalg.norm(r["x"])
