@@ -672,8 +672,7 @@ __global__ void __launch_bounds__(256) cg_precond_wp_kernel(const CgArgs a, cons
   constexpr int NSLOT = (BS > 0 && BS <= 32) ? 1 : 2;
   const int nslot = NSLOT == 1 ? 1 : L.S;
   const uint32_t fb = (uint32_t)(uM * (int64_t)sizeof(FT));
-  auto issue = [&](int64_t i) {   // lane 0: unit u0 + i into stage i % ns
-    const int st = (int)(i % pl.ns);
+  auto issue = [&](int64_t i, int st) {   // lane 0: unit u0 + i into stage st (= i mod ns)
     const int64_t u = u0 + i;
     const int64_t row0 = u * L.U;
     const int64_t rows = min((int64_t)L.U, L.n - row0);
@@ -687,13 +686,14 @@ __global__ void __launch_bounds__(256) cg_precond_wp_kernel(const CgArgs a, cons
   if (lane == 0) {
     for (int st = 0; st < pl.ns; ++st) mbar_init(&mbar[st], 1);
     mbar_fence_init();
-    for (int64_t i = 0; i < nu && i < pl.ns; ++i) issue(i);
+    for (int64_t i = 0; i < nu && i < pl.ns; ++i) issue(i, (int)i);
   }
   __syncwarp();
   double v0 = 0.0, v1 = 0.0;
+  // stage of unit i is i mod ns and its phase parity (i / ns) mod 2, kept as running counters
+  int st = 0;
+  uint32_t parity = 0u;
   for (int64_t i = 0; i < nu; ++i) {
-    const int st = (int)(i % pl.ns);
-    const uint32_t parity = (uint32_t)((i / pl.ns) & 1);
     const bool ok = mbar_wait_bounded(&mbar[st], parity, 4000000000LL);
     if (!__all_sync(FULL, ok)) {
       if (lane == 0) {
@@ -735,7 +735,11 @@ __global__ void __launch_bounds__(256) cg_precond_wp_kernel(const CgArgs a, cons
       v1 = fma(rv[t], rv[t], v1);
     }
     __syncwarp();   // every lane is done with the stage before it is refilled
-    if (lane == 0 && i + pl.ns < nu) issue(i + pl.ns);
+    if (lane == 0 && i + pl.ns < nu) issue(i + pl.ns, st);
+    if (++st == pl.ns) {
+      st = 0;
+      parity ^= 1u;
+    }
   }
   double v[2] = {v0, v1};
   if (!cg_last_cta<2>(v, a.part, &S->cnt[1], sm, &is_last)) return;
