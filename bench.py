@@ -486,7 +486,8 @@ def kernel_table(n, nnz, vb, bs, prec, spmv_us, prec_us, upd_us, peak, peak_kind
                     "frac": gbs(prec_bytes, prec_us) / peak},
         "update": {"us": upd_us, "GBs": gbs(upd_bytes, upd_us), "bytes": upd_bytes,
                    "frac": gbs(upd_bytes, upd_us) / peak},
-        "note": "profiling-mode launches (events around each kernel), includes per-launch overhead",
+        "note": "profiling mode: kernels launched one by one with CUDA events around each; every step "
+                "starts with a 40 us spacer kernel so that the intervals exclude host launch latency",
     }
     return roofline, kernels
 

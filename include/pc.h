@@ -43,7 +43,9 @@
  *   PC_BIN_SPMV=pipe|plain          row loop of the binned CG SpMV, read when a handle first
  *                                   solves: pipelined (default, 2 CTAs per SM) or plain (4).
  *   PC_CG_PROFILE=1                 graph engine: launch the loop body kernels one by one with
- *                                   events around each (per-kernel times, pc_get_trace).
+ *                                   events around each (per-kernel times, pc_get_trace); every
+ *                                   step starts with a 40 us spacer kernel so that the event
+ *                                   intervals exclude the host's launch latency.
  *   PC_TRACE_BARRIERS=N             persistent engine: record N barrier timestamps.
  *   PC_BATCH_PROFILE=1              batched mode: per-phase device timers (pc_batch_profile).
  */

@@ -1045,8 +1045,18 @@ cudaError_t cg_graph_round(void* h, bool val_f32, bool fac_f32, cudaStream_t st)
   return cudaGetLastError();
 }
 
+// Keeps the GPU busy for about ns nanoseconds (a bounded sleep on the global timer), so that
+// the launches the host enqueues meanwhile are waiting in the stream when it ends.
+__global__ void cg_spacer_kernel(unsigned long long ns) {
+  const unsigned long long t0 = globaltimer_ns();
+  for (int i = 0; i < 100000 && globaltimer_ns() - t0 < ns; ++i) __nanosleep(500);
+}
+
 // Profiling round: the loop body kernels are launched one by one from the host with CUDA
-// events around each (per-kernel times accumulate into ms[3]); same kernels and results.
+// events around each (per-kernel times accumulate into ms[3]); same kernels and results.  The
+// host reads the loop condition after every step, so each step starts with a 40 us spacer
+// kernel: by the time it ends, the step's events and kernels are all enqueued, and the first
+// kernel's event interval does not contain the host's launch latency.
 template <typename VT, typename FT, int BS>
 static cudaError_t eager_round_t(CgGraph* g, cudaStream_t st, double* ms, int* iters) {
   CgGraph eg = *g;
@@ -1058,6 +1068,7 @@ static cudaError_t eager_round_t(CgGraph* g, cudaStream_t st, double* ms, int* i
   if (e == cudaSuccess) e = cudaMemcpyAsync(&cont, &eg.args.s->cont, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   while (e == cudaSuccess && cont) {
+    cg_spacer_kernel<<<1, 32, 0, st>>>(40000ull);
     cudaEventRecord(ev[0], st);
     launch_spmv_mode<VT, 1>(eg.g_spmv, st, eg.args);
     cudaEventRecord(ev[1], st);
