@@ -13,9 +13,10 @@
 // with max_iter and breakdown checks in the order the iteration meets them.  The host
 // restarts from x (at most 3 times) when the true residual is above tol.
 //
-// Kernels are separate launches so each runs at full occupancy with its own register budget:
-// the SpMV streams the CSR with ordinary L1-allocating loads (neighbouring rows share the
-// cache lines of the column/value arrays) and keeps 8 gathers in flight per row.
+// Kernels are separate launches so each runs with its own register budget: the SpMV streams
+// the CSR with ordinary L1-allocating loads (neighbouring rows share the cache lines of the
+// column/value arrays), keeps 8 gathers in flight per row and pipelines each thread's rows
+// (its time is set by the memory round trips in flight, not by its FP64 products).
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -69,40 +70,6 @@ __device__ __forceinline__ bool cg_last_cta(double* v, double* part, unsigned* c
   for (int i = 0; i < NV; ++i) v[i] = acc[i];
   if (threadIdx.x == 0) *counter = 0u;
   return true;
-}
-
-// SpMV row with 8 loads in flight, L1-allocating CSR loads (x may have been written by the
-// previous kernel: kernel boundaries make it visible).  Called by full warps (rows past n
-// have an empty range): the entry count is made warp-uniform so a product slot is issued
-// only if some lane needs it (a fully masked FP64 instruction still costs FP64-pipe time),
-// and float values are widened on the integer pipe.
-template <typename VT>
-__device__ __forceinline__ double cg_row_range(const int32_t* __restrict__ ci, const VT* __restrict__ va,
-                                               const double* __restrict__ x, int32_t s, int32_t cnt, int32_t wmax) {
-  const int32_t s0 = cnt > 0 ? s : 0;   // an empty row loads (and ignores) entry 0, which exists when wmax > 0
-  double acc = 0.0;
-  for (int32_t k0 = 0; k0 < wmax; k0 += 8) {
-    int32_t c[8];
-    VT v[8];
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      const int32_t k = s0 + min(k0 + t, max(cnt, 1) - 1);
-      c[t] = __ldg(ci + k);
-      v[t] = __ldg(va + k);
-    }
-    double xv[8];
-#pragma unroll
-    for (int t = 0; t < 8; ++t) xv[t] = __ldg(x + c[t]);
-    const int rem = wmax - k0;   // warp-uniform
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      if (t < rem) {
-        const double pr = fma(from_ft(v[t]), xv[t], acc);
-        acc = (k0 + t < cnt) ? pr : acc;
-      }
-    }
-  }
-  return acc;
 }
 
 // Binned SpMV row work, one load phase after the other: one row per group of LPR lanes
@@ -239,6 +206,91 @@ __device__ __forceinline__ double cg_range(const int32_t* __restrict__ ci, const
   else return cg_range_plain<VT, LPR>(ci, va, x, s, cnt, lim, init, ps, pk);
 }
 
+// Natural row order: each thread walks rows base + tid, base + S + tid, ... (S = threads in the
+// grid), software-pipelined over them: the row pointers two rows ahead and the column indices
+// one row ahead are in flight while the current row's values, its gathers of x and its own
+// entry of w (the vector the caller's epilogue needs: p or b) are loaded, so a row costs about
+// one dependent memory round trip instead of three.  The first 8 entries of a row go through
+// the pipeline, further entries (rare in the natural order, which serves short uniform rows)
+// take plain rounds.  Each row is one FMA chain over its entries in storage order (the order
+// of the oracle's sum), with float values widened on the integer pipe.  Rows past n are masked (empty
+// ranges).  Called by whole CTAs; fin(row, sum, w_row) runs for the rows below n.
+template <typename VT, typename FIN>
+__device__ __forceinline__ void cg_rows_pipe(const CgArgs& a, const VT* __restrict__ va, const double* __restrict__ x,
+                                             const double* __restrict__ w, FIN fin) {
+  const int64_t n = a.lay.n;
+  const int64_t S = (int64_t)gridDim.x * blockDim.x;
+  const int32_t* __restrict__ ci = a.ci;
+  int64_t base = (int64_t)blockIdx.x * blockDim.x;
+  if (base >= n) return;
+  auto row_range = [&](int64_t b, int32_t& s, int32_t& e) {
+    const int64_t r = b + threadIdx.x;
+    s = 0;
+    e = 0;
+    if (r < n) {
+      s = __ldg(a.rp + r);
+      e = __ldg(a.rp + r + 1);
+    }
+  };
+  // entry slot t of a row: an empty row reads (and ignores) entry 0, which exists for n > 0
+  auto slot = [](int32_t s, int32_t cnt, int t) { return (cnt > 0 ? s : 0) + min(t, max(cnt, 1) - 1); };
+  int32_t s0, e0, s1, e1;
+  row_range(base, s0, e0);
+  row_range(base + S, s1, e1);
+  int32_t c[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) c[t] = __ldg(ci + slot(s0, e0 - s0, t));
+  for (; base < n; base += S) {
+    const int64_t row = base + threadIdx.x;
+    const bool valid = row < n;
+    const int32_t cnt = e0 - s0;
+    const int32_t wmax = __reduce_max_sync(FULL, cnt);   // warp-uniform
+    VT v[8];
+    double xv[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      v[t] = __ldg(va + slot(s0, cnt, t));
+      xv[t] = __ldg(x + c[t]);
+    }
+    const double wr = valid ? __ldg(w + row) : 0.0;
+    int32_t s2, e2;
+    row_range(base + 2 * S, s2, e2);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) c[t] = __ldg(ci + slot(s1, e1 - s1, t));
+    double sum = 0.0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      if (t < wmax) {   // a fully masked FP64 instruction still costs FP64-pipe time
+        const double pr = fma(from_ft(v[t]), xv[t], sum);
+        sum = t < cnt ? pr : sum;
+      }
+    }
+    for (int32_t k0 = 8; k0 < wmax; k0 += 8) {
+      int32_t cc[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int32_t k = slot(s0, cnt, k0 + t);
+        cc[t] = __ldg(ci + k);
+        v[t] = __ldg(va + k);
+      }
+#pragma unroll
+      for (int t = 0; t < 8; ++t) xv[t] = __ldg(x + cc[t]);
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        if (k0 + t < wmax) {
+          const double pr = fma(from_ft(v[t]), xv[t], sum);
+          sum = k0 + t < cnt ? pr : sum;
+        }
+      }
+    }
+    if (valid) fin(row, sum, wr);
+    s0 = s1;
+    e0 = e1;
+    s1 = s2;
+    e1 = e2;
+  }
+}
+
 template <typename VT, int MODE, bool BIN, bool PIPE = false>
 __device__ __forceinline__ void cg_spmv_body(const CgArgs& a, double* sm, int* is_last_p) {
   int& is_last = *is_last_p;
@@ -319,14 +371,17 @@ __device__ __forceinline__ void cg_spmv_body(const CgArgs& a, double* sm, int* i
       }
     }
   } else {
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
-      const int64_t row = base + threadIdx.x;
-      const bool valid = row < n;
-      const int32_t s0 = valid ? __ldg(a.rp + row) : 0;
-      const int32_t cnt0 = valid ? __ldg(a.rp + row + 1) - s0 : 0;
-      const double v = cg_row_range<VT>(a.ci, va, X, s0, cnt0, __reduce_max_sync(FULL, cnt0));
-      if (valid) finish(row, v);
-    }
+    // the epilogue's vector entry (p_i, or b_i) is loaded with the row's values
+    cg_rows_pipe<VT>(a, va, X, MODE == 1 ? a.p : a.b, [&](int64_t r_, double v_, double w_) {
+      if (MODE == 1) {
+        a.q[r_] = v_;
+        acc = fma(w_, v_, acc);
+      } else {
+        const double ri = w_ - v_;
+        a.r[r_] = ri;
+        acc = MODE == 0 ? fma(w_, w_, acc) : fma(ri, ri, acc);
+      }
+    });
   }
   double v[1] = {acc};
   if (!cg_last_cta<1>(v, a.part, &S->cnt[MODE == 2 ? 2 : 0], sm, &is_last)) return;
@@ -351,8 +406,11 @@ __device__ __forceinline__ void cg_spmv_body(const CgArgs& a, double* sm, int* i
   }
 }
 
+// Natural order.  The pipelined row walk keeps two rows' loads live: up to 64 registers, 4 CTAs
+// per SM (the grid is capped there too: fewer, longer thread walks measured faster than a full
+// 8 CTAs per SM).
 template <typename VT, int MODE>
-__global__ void __launch_bounds__(256) cg_spmv_kernel(const CgArgs a) {
+__global__ void __launch_bounds__(256, 4) cg_spmv_kernel(const CgArgs a) {
   __shared__ double sm[32];
   __shared__ int is_last;
   cg_spmv_body<VT, MODE, false>(a, sm, &is_last);
@@ -906,7 +964,8 @@ static int sms_now() {
 int cg_graph_partials() { return sms_now() * 16 * 2 + 64; }
 
 // Resident CTAs per SM of the natural-order SpMV (its grid is one wave: the grid-stride loop
-// gives every CTA the same share of rows).
+// gives every CTA the same share of rows), at most SPMV_NAT_CTAS_PER_SM.
+constexpr int SPMV_NAT_CTAS_PER_SM = 4;
 static int spmv_ctas_per_sm(bool val_f32) {
   int occ = 0;
   const cudaError_t e =
@@ -916,7 +975,7 @@ static int spmv_ctas_per_sm(bool val_f32) {
     cudaGetLastError();
     return 8;
   }
-  return occ < 1 ? 1 : occ > 8 ? 8 : occ;
+  return occ < 1 ? 1 : occ > SPMV_NAT_CTAS_PER_SM ? SPMV_NAT_CTAS_PER_SM : occ;
 }
 
 size_t cg_scalars_bytes() { return sizeof(CgScalars); }
