@@ -97,7 +97,8 @@ def parse(argv=None):
     ap.add_argument("--col-segments", default="auto",
                     help="column segments of the binned SpMV: auto (the library default, 1) or 1..8")
     ap.add_argument("--n-sys", type=int, default=512, help="systems in the batched workload")
-    ap.add_argument("--no-tune", action="store_true", help="batched workload: skip the launch-shape autotuner")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the launch-shape autotuners (single-system loop kernels; batched launch)")
     ap.add_argument("--tune-trials", type=int, default=0, help="batched autotuner candidates (0 = all)")
     ap.add_argument("--batch-shape", default="",
                     help="batched workload: explicit launch shape 'ctas_per_sm,team_max,slots_per_cta,setup_kb' "
@@ -515,6 +516,19 @@ def run_ours(args):
     n, nnz = A.n, A.nnz
     st = torch.cuda.current_stream()
 
+    # launch shapes of the CG loop kernels, picked by the library's autotuner for each block
+    # size and precision timed below (outside every timed region)
+    shapes = {}
+
+    def tuned(bsz, prec):
+        if not args.no_tune and (bsz, prec) not in shapes:
+            shapes[(bsz, prec)] = pc.autotune(Ad, bsz, prec, iterations=50)
+        return shapes.get((bsz, prec))
+
+    tuned(args.bs, args.prec)
+    if not args.no_fp64_compare:
+        tuned(args.bs, "fp64")
+
     for _ in range(args.warmup):
         x, info = pc.pcg(Ad, bd, args.bs, tol=args.tol, max_iter=args.maxit, prec=args.prec)
     torch.cuda.synchronize()
@@ -571,6 +585,7 @@ def run_ours(args):
         "roofline": roofline,
         "kernels": kernels,
         "spmv_order": spmv_order,
+        "launch_shapes": {f"bs{k[0]}_{k[1]}": v for k, v in shapes.items()} or "library defaults (--no-tune)",
         "gpu_launches": launches,
     }
     line["clocks"] = clk.summary()
@@ -595,6 +610,7 @@ def run_ours(args):
         for bsz in (8, 16, 32, 64):
             row = {}
             for prec in ("fp32", "tf32", "fp64"):
+                tuned(bsz, prec)
                 _, si, sms = timed_solves(pc, Ad, bd, bsz, prec, args, 1, 1)
                 si = si[-1]
                 sb = step_bytes(n, nnz, bsz, prec, si["iterations"], vb)[0]
@@ -1074,6 +1090,8 @@ def powerlaw_result(pc, args, steps, warmup):
     bd = torch.from_numpy(b).cuda()
     n, nnz, vb = A.n, A.nnz, A.val.dtype.itemsize
     peak, peak_kind = measured_hbm()
+    # launch shapes of the loop kernels (binned row loop, ring depth) from the autotuner
+    shapes = {} if args.no_tune else {p: pc.autotune(Ad, bs, p, iterations=30) for p in (args.prec, "fp64")}
     with ClockSampler(0) as clk:
         x, infos, ms_total = timed_solves(pc, Ad, bd, bs, args.prec, args, steps, warmup)
     ms = ms_total / steps
@@ -1094,6 +1112,7 @@ def powerlaw_result(pc, args, steps, warmup):
            "setup_ms": statistics.mean(i["setup_ms"] for i in infos),
            "solve_ms": statistics.mean(i["solve_ms"] for i in infos),
            "frac_of_hbm_peak": value / peak, "roofline": roofline, "kernels": kernels, "spmv_order": order,
+           "launch_shapes": shapes or "library defaults (--no-tune)",
            "generation_s": gen_s,
            "gpu_launches": sum(2 + 6 + 4 * (i["restarts"] + 1) + 3 * i["iterations"] for i in infos)}
     res["clocks"] = clk.summary()

@@ -494,6 +494,57 @@ void pc_set_col_segments(int32_t segs);
 /* Column segments of the handle's binned CG SpMV (1 if unsegmented or not binned). */
 int32_t pc_handle_col_segments(const pc_handle *h);
 
+/* Launch shape of the graph engine's CG loop kernels (the paper fixes none; these are
+ * implementation choices that change speed, and results only through the order of the
+ * per-CTA partial sums).  0 in a field: the library default. */
+typedef struct {
+  int32_t spmv_ctas_per_sm;   /* natural-order SpMV: resident CTAs per SM, 1..8 (default 4)  */
+  int32_t ring_stages;        /* warp-ring preconditioner: stages per warp, 2..4 (default:
+                                 the deepest that fits 110 KB of shared memory per CTA)       */
+  int32_t bin_pipe;           /* binned SpMV row loop: -1 default (pipelined), 0 plain,
+                                 1 pipelined                                                  */
+  int32_t reserved;
+  double us_per_iteration;    /* time per CG iteration measured for this shape (0: none)     */
+} pc_shape;
+
+/* pc_autotune - kernel-shape autotuner of the single-system solve.  Sets up a handle for A
+ * (block_size, prec), then for each candidate shape (natural row order: SpMV CTAs per SM
+ * {2, 3, 4, 6, 8} x ring stages {2, 3, 4}; binned: row loop {plain, pipelined} x ring stages)
+ * runs `iterations` CG iterations twice (right-hand side of ones, tolerance 0) and times the
+ * second run with CUDA events; max_trials > 0 caps the candidates.  The fastest shape is
+ * recorded for A's key (block size, precision, ceil(log2 n), round(log2(nnz / n)), SM count
+ * of the current device); handles with that key use it when they build their loop graph (at
+ * their first solve), and when the environment variable PC_TUNE_CACHE names a file it is
+ * saved there.  best (HOST, may be NULL) receives the shape with its time per iteration.
+ * Allocates and frees its own buffers; synchronises the stream.  1 <= iterations <= 10000. */
+pc_status pc_autotune(const pc_csr *A, int32_t block_size, int32_t prec, int32_t iterations,
+                      int32_t max_trials, void *stream, pc_shape *best);
+
+/* Records (pc_tune_set) or looks up (pc_tune_get: 1 if found, 0 if not) the shape for the key
+ * of a system with n rows, nnz entries, this block size and precision on the current device.
+ * Host-only (no device work; with no device the SM count of the key is 0).  pc_tune_set
+ * returns PC_ERR_INVALID_ARG for a field outside its range. */
+pc_status pc_tune_set(int32_t block_size, int32_t prec, int64_t n, int64_t nnz, const pc_shape *shape);
+int32_t pc_tune_get(int32_t block_size, int32_t prec, int64_t n, int64_t nnz, pc_shape *shape);
+
+/* Forgets every recorded shape, single-system and batched (a file named by PC_TUNE_CACHE is
+ * not read again until pc_tune_load). */
+void pc_tune_clear(void);
+
+/* Cache file of the recorded shapes: one flat JSON object per line, "kind" "cg" (the key and
+ * pc_shape fields) or "batch" (the batch signature of pc_batch_autotune and its launch
+ * shape).  pc_tune_save writes every recorded shape (through a temporary file renamed into
+ * place); pc_tune_load merges a file into the table, skipping lines that do not parse, and
+ * reports the entries taken in *entries (HOST, may be NULL).  PC_ERR_INVALID_ARG when the
+ * file cannot be written or opened.  The file named by PC_TUNE_CACHE is loaded once per
+ * process at the first lookup.  Host-only. */
+pc_status pc_tune_save(const char *path);
+pc_status pc_tune_load(const char *path, int32_t *entries);
+
+/* The launch shape h's loop graph was built with (after its first solve with the graph engine;
+ * PC_ERR_INVALID_ARG before).  us_per_iteration is that of the recorded shape, if any. */
+pc_status pc_handle_shape(const pc_handle *h, pc_shape *out);
+
 /* Phase trace of the last pcg_solve_h on h, when the environment variable
  * PC_TRACE_BARRIERS=N (N > 0) was set for that solve: out[0] is the device globaltimer (ns)
  * at kernel start and out[k] the time after the k-th grid-wide synchronisation (entries

@@ -12,7 +12,8 @@ _BINDING_NAMES = ("setup", "apply", "kappa", "pcg", "spmv", "dot", "extract_bloc
                   "csr_check", "debug_convert", "debug_mma_tf32", "csr_z", "CSRZ", "pcg_z", "kappa_z",
                   "hermitian_real_form", "pcg_batched", "Batch", "batch_schedule", "batch_set_tuning", "batch_autotune",
                   "grad_val", "grad_edges", "status_string", "PcError", "set_wait_budget", "set_ctas_per_sm",
-                  "set_cg_engine", "set_row_binning", "set_col_segments")
+                  "set_cg_engine", "set_row_binning", "set_col_segments", "autotune", "tune_set", "tune_get",
+                  "tune_clear", "tune_save", "tune_load")
 
 
 def load():

@@ -49,6 +49,23 @@ class pc_solve_info(ctypes.Structure):
         return d
 
 
+class pc_shape(ctypes.Structure):
+    _fields_ = [("spmv_ctas_per_sm", ctypes.c_int32), ("ring_stages", ctypes.c_int32), ("bin_pipe", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("us_per_iteration", ctypes.c_double)]
+
+    def to_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+    @classmethod
+    def from_dict(cls, d):
+        s = cls()
+        s.spmv_ctas_per_sm = int(d.get("spmv_ctas_per_sm", 0))
+        s.ring_stages = int(d.get("ring_stages", 0))
+        s.bin_pipe = int(d.get("bin_pipe", -1))
+        s.us_per_iteration = float(d.get("us_per_iteration", 0.0))
+        return s
+
+
 class pc_kappa_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("steps", ctypes.c_int32), ("kappa", ctypes.c_double),
                 ("lambda_min", ctypes.c_double), ("lambda_max", ctypes.c_double),
@@ -131,6 +148,13 @@ def lib():
         "pc_handle_col_segments": (_I32, [_P]),
         "pc_handle_refactored_fp64": (_I32, [_P]),
         "pc_handle_row_binned": (_I32, [_P]),
+        "pc_autotune": (_I32, [ctypes.POINTER(pc_csr), _I32, _I32, _I32, _I32, _P, ctypes.POINTER(pc_shape)]),
+        "pc_tune_set": (_I32, [_I32, _I32, _I64, _I64, ctypes.POINTER(pc_shape)]),
+        "pc_tune_get": (_I32, [_I32, _I32, _I64, _I64, ctypes.POINTER(pc_shape)]),
+        "pc_tune_clear": (None, []),
+        "pc_tune_save": (_I32, [ctypes.c_char_p]),
+        "pc_tune_load": (_I32, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32)]),
+        "pc_handle_shape": (_I32, [_P, ctypes.POINTER(pc_shape)]),
         "pc_status_string": (ctypes.c_char_p, [_I32]),
         "pc_version": (_I32, []),
     }
@@ -281,6 +305,12 @@ class Handle:
     def col_segments(self) -> int:
         """Column segments swept by this handle's binned CG SpMV (1: whole rows)."""
         return int(lib().pc_handle_col_segments(self._h))
+
+    def shape(self) -> dict:
+        """Launch shape of this handle's loop graph (after its first graph-engine solve)."""
+        out = pc_shape()
+        _check(lib().pc_handle_shape(self._h, ctypes.byref(out)), "pc_handle_shape")
+        return out.to_dict()
 
     def trace(self, max_entries: int = 4096) -> np.ndarray:
         """Barrier timestamps (ns) of the last solve when PC_TRACE_BARRIERS was set."""
@@ -656,6 +686,45 @@ def set_ctas_per_sm(ctas: int):
 def set_row_binning(mode: str):
     """"auto" (default), "off" or "on": row order of the CG SpMV (see pc_set_row_binning)."""
     lib().pc_set_row_binning({"off": 0, "on": 1}.get(mode, -1))
+
+
+def autotune(A, block_size: int, prec: str = "fp32", iterations: int = 100, max_trials: int = 0) -> dict:
+    """Kernel-shape autotuner of the single-system solve (pc_autotune): times the candidate
+    launch shapes on `iterations` CG iterations of A and records the fastest for A's key.
+    Returns that shape as a dict."""
+    A = _as_csr(A)
+    d = A.desc()
+    out = pc_shape()
+    _check(lib().pc_autotune(ctypes.byref(d), int(block_size), PREC[prec], int(iterations), int(max_trials),
+                             _stream(), ctypes.byref(out)), "pc_autotune")
+    return out.to_dict()
+
+
+def tune_set(block_size: int, prec: str, n: int, nnz: int, shape: dict):
+    """Records a launch shape for the key of an n-row, nnz-entry system (pc_tune_set)."""
+    _check(lib().pc_tune_set(int(block_size), PREC[prec], int(n), int(nnz), ctypes.byref(pc_shape.from_dict(shape))),
+           "pc_tune_set")
+
+
+def tune_get(block_size: int, prec: str, n: int, nnz: int):
+    """The recorded launch shape for that key as a dict, or None (pc_tune_get)."""
+    out = pc_shape()
+    return out.to_dict() if lib().pc_tune_get(int(block_size), PREC[prec], int(n), int(nnz), ctypes.byref(out)) else None
+
+
+def tune_clear():
+    lib().pc_tune_clear()
+
+
+def tune_save(path: str):
+    _check(lib().pc_tune_save(os.fsencode(path)), "pc_tune_save")
+
+
+def tune_load(path: str) -> int:
+    """Merges a cache file into the table; returns the entries taken (pc_tune_load)."""
+    n = ctypes.c_int32(0)
+    _check(lib().pc_tune_load(os.fsencode(path), ctypes.byref(n)), "pc_tune_load")
+    return int(n.value)
 
 
 def set_col_segments(segs):

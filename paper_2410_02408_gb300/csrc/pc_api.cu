@@ -6,11 +6,13 @@
 #include <string.h>
 
 #include <mutex>
+#include <vector>
 
 #include <nvtx3/nvToolsExt.h>
 
 #include "pc.h"
 #include "pc_kernels.cuh"
+#include "pc_tune.h"
 
 using pc::Layout;
 
@@ -53,6 +55,10 @@ struct pc_handle {
   void* gscal;           // CG scalars
   int64_t prof_ns[3];    // graph engine, profiling mode: mean ns per iteration of the 3 kernels
   int prof_valid;
+  // launch shape of the loop graph: forced (autotuner trials), else the tuned table, else defaults
+  int shape_forced;
+  pc_shape shape_force;
+  pc_shape shape_used;   // valid once the graph exists
 };
 
 namespace {
@@ -482,10 +488,12 @@ static int col_segments() { return g_col_segments >= 1 ? g_col_segments : 1; }
 // SpMV, so it is the default; PC_BIN_SPMV=pipe|plain overrides it.
 constexpr bool kBinPipeDefault = true;
 
-static bool bin_spmv_pipelined() {
+// PC_BIN_SPMV first, then the handle's launch shape (bin_pipe 0 / 1), then the default.
+static bool bin_spmv_pipelined(int shape_pipe) {
   const char* e = getenv("PC_BIN_SPMV");
   if (e && strcmp(e, "pipe") == 0) return true;
   if (e && strcmp(e, "plain") == 0) return false;
+  if (shape_pipe == 0 || shape_pipe == 1) return shape_pipe == 1;
   return kBinPipeDefault;
 }
 
@@ -523,7 +531,7 @@ static pc_status choose_row_order(pc_handle* h, cudaStream_t st) {
     bin = (double)waste > 1.25 * (double)h->A.nnz;
   }
   if (!bin) return PC_OK;
-  h->bin_pipe = bin_spmv_pipelined() ? 1 : 0;
+  h->bin_pipe = bin_spmv_pipelined(h->shape_used.bin_pipe) ? 1 : 0;
   const int n_warps = pc::cg_spmv_bin_warps(h->bin_pipe != 0);
   const int64_t stride = vec_stride(n);
   const int64_t n_groups = (n + 31) / 32;
@@ -592,6 +600,15 @@ static pc_status pcg_solve_graph(pc_handle* h, const double* b, double* x, doubl
   if (s == PC_OK && !h->gscal) s = dalloc(&h->gscal, pc::cg_scalars_bytes());
   if (s != PC_OK) return s;
   if (!h->graph) {
+    // the launch shape: forced, else recorded for this system's key, else the defaults
+    memset(&h->shape_used, 0, sizeof(h->shape_used));
+    h->shape_used.bin_pipe = -1;
+    if (h->shape_forced) {
+      h->shape_used = h->shape_force;
+    } else {
+      pc_shape t;
+      if (pc::tune_lookup(pc::tune_key(h->bs, h->prec, h->A.n, h->A.nnz), &t)) h->shape_used = t;
+    }
     if (!h->perm_checked) {
       s = choose_row_order(h, st);
       if (s != PC_OK) return s;
@@ -611,7 +628,8 @@ static pc_status pcg_solve_graph(pc_handle* h, const double* b, double* x, doubl
     }
     PC_TRY(pc::cg_graph_create(&h->graph, h->L, h->A.row_ptr, h->A.col_idx, h->A.val, h->val_f32, h->minv,
                                h->fac_f32, h->gbx, h->gbx + vs, h->cg, h->cg + vs, h->cg + 2 * vs, h->cg + 3 * vs,
-                               h->gpart, h->gscal, &bin, st));
+                               h->gpart, h->gscal, &bin,
+                               pc::CgShape{h->shape_used.spmv_ctas_per_sm, h->shape_used.ring_stages}, st));
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   PC_TRY(cudaEventCreate(&e0));
@@ -771,6 +789,100 @@ pc_status pcg_solve(const pc_csr* A, int32_t block_size, const double* b, double
   if (info) info->setup_ms = setup_ms;
   pc_destroy(h);
   return s;
+}
+
+pc_status pc_handle_shape(const pc_handle* h, pc_shape* out) {
+  if (!h || !out || !h->graph) return PC_ERR_INVALID_ARG;
+  *out = h->shape_used;
+  return PC_OK;
+}
+
+pc_status pc_autotune(const pc_csr* A, int32_t block_size, int32_t prec, int32_t iterations, int32_t max_trials,
+                      void* stream, pc_shape* best) {
+  NvtxRange nv("pc_autotune");
+  if (!csr_ok(A) || iterations < 1 || iterations > 10000 || max_trials < 0) return PC_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = A->n;
+  pc_handle* h = nullptr;
+  pc_status s = pc_setup(A, block_size, 0.0, prec, stream, &h);
+  if (s != PC_OK) {
+    if (h) pc_destroy(h);
+    return s;
+  }
+  double *b = nullptr, *x = nullptr;
+  s = dalloc(&b, sizeof(double) * (size_t)n);
+  if (s == PC_OK) s = dalloc(&x, sizeof(double) * (size_t)n);
+  if (s == PC_OK) {
+    const std::vector<double> ones((size_t)n, 1.0);
+    const cudaError_t e = cudaMemcpy(b, ones.data(), sizeof(double) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) s = from_cuda(e);
+  }
+  // one solve under the default shape decides the row order (natural or binned)
+  auto run = [&](double* ms_per_it) -> pc_status {
+    PC_TRY(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n, st));
+    pc_solve_info info;
+    memset(&info, 0, sizeof(info));
+    const pc_status r = pcg_solve_graph(h, b, x, 0.0, iterations, &info, st);
+    if (r != PC_OK && r != PC_ERR_NO_CONVERGENCE) return r;
+    if (ms_per_it) *ms_per_it = info.iterations > 0 ? info.solve_ms / info.iterations : 1e300;
+    return PC_OK;
+  };
+  if (s == PC_OK) s = run(nullptr);
+  std::vector<pc_shape> cands;
+  if (s == PC_OK) {
+    pc_shape c;
+    memset(&c, 0, sizeof(c));
+    c.bin_pipe = -1;
+    if (h->perm) {
+      for (int pipe : {1, 0})
+        for (int ring : {4, 3, 2}) {
+          c.bin_pipe = pipe;
+          c.ring_stages = ring;
+          cands.push_back(c);
+        }
+    } else {
+      for (int ctas : {4, 2, 3, 6, 8})
+        for (int ring : {4, 3, 2}) {
+          c.spmv_ctas_per_sm = ctas;
+          c.ring_stages = ring;
+          cands.push_back(c);
+        }
+    }
+    if (max_trials > 0 && (size_t)max_trials < cands.size()) cands.resize((size_t)max_trials);
+  }
+  pc_shape bestc;
+  memset(&bestc, 0, sizeof(bestc));
+  bestc.bin_pipe = -1;
+  double best_ms = 1e300;
+  for (size_t i = 0; s == PC_OK && i < cands.size(); ++i) {
+    // a new loop graph (and, for another row loop, a new binned split) with this shape
+    if (h->graph) {
+      pc::cg_graph_destroy(h->graph);
+      h->graph = nullptr;
+    }
+    if (h->perm && cands[i].bin_pipe != h->bin_pipe) {
+      release_binning(h);
+      h->perm_checked = 0;
+    }
+    h->shape_forced = 1;
+    h->shape_force = cands[i];
+    double ms = 0.0;
+    s = run(nullptr);   // builds the graph and warms it
+    if (s == PC_OK) s = run(&ms);
+    if (s == PC_OK && ms < best_ms) {
+      best_ms = ms;
+      bestc = cands[i];
+    }
+  }
+  cudaStreamSynchronize(st);
+  dfree(b);
+  dfree(x);
+  pc_destroy(h);
+  if (s != PC_OK) return s;
+  bestc.us_per_iteration = best_ms < 1e299 ? 1000.0 * best_ms : 0.0;
+  pc::tune_record(pc::tune_key(block_size, prec, A->n, A->nnz), bestc);
+  if (best) *best = bestc;
+  return pc::tune_save_env();
 }
 
 // ------------------------------------------------------------------ Lanczos

@@ -19,14 +19,20 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <stdio.h>
+
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
 
 #include "pc.h"
 #include "pc_kernels.cuh"
+#include "pc_tune.h"
 #include "pc_setup_unit.cuh"
 
 namespace pc {
@@ -732,23 +738,87 @@ int g_batch_team_max = 0;      // 0: default
 double g_batch_split = 0.0;    // 0: default slots-per-CTA target
 int g_batch_setup_kb = 0;      // 0: default shared-memory budget for setup slots (KB)
 
-// Launch shape chosen by pc_batch_autotune for a batch signature.
+// Launch shape chosen by pc_batch_autotune for a batch signature on a device with sms SMs.
 struct Tuned {
   int32_t n_sys;
   int64_t n_rows, nnz;
-  int32_t prec;
+  int32_t prec, sms;
   int32_t ctas_per_sm, team_max, setup_kb;
   double split;
 };
+std::mutex g_tuned_mu;
 std::vector<Tuned> g_tuned;
 
-const Tuned* find_tuned(const pc_batch* B, int32_t prec) {
+bool same_batch(const Tuned& a, const Tuned& b) {
+  return a.n_sys == b.n_sys && a.n_rows == b.n_rows && a.nnz == b.nnz && a.prec == b.prec && a.sms == b.sms;
+}
+
+void put_tuned(const Tuned& t) {
+  std::lock_guard<std::mutex> lk(g_tuned_mu);
+  for (Tuned& e : g_tuned)
+    if (same_batch(e, t)) {
+      e = t;
+      return;
+    }
+  g_tuned.push_back(t);
+}
+
+bool find_tuned(const pc_batch* B, int32_t prec, Tuned* out) {
+  pc::tune_autoload();
+  Tuned k{};
+  k.n_sys = B->n_sys;
+  k.n_rows = B->n_rows;
+  k.nnz = B->nnz;
+  k.prec = prec;
+  k.sms = pc::current_sms();
+  std::lock_guard<std::mutex> lk(g_tuned_mu);
   for (const Tuned& t : g_tuned)
-    if (t.n_sys == B->n_sys && t.n_rows == B->n_rows && t.nnz == B->nnz && t.prec == prec) return &t;
-  return nullptr;
+    if (same_batch(t, k)) {
+      *out = t;
+      return true;
+    }
+  return false;
 }
 
 }  // namespace
+
+namespace pc {
+
+bool batch_tune_parse(const std::map<std::string, std::string>& kv) {
+  auto num = [&](const char* k, double* v) {
+    auto it = kv.find(k);
+    if (it == kv.end() || it->second.empty()) return false;
+    char* end = nullptr;
+    *v = strtod(it->second.c_str(), &end);
+    return end != it->second.c_str() && *end == '\0' && std::isfinite(*v);
+  };
+  double ns, nr, nz, pr, sm, occ, team, kb, split;
+  if (!num("n_sys", &ns) || !num("n_rows", &nr) || !num("nnz", &nz) || !num("prec", &pr) || !num("sms", &sm) ||
+      !num("ctas_per_sm", &occ) || !num("team_max", &team) || !num("setup_kb", &kb) || !num("split", &split))
+    return false;
+  if (ns < 1 || nr < 1 || nz < 0 || pr < 0 || pr > 2 || occ < 0 || occ > 64 || team < 1 || team > 1024 || kb < 1 ||
+      kb > 228 || !(split > 0.0) || split > 64.0)
+    return false;
+  Tuned t{(int32_t)ns, (int64_t)nr, (int64_t)nz, (int32_t)pr, (int32_t)sm, (int32_t)occ, (int32_t)team, (int32_t)kb,
+          split};
+  put_tuned(t);
+  return true;
+}
+
+void batch_tune_lines(std::string& out) {
+  std::lock_guard<std::mutex> lk(g_tuned_mu);
+  char buf[512];
+  for (const Tuned& t : g_tuned) {
+    snprintf(buf, sizeof buf,
+             "{\"kind\": \"batch\", \"n_sys\": %d, \"n_rows\": %lld, \"nnz\": %lld, \"prec\": %d, \"sms\": %d, "
+             "\"ctas_per_sm\": %d, \"team_max\": %d, \"setup_kb\": %d, \"split\": %.6g}\n",
+             t.n_sys, (long long)t.n_rows, (long long)t.nnz, t.prec, t.sms, t.ctas_per_sm, t.team_max, t.setup_kb,
+             t.split);
+    out += buf;
+  }
+}
+
+}  // namespace pc
 
 extern "C" {
 
@@ -760,7 +830,10 @@ void pc_batch_set_tuning(int32_t ctas_per_sm, int32_t team_max, double slots_per
 
 void pc_batch_set_setup_smem(int32_t kb) { g_batch_setup_kb = kb > 0 ? kb : 0; }
 
-void pc_batch_clear_tuned(void) { g_tuned.clear(); }
+void pc_batch_clear_tuned(void) {
+  std::lock_guard<std::mutex> lk(g_tuned_mu);
+  g_tuned.clear();
+}
 
 int32_t pc_batch_schedule(int32_t n_sys, const int64_t* n_rows, const int64_t* nnz, const int32_t* block_size,
                           int32_t n_ctas, int32_t team_max, double slots_per_cta, int32_t* team, int32_t* slot0,
@@ -878,9 +951,10 @@ pc_status pc_batch_create(const pc_batch* B, int32_t prec, double pivot_tol, voi
   for (int bsz = 1; bsz <= B->max_block_size; ++bsz)
     need = std::max(need, pc::setup_unit_smem(pc::make_layout(64, bsz), fts));
   const int slot_bytes = (int)((need + 15) & ~(size_t)15);
+  Tuned tuned{};
   const Tuned* tu = (g_batch_ctas_per_sm || g_batch_team_max || g_batch_split > 0.0 || g_batch_setup_kb)
                         ? nullptr
-                        : find_tuned(B, prec);
+                        : (find_tuned(B, prec, &tuned) ? &tuned : nullptr);
   const int setup_kb = g_batch_setup_kb ? g_batch_setup_kb : (tu ? tu->setup_kb : 70);
   const int budget = setup_kb * 1024;
   int setup_warps = std::max(1, std::min(pc::BNW, budget / slot_bytes));
@@ -1241,15 +1315,9 @@ pc_status pc_batch_autotune(const pc_batch* B, int32_t prec, const double* b, do
     best_cfg[2] = (int32_t)(bc.split * 1000.0);
     best_cfg[3] = bc.kb;
   }
-  Tuned t{B->n_sys, B->n_rows, B->nnz, prec, bc.occ, bc.team, bc.kb, bc.split};
-  bool found = false;
-  for (Tuned& e : g_tuned)
-    if (e.n_sys == t.n_sys && e.n_rows == t.n_rows && e.nnz == t.nnz && e.prec == t.prec) {
-      e = t;
-      found = true;
-    }
-  if (!found) g_tuned.push_back(t);
-  return PC_OK;
+  Tuned t{B->n_sys, B->n_rows, B->nnz, prec, pc::current_sms(), bc.occ, bc.team, bc.kb, bc.split};
+  put_tuned(t);
+  return pc::tune_save_env();
 }
 
 pc_status pcg_solve_batched(const pc_batch* B, const double* b, double* x, double tol, int32_t max_iter,

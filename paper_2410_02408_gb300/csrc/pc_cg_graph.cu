@@ -853,7 +853,7 @@ struct CgGraph {
 
 // Plan of the warp-pipelined preconditioner: NS stages of one warp unit each per warp, as
 // deep as fits in about 110 KB per CTA.  Needs 16-byte aligned vector rows (U even).
-static CgWarpPlan warp_plan(const Layout& L, bool fac_f32, bool* usable) {
+static CgWarpPlan warp_plan(const Layout& L, bool fac_f32, int ring, bool* usable) {
   CgWarpPlan pl;
   auto up = [](int64_t v, int64_t m) { return (v + m - 1) / m * m; };
   const int64_t unit_bytes = unit_elems_minv(L) * (fac_f32 ? 4 : 8);
@@ -862,7 +862,7 @@ static CgWarpPlan warp_plan(const Layout& L, bool fac_f32, bool* usable) {
   pl.off_q = (int)(pl.off_r + vec);
   pl.stage = (int)(pl.off_q + vec);
   pl.units = L.n_units;
-  pl.ns = 4;
+  pl.ns = (ring >= 2 && ring <= 4) ? ring : 4;   // ring: stages asked for (0: the deepest that fits)
   while (pl.ns > 2 && (int64_t)CGW_WARPS * pl.ns * pl.stage > 110 * 1024) --pl.ns;
   pl.smem = 512 + CGW_WARPS * pl.ns * pl.stage;
   *usable = (L.U % 2 == 0) && pl.smem <= 110 * 1024 + 512;
@@ -966,7 +966,8 @@ int cg_graph_partials() { return sms_now() * 16 * 2 + 64; }
 // Resident CTAs per SM of the natural-order SpMV (its grid is one wave: the grid-stride loop
 // gives every CTA the same share of rows), at most SPMV_NAT_CTAS_PER_SM.
 constexpr int SPMV_NAT_CTAS_PER_SM = 4;
-static int spmv_ctas_per_sm(bool val_f32) {
+static int spmv_ctas_per_sm(bool val_f32, int cap) {
+  if (cap < 1 || cap > 8) cap = SPMV_NAT_CTAS_PER_SM;
   int occ = 0;
   const cudaError_t e =
       val_f32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cg_spmv_kernel<float, 1>, 256, 0)
@@ -975,7 +976,7 @@ static int spmv_ctas_per_sm(bool val_f32) {
     cudaGetLastError();
     return 8;
   }
-  return occ < 1 ? 1 : occ > SPMV_NAT_CTAS_PER_SM ? SPMV_NAT_CTAS_PER_SM : occ;
+  return occ < 1 ? 1 : occ > cap ? cap : occ;
 }
 
 size_t cg_scalars_bytes() { return sizeof(CgScalars); }
@@ -985,14 +986,14 @@ size_t cg_scalars_bytes() { return sizeof(CgScalars); }
 cudaError_t cg_graph_create(void** out, const Layout& L, const int32_t* rp, const int32_t* ci, const void* va,
                             bool val_f32, const void* minv, bool fac_f32, const double* b, double* x, double* r,
                             double* z, double* p, double* q, double* part, void* scal, const CgBinned* bin,
-                            cudaStream_t st) {
+                            const CgShape& shape, cudaStream_t st) {
   CgGraph* g = new CgGraph();
   memset(g, 0, sizeof(*g));
   const int sms = sms_now();
   const int64_t n = L.n;
-  g->g_spmv = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * spmv_ctas_per_sm(val_f32));
+  g->g_spmv = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * spmv_ctas_per_sm(val_f32, shape.spmv_ctas_per_sm));
   g->pl = precond_plan(L, fac_f32, &g->tma);
-  g->wpl = warp_plan(L, fac_f32, &g->wp);
+  g->wpl = warp_plan(L, fac_f32, shape.ring_stages, &g->wp);
   if (g->wp) {
     // one wave of resident CTAs, at most one CTA per 8 units
     const int per_sm = std::max(1, std::min(8, (228 * 1024) / (g->wpl.smem + 1024)));

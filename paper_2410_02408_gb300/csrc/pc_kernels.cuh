@@ -182,10 +182,15 @@ struct CgBinned {
   int32_t pipe;            // 1: pipelined row loop (gsplit sized for cg_spmv_bin_warps(true))
 };
 // bin: null (or bin->perm null) for the natural row order.
+// Launch shape of the graph engine's loop kernels (0: the default of each field).
+struct CgShape {
+  int32_t spmv_ctas_per_sm;   // natural-order SpMV: resident CTAs per SM (1..8; default 4)
+  int32_t ring_stages;        // warp-ring preconditioner: stages per warp (2..4; default the deepest that fits)
+};
 cudaError_t cg_graph_create(void** out, const Layout& L, const int32_t* rp, const int32_t* ci, const void* va,
                             bool val_f32, const void* minv, bool fac_f32, const double* b, double* x, double* r,
                             double* z, double* p, double* q, double* part, void* scal, const CgBinned* bin,
-                            cudaStream_t st);
+                            const CgShape& shape, cudaStream_t st);
 
 // Row binning (pc_rowbin.cu): rows sorted by length inside windows of ROWBIN_W rows.
 constexpr int ROWBIN_W = 2048;
