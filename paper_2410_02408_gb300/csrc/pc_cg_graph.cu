@@ -328,46 +328,70 @@ __device__ __forceinline__ void cg_spmv_body(const CgArgs& a, double* sm, int* i
         if (last) finish(__ldg(B.perm + pos), v_);
         else __stcg(B.spart + pos, v_);
       };
+      // The next item's bounds (and the index of the one after) load while the current
+      // item's rows are processed, so an item does not start with two dependent round trips.
+      // A row item (< 0) gives every lane that row's range; a group item gives each lane its
+      // row's range and the group's longest row.
+      auto item_bounds = [&](int32_t item, int32_t& s_, int32_t& c_, int32_t& gm_) {
+        if (item < 0) {
+          const int64_t pos = -(int64_t)item - 1;
+          s_ = __ldg(lo_b + pos);
+          c_ = __ldg(hi_b + pos) - s_;
+          gm_ = 0;
+        } else {
+          const int64_t idx = (int64_t)item * 32 + lane;
+          s_ = idx < n ? __ldg(lo_b + idx) : 0;
+          c_ = idx < n ? __ldg(hi_b + idx) - s_ : 0;
+          gm_ = __ldg(B.gmax + item);
+        }
+      };
+      int32_t item = g0 < g1 ? __ldg(B.items + g0) : 0;            // warp-uniform
+      int32_t item1 = g0 + 1 < g1 ? __ldg(B.items + g0 + 1) : 0;
+      int32_t s_c = 0, c_c = 0, gm_c = 0;
+      if (g0 < g1) item_bounds(item, s_c, c_c, gm_c);
       for (int32_t it = g0; it < g1; ++it) {
-        const int32_t item = __ldg(B.items + it);   // warp-uniform
+        const int32_t item2 = it + 2 < g1 ? __ldg(B.items + it + 2) : 0;
+        int32_t s_n = 0, c_n = 0, gm_n = 0;
+        if (it + 1 < g1) item_bounds(item1, s_n, c_n, gm_n);
         if (item < 0) {
           // one row of a group of hub rows: the whole warp on it
           const int64_t pos = -(int64_t)item - 1;
-          const int32_t s = __ldg(lo_b + pos);
-          const int32_t cnt = __ldg(hi_b + pos) - s;
-          double v = cg_range<VT, 32, PIPE>(a.ci, va, X, s, cnt, cnt, 0.0, ps, pk);
+          double v = cg_range<VT, 32, PIPE>(a.ci, va, X, s_c, c_c, c_c, 0.0, ps, pk);
           if (lane == 0) {
             if (!first) v += __ldcg(B.spart + pos);
             done_pos(pos, v);
           }
-          continue;
-        }
-        const int32_t g = item;
-        const int64_t idx = (int64_t)g * 32 + lane;
-        const bool valid = idx < n;
-        const int32_t s0 = valid ? __ldg(lo_b + idx) : 0;
-        const int32_t cnt0 = valid ? __ldg(hi_b + idx) - s0 : 0;
-        const int32_t gmax = __ldg(B.gmax + g);   // warp-uniform
-        if (gmax <= 64) {
-          const double init = (!first && valid) ? __ldcg(B.spart + idx) : 0.0;
-          const double v = cg_range<VT, 1, PIPE>(a.ci, va, X, s0, cnt0, __reduce_max_sync(FULL, cnt0), init, ps, pk);
-          if (valid) done_pos(idx, v);
         } else {
-          // 8 lanes per row, 4 rows per pass (groups whose longest row has more than 256
-          // entries are split into single-row items when the items are built)
-          for (int pp = 0; pp < 8; ++pp) {
-            const int src = pp * 4 + (lane >> 3);
-            const int32_t s = __shfl_sync(FULL, s0, src);
-            const int32_t cnt = __shfl_sync(FULL, cnt0, src);
-            const int vld = __shfl_sync(FULL, (int)valid, src);
-            double v = cg_range<VT, 8, PIPE>(a.ci, va, X, s, cnt, __reduce_max_sync(FULL, cnt), 0.0, ps, pk);
-            if ((lane & 7) == 0 && vld) {
-              const int64_t pos = (int64_t)g * 32 + src;
-              if (!first) v += __ldcg(B.spart + pos);
-              done_pos(pos, v);
+          const int32_t g = item;
+          const int64_t idx = (int64_t)g * 32 + lane;
+          const bool valid = idx < n;
+          const int32_t s0 = s_c, cnt0 = c_c;
+          if (gm_c <= 64) {
+            const double init = (!first && valid) ? __ldcg(B.spart + idx) : 0.0;
+            const double v = cg_range<VT, 1, PIPE>(a.ci, va, X, s0, cnt0, __reduce_max_sync(FULL, cnt0), init, ps, pk);
+            if (valid) done_pos(idx, v);
+          } else {
+            // 8 lanes per row, 4 rows per pass (groups whose longest row has more than 256
+            // entries are split into single-row items when the items are built)
+            for (int pp = 0; pp < 8; ++pp) {
+              const int src = pp * 4 + (lane >> 3);
+              const int32_t s = __shfl_sync(FULL, s0, src);
+              const int32_t cnt = __shfl_sync(FULL, cnt0, src);
+              const int vld = __shfl_sync(FULL, (int)valid, src);
+              double v = cg_range<VT, 8, PIPE>(a.ci, va, X, s, cnt, __reduce_max_sync(FULL, cnt), 0.0, ps, pk);
+              if ((lane & 7) == 0 && vld) {
+                const int64_t pos = (int64_t)g * 32 + src;
+                if (!first) v += __ldcg(B.spart + pos);
+                done_pos(pos, v);
+              }
             }
           }
         }
+        item = item1;
+        item1 = item2;
+        s_c = s_n;
+        c_c = c_n;
+        gm_c = gm_n;
       }
     }
   } else {
