@@ -166,6 +166,19 @@ int32_t pc_handle_refactored_fp64(const pc_handle *h);
  * must not overlap.  Stream-ordered, does not synchronise. */
 pc_status pc_apply(pc_handle *h, int32_t mode, const double *in, double *out, void *stream);
 
+/* pc_apply_tol - pc_apply with a refinement tolerance for z = M^{-1} r (Sec. 3.3's per-block
+ * solve; the mixed-precision pattern "FP32 factors, FP64 refinement").  tol = 0: exactly
+ * pc_apply (any mode).  tol > 0 (mode PC_APPLY_INV only, else PC_ERR_INVALID_ARG): z starts as
+ * the apply with the stored factors, then while ||r - blockdiag(A) z|| > tol ||r|| (the
+ * diagonal blocks of the partition read from the CSR in FP64) and fewer than 20 corrections
+ * were made, z += M^{-1} (r - blockdiag(A) z).  *steps (HOST, may be NULL): corrections made;
+ * *rel_residual (HOST, may be NULL): the last ||r - blockdiag(A) z|| / ||r|| (0 for r = 0).
+ * Returns PC_ERR_NO_CONVERGENCE when the tolerance was not reached (out holds the last z) and
+ * PC_ERR_BREAKDOWN for a non-finite residual.  With tol > 0 it synchronises the stream and
+ * allocates a workspace of about 2n + 521 doubles on the handle at its first use. */
+pc_status pc_apply_tol(pc_handle *h, int32_t mode, const double *in, double *out, double tol,
+                       int32_t *steps, double *rel_residual, void *stream);
+
 /* pc_get_factor - copy the stored factor of h into dense row-major blocks
  * out[k][i][j] (device, nblocks * bs * bs doubles): which = 0 gives L_k^{-1} (lower
  * triangular), which = 1 gives M_k^{-1}.  Padding rows/columns of the last block are

@@ -148,6 +148,8 @@ def lib():
         "pc_handle_col_segments": (_I32, [_P]),
         "pc_handle_refactored_fp64": (_I32, [_P]),
         "pc_handle_row_binned": (_I32, [_P]),
+        "pc_apply_tol": (_I32, [_P, _I32, _P, _P, _D, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
+                                _P]),
         "pc_autotune": (_I32, [ctypes.POINTER(pc_csr), _I32, _I32, _I32, _I32, _P, ctypes.POINTER(pc_shape)]),
         "pc_tune_set": (_I32, [_I32, _I32, _I64, _I64, ctypes.POINTER(pc_shape)]),
         "pc_tune_get": (_I32, [_I32, _I32, _I64, _I64, ctypes.POINTER(pc_shape)]),
@@ -273,6 +275,19 @@ class Handle:
         out = torch.empty_like(v) if out is None else out
         _check(lib().pc_apply(self._h, APPLY[mode], _ptr(v), _ptr(out), _stream()), f"pc_apply({mode})")
         return out
+
+    def apply_refined(self, v, tol: float, out=None, mode: str = "inv"):
+        """z = M^{-1} v refined against the FP64 diagonal blocks until ||v - blockdiag(A) z|| <=
+        tol ||v|| (pc_apply_tol; tol = 0 is pc_apply in any mode).  Returns (z, corrections
+        made, relative block residual)."""
+        torch = _torch()
+        v = _dev(v, torch.float64)
+        out = torch.empty_like(v) if out is None else out
+        steps = ctypes.c_int32(0)
+        rel = ctypes.c_double(0.0)
+        _check(lib().pc_apply_tol(self._h, APPLY[mode], _ptr(v), _ptr(out), float(tol), ctypes.byref(steps),
+                                  ctypes.byref(rel), _stream()), "pc_apply_tol")
+        return out, int(steps.value), float(rel.value)
 
     def factor(self, which: str = "minv"):
         torch = _torch()

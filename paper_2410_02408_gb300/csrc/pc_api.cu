@@ -1,6 +1,7 @@
 // Host side of the libpc C ABI (include/pc.h): argument checks, handle and workspace
 // management, kernel dispatch and status reporting.  No call prints, aborts or traps.
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -56,6 +57,7 @@ struct pc_handle {
   int64_t prof_ns[3];    // graph engine, profiling mode: mean ns per iteration of the 3 kernels
   int prof_valid;
   // launch shape of the loop graph: forced (autotuner trials), else the tuned table, else defaults
+  double* ref_ws;        // pc_apply_tol: residual, correction, dot partials and results
   int shape_forced;
   pc_shape shape_force;
   pc_shape shape_used;   // valid once the graph exists
@@ -260,6 +262,7 @@ pc_status pc_destroy(pc_handle* h) {
   dfree(h->spart);
   dfree(h->gpart);
   dfree(h->gscal);
+  dfree(h->ref_ws);
   delete h;
   return PC_OK;
 }
@@ -385,6 +388,56 @@ pc_status pc_apply(pc_handle* h, int32_t mode, const double* in, double* out, vo
     }
     default: return PC_ERR_INVALID_ARG;
   }
+}
+
+pc_status pc_apply_tol(pc_handle* h, int32_t mode, const double* in, double* out, double tol, int32_t* steps,
+                       double* rel_residual, void* stream) {
+  NvtxRange nv("pc_apply_tol");
+  if (steps) *steps = 0;
+  if (rel_residual) *rel_residual = -1.0;
+  if (!h || !in || !out || in == out || !(tol >= 0.0) || !isfinite(tol)) return PC_ERR_INVALID_ARG;
+  if (tol == 0.0) return pc_apply(h, mode, in, out, stream);
+  if (mode != PC_APPLY_INV) return PC_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = h->A.n;
+  const int64_t vs = vec_stride(n);
+  if (!h->ref_ws) {
+    const pc_status sa = dalloc(&h->ref_ws, sizeof(double) * (size_t)(2 * vs + pc::dot_partials() + 8));
+    if (sa != PC_OK) return sa;
+  }
+  double* d = h->ref_ws;
+  double* e = h->ref_ws + vs;
+  double* part = h->ref_ws + 2 * vs;
+  double* res = part + pc::dot_partials();   // res[0] = r.r, res[1] = d.d
+  PC_TRY(pc::launch_dot(n, in, in, res, part, st));
+  double rr = 0.0;
+  PC_TRY(cudaMemcpyAsync(&rr, res, sizeof(double), cudaMemcpyDeviceToHost, st));
+  PC_TRY(pc::launch_apply(h->L, h->minv, h->fac_f32, 0, in, out, st));
+  PC_TRY(cudaStreamSynchronize(st));
+  if (rr == 0.0) {
+    if (rel_residual) *rel_residual = 0.0;
+    return PC_OK;
+  }
+  constexpr int kMaxSteps = 20;
+  double rel = 0.0;
+  int k = 0;
+  for (;;) {
+    // d = r - blockdiag(A) z in FP64; stop when ||d|| <= tol ||r||, else z += M^{-1} d
+    PC_TRY(pc::launch_block_residual(n, h->bs, h->A.row_ptr, h->A.col_idx, h->A.val, h->val_f32, in, out, d, st));
+    PC_TRY(pc::launch_dot(n, d, d, res + 1, part, st));
+    double dd = 0.0;
+    PC_TRY(cudaMemcpyAsync(&dd, res + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    PC_TRY(cudaStreamSynchronize(st));
+    rel = sqrt(dd / rr);
+    if (!(rel > tol) || k >= kMaxSteps) break;
+    PC_TRY(pc::launch_apply(h->L, h->minv, h->fac_f32, 0, d, e, st));
+    PC_TRY(pc::launch_add(n, e, out, st));
+    ++k;
+  }
+  if (steps) *steps = k;
+  if (rel_residual) *rel_residual = rel;
+  if (!isfinite(rel)) return PC_ERR_BREAKDOWN;
+  return rel <= tol ? PC_OK : PC_ERR_NO_CONVERGENCE;
 }
 
 pc_status pc_get_factor(const pc_handle* h, int32_t which, double* out, void* stream) {

@@ -123,6 +123,10 @@ cudaError_t launch_dot(int64_t n, const double* x, const double* y, double* resu
 int dot_partials();
 cudaError_t launch_apply(const Layout& L, const void* fac, bool fac_f32, int mode, const double* in,
                          double* out, cudaStream_t st);
+// d = r - blockdiag(A) z (FP64, the diagonal blocks of the partition read from the CSR); z += e.
+cudaError_t launch_block_residual(int64_t n, int32_t bs, const int32_t* rp, const int32_t* ci, const void* va,
+                                  bool val_f32, const double* r, const double* z, double* d, cudaStream_t st);
+cudaError_t launch_add(int64_t n, const double* e, double* z, cudaStream_t st);
 // out = L^{-1} (A t) (+ optional Lanczos epilogue, see pc_ops.cu)
 struct SymPhase2Args {
   Layout lay;

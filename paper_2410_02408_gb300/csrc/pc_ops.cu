@@ -1,8 +1,8 @@
 // Stand-alone operators: CSR SpMV, fixed-order dot product, block preconditioner
 // application (M^{-1}, L^{-1}, L^{-T}), the second phase of the symmetric operator
 // L^{-1} A L^{-T} (SpMV with a fused per-unit L^{-1} epilogue), the SpMV row split of
-// the persistent CG kernel, the adjoint gradient on the sparsity pattern, and the O(nnz)
-// structure check of a CSR matrix.
+// the persistent CG kernel, the adjoint gradient on the sparsity pattern, the O(nnz)
+// structure check of a CSR matrix, and the block residual of the refined preconditioner apply.
 #include "pc_kernels.cuh"
 #include "pc_setup_unit.cuh"
 
@@ -96,6 +96,55 @@ cudaError_t launch_validate_csr(int64_t n, int64_t nnz, const int32_t* rp, const
   cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   validate_csr_kernel<<<grid > 0 ? grid : 1, 256, 0, st>>>(n, nnz, rp, ci, flags);
+  return cudaGetLastError();
+}
+
+// d = r - blockdiag(A) z: each row's sum runs over its stored entries whose column lies in the
+// row's own diagonal block [k bs, min((k + 1) bs, n)) (one FMA chain in storage order), in FP64
+// from the CSR values (float values widened exactly).
+template <typename VT>
+__global__ void __launch_bounds__(256) block_residual_kernel(int64_t n, int32_t bs, const int32_t* __restrict__ rp,
+                                                             const int32_t* __restrict__ ci, const VT* __restrict__ va,
+                                                             const double* __restrict__ r, const double* __restrict__ z,
+                                                             double* __restrict__ d) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c0 = (i / bs) * bs, c1 = c0 + bs < n ? c0 + bs : n;
+    double s = 0.0;
+    for (int32_t e = __ldg(rp + i), e1 = __ldg(rp + i + 1); e < e1; ++e) {
+      const int64_t c = __ldg(ci + e);
+      if (c >= c0 && c < c1) s = fma((double)__ldg(va + e), z[c], s);
+    }
+    d[i] = r[i] - s;
+  }
+}
+
+__global__ void __launch_bounds__(256) add_kernel(int64_t n, const double* __restrict__ e, double* __restrict__ z) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    z[i] += e[i];
+}
+
+static int grid_for(int64_t n) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t cap = (int64_t)(sms > 0 ? sms : 1) * 8;
+  const int64_t want = (n + 255) / 256;
+  return (int)(want < 1 ? 1 : want < cap ? want : cap);
+}
+
+cudaError_t launch_block_residual(int64_t n, int32_t bs, const int32_t* rp, const int32_t* ci, const void* va,
+                                  bool val_f32, const double* r, const double* z, double* d, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (val_f32)
+    block_residual_kernel<float><<<grid_for(n), 256, 0, st>>>(n, bs, rp, ci, (const float*)va, r, z, d);
+  else
+    block_residual_kernel<double><<<grid_for(n), 256, 0, st>>>(n, bs, rp, ci, (const double*)va, r, z, d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add(int64_t n, const double* e, double* z, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  add_kernel<<<grid_for(n), 256, 0, st>>>(n, e, z);
   return cudaGetLastError();
 }
 
