@@ -325,7 +325,7 @@ __device__ __forceinline__ void cg_spmv_body(const CgArgs& a, double* sm, int* i
       const bool first = sg == 0, last = sg == nseg - 1;
       // position pos of the binned order is done with this segment: keep the partial or finish
       auto done_pos = [&](int64_t pos, double v_) {
-        if (last) finish(__ldg(B.perm + pos), v_);
+        if (last) finish(ld_hint(B.perm + pos, ps), v_);
         else __stcg(B.spart + pos, v_);
       };
       // The next item's bounds (and the index of the one after) load while the current
@@ -335,22 +335,22 @@ __device__ __forceinline__ void cg_spmv_body(const CgArgs& a, double* sm, int* i
       auto item_bounds = [&](int32_t item, int32_t& s_, int32_t& c_, int32_t& gm_) {
         if (item < 0) {
           const int64_t pos = -(int64_t)item - 1;
-          s_ = __ldg(lo_b + pos);
-          c_ = __ldg(hi_b + pos) - s_;
+          s_ = ld_hint(lo_b + pos, ps);
+          c_ = ld_hint(hi_b + pos, ps) - s_;
           gm_ = 0;
         } else {
           const int64_t idx = (int64_t)item * 32 + lane;
-          s_ = idx < n ? __ldg(lo_b + idx) : 0;
-          c_ = idx < n ? __ldg(hi_b + idx) - s_ : 0;
-          gm_ = __ldg(B.gmax + item);
+          s_ = idx < n ? ld_hint(lo_b + idx, ps) : 0;
+          c_ = idx < n ? ld_hint(hi_b + idx, ps) - s_ : 0;
+          gm_ = ld_hint(B.gmax + item, ps);
         }
       };
-      int32_t item = g0 < g1 ? __ldg(B.items + g0) : 0;            // warp-uniform
-      int32_t item1 = g0 + 1 < g1 ? __ldg(B.items + g0 + 1) : 0;
+      int32_t item = g0 < g1 ? ld_hint(B.items + g0, ps) : 0;            // warp-uniform
+      int32_t item1 = g0 + 1 < g1 ? ld_hint(B.items + g0 + 1, ps) : 0;
       int32_t s_c = 0, c_c = 0, gm_c = 0;
       if (g0 < g1) item_bounds(item, s_c, c_c, gm_c);
       for (int32_t it = g0; it < g1; ++it) {
-        const int32_t item2 = it + 2 < g1 ? __ldg(B.items + it + 2) : 0;
+        const int32_t item2 = it + 2 < g1 ? ld_hint(B.items + it + 2, ps) : 0;
         int32_t s_n = 0, c_n = 0, gm_n = 0;
         if (it + 1 < g1) item_bounds(item1, s_n, c_n, gm_n);
         if (item < 0) {
