@@ -445,8 +445,8 @@ void pc_batch_set_tuning(int32_t ctas_per_sm, int32_t team_max, double slots_per
 void pc_batch_set_setup_smem(int32_t kb);
 
 /* Autotuner of the batched launch: solves the batch (setup + PCG, right-hand side b) with
- * up to max_trials candidate launch shapes (0 = all 24: CTAs per SM {occupancy maximum, 1}
- * x team limit {8, 32} x slots per CTA {1, 2, 4} x setup shared memory {70, 140} KB),
+ * up to max_trials candidate launch shapes (0 = all 36: CTAs per SM {occupancy maximum, 1}
+ * x team limit {4, 8, 32} x slots per CTA {8, 4, 2} x setup shared memory {70, 140} KB),
  * timing the second (graph-replayed) solve of each, and records the fastest for this batch
  * signature (n_sys, n_rows, nnz, prec): later pc_batch_create calls on a matching batch use
  * it unless explicit tuning was set.  Allocates a scratch x.  best_ms (host, may be NULL):

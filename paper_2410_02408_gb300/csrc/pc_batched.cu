@@ -1260,9 +1260,10 @@ pc_status pc_batch_autotune(const pc_batch* B, int32_t prec, const double* b, do
     double split;
   };
   std::vector<Cand> cands;
+  // the measured best on the 512-system RGG batch (team limit 4, 8 slots per CTA) comes first
   for (int occ : {0, 1})
-    for (int team : {8, 32})
-      for (double split : {1.0, 2.0, 4.0})
+    for (int team : {4, 8, 32})
+      for (double split : {8.0, 4.0, 2.0})
         for (int kb : {70, 140}) cands.push_back({occ, team, kb, split});
   const int saved_occ = g_batch_ctas_per_sm, saved_team = g_batch_team_max, saved_kb = g_batch_setup_kb;
   const double saved_split = g_batch_split;

@@ -183,7 +183,7 @@ def test_batched_autotune_records_a_shape(pc, small_batch):
     b = _rhs(batch, 9)
     pc.binding.lib().pc_batch_clear_tuned()
     ms, cfg = pc.batch_autotune(batch, b, tol=1e-10, max_trials=4)
-    assert ms > 0 and cfg["team_max"] in (8, 32) and cfg["setup_kb"] in (70, 140)
+    assert ms > 0 and cfg["team_max"] in (4, 8, 32) and cfg["setup_kb"] in (70, 140)
     H = pc.Batch(batch)
     try:
         li = H.launch_info()
