@@ -58,8 +58,9 @@ from paper_2410_02408_gb300 import workloads as W  # noqa: E402
 METRIC = "PCG+precond GB/s (% HBM peak), mixed vs FP64, to rel. residual 1e-10"
 FALLBACK_HBM_GBS = 6800.0
 # Launch shape of the batched workload when its autotuner is skipped (the fastest measured on
-# the 512-system batch): CTAs per SM, team limit, slots per CTA, setup shared memory (KB).
-BATCH_SHAPE_DEFAULT = "2,4,8,70"
+# the 512-system batch for each factor precision): CTAs per SM, team limit, slots per CTA,
+# setup shared memory (KB).
+BATCH_SHAPE_DEFAULT = {"fp32": "2,4,8,70", "tf32": "2,4,8,70", "fp64": "2,8,4,70"}
 
 
 def parse(argv=None):
@@ -921,12 +922,18 @@ def batched_result(pc, args, steps, warmup, tune=True):
     st = torch.cuda.current_stream()
     peak, peak_kind = measured_hbm()
     tuning = {}
-    shape = args.batch_shape or ("" if tune and not args.no_tune else BATCH_SHAPE_DEFAULT)
-    if shape:
-        occ, team, split, kb = shape.split(",")
+    use_defaults = not args.batch_shape and not (tune and not args.no_tune)
+
+    def set_shape(sh):
+        occ, team, split, kb = sh.split(",")
         pc.batch_set_tuning(int(occ), int(team), float(split))
         pc.binding.lib().pc_batch_set_setup_smem(int(kb))
-        tuning["explicit"] = shape
+
+    if args.batch_shape:
+        set_shape(args.batch_shape)
+        tuning["explicit"] = args.batch_shape
+    elif use_defaults:
+        tuning["explicit"] = dict(BATCH_SHAPE_DEFAULT)
     else:
         for prec in ([args.prec, "fp64"] if args.prec != "fp64" and not args.no_fp64_compare else [args.prec]):
             t0 = time.time()
@@ -934,6 +941,8 @@ def batched_result(pc, args, steps, warmup, tune=True):
             tuning[prec] = {"best_ms": tms, "config": cfg, "tuning_s": time.time() - t0}
 
     def timed(prec, nsteps, nwarm):
+        if use_defaults:
+            set_shape(BATCH_SHAPE_DEFAULT.get(prec, BATCH_SHAPE_DEFAULT["fp32"]))
         H = pc.Batch(batch, prec)
         x = torch.empty_like(bd)
         for _ in range(nwarm):
@@ -1005,6 +1014,8 @@ def batched_result(pc, args, steps, warmup, tune=True):
         hrp = torch.from_numpy(batch.row_ptr).pin_memory()
         hci = torch.from_numpy(batch.col).pin_memory()
         hva = torch.from_numpy(batch.val).pin_memory()
+        if use_defaults:
+            set_shape(BATCH_SHAPE_DEFAULT.get(args.prec, BATCH_SHAPE_DEFAULT["fp32"]))
         H = pc.Batch(batch, args.prec)
         dbb = torch.empty_like(hb, device="cuda")
         xe = torch.empty_like(dbb)
