@@ -300,18 +300,6 @@ __device__ __forceinline__ void cg_spmv_body(const CgArgs& a, double* sm, int* i
   const int64_t n = a.lay.n;
   const double* X = MODE == 1 ? a.p : a.x;
   double acc = 0.0;
-  // the row's result goes to the lane that computed it
-  auto finish = [&](int64_t r_, double v_) {
-    if (MODE == 1) {
-      a.q[r_] = v_;
-      acc = fma(__ldg(a.p + r_), v_, acc);
-    } else {
-      const double bi = __ldg(a.b + r_);
-      const double ri = bi - v_;
-      a.r[r_] = ri;
-      acc = MODE == 0 ? fma(bi, bi, acc) : fma(ri, ri, acc);
-    }
-  };
   if constexpr (BIN) {
     const CgBinned& B = a.bin;
     const int lane = threadIdx.x & 31;
@@ -319,57 +307,75 @@ __device__ __forceinline__ void cg_spmv_body(const CgArgs& a, double* sm, int* i
     const int32_t g0 = __ldg(B.gsplit + gw), g1 = __ldg(B.gsplit + gw + 1);
     const int nseg = B.nseg;
     const uint64_t ps = l2_policy_evict_first(), pk = l2_policy_evict_last();
+    const double* __restrict__ W = MODE == 1 ? a.p : a.b;   // the epilogue's vector
+    // the row's result with its preloaded entry w_ of the epilogue's vector
+    auto finish_w = [&](int64_t r_, double v_, double w_) {
+      if (MODE == 1) {
+        a.q[r_] = v_;
+        acc = fma(w_, v_, acc);
+      } else {
+        const double ri = w_ - v_;
+        a.r[r_] = ri;
+        acc = MODE == 0 ? fma(w_, w_, acc) : fma(ri, ri, acc);
+      }
+    };
     for (int sg = 0; sg < nseg; ++sg) {
       const int32_t* lo_b = B.bnd + (int64_t)sg * B.bstride;
       const int32_t* hi_b = lo_b + B.bstride;
       const bool first = sg == 0, last = sg == nseg - 1;
-      // position pos of the binned order is done with this segment: keep the partial or finish
-      auto done_pos = [&](int64_t pos, double v_) {
-        if (last) finish(ld_hint(B.perm + pos, ps), v_);
-        else __stcg(B.spart + pos, v_);
-      };
-      // The next item's bounds (and the index of the one after) load while the current
-      // item's rows are processed, so an item does not start with two dependent round trips.
-      // A row item (< 0) gives every lane that row's range; a group item gives each lane its
-      // row's range and the group's longest row.
-      auto item_bounds = [&](int32_t item, int32_t& s_, int32_t& c_, int32_t& gm_) {
+      // The next item's bounds, and in the last segment its rows' original indices, load while
+      // the current item's rows are processed; the rows' entries of the epilogue's vector load
+      // when the item starts.  So an item neither starts with two dependent round trips nor
+      // ends with two (the permutation, then the vector entry it addresses).  A row item (< 0)
+      // gives every lane that row's range and index; a group item gives each lane its row's
+      // range and index and the group's longest row.
+      auto item_bounds = [&](int32_t item, int32_t& s_, int32_t& c_, int32_t& gm_, int32_t& r_) {
+        r_ = 0;
         if (item < 0) {
           const int64_t pos = -(int64_t)item - 1;
           s_ = ld_hint(lo_b + pos, ps);
           c_ = ld_hint(hi_b + pos, ps) - s_;
           gm_ = 0;
+          if (last) r_ = ld_hint(B.perm + pos, ps);
         } else {
           const int64_t idx = (int64_t)item * 32 + lane;
           s_ = idx < n ? ld_hint(lo_b + idx, ps) : 0;
           c_ = idx < n ? ld_hint(hi_b + idx, ps) - s_ : 0;
           gm_ = ld_hint(B.gmax + item, ps);
+          if (last && idx < n) r_ = ld_hint(B.perm + idx, ps);
         }
       };
       int32_t item = g0 < g1 ? ld_hint(B.items + g0, ps) : 0;            // warp-uniform
       int32_t item1 = g0 + 1 < g1 ? ld_hint(B.items + g0 + 1, ps) : 0;
-      int32_t s_c = 0, c_c = 0, gm_c = 0;
-      if (g0 < g1) item_bounds(item, s_c, c_c, gm_c);
+      int32_t s_c = 0, c_c = 0, gm_c = 0, r_c = 0;
+      if (g0 < g1) item_bounds(item, s_c, c_c, gm_c, r_c);
       for (int32_t it = g0; it < g1; ++it) {
         const int32_t item2 = it + 2 < g1 ? ld_hint(B.items + it + 2, ps) : 0;
-        int32_t s_n = 0, c_n = 0, gm_n = 0;
-        if (it + 1 < g1) item_bounds(item1, s_n, c_n, gm_n);
+        int32_t s_n = 0, c_n = 0, gm_n = 0, r_n = 0;
+        if (it + 1 < g1) item_bounds(item1, s_n, c_n, gm_n, r_n);
         if (item < 0) {
           // one row of a group of hub rows: the whole warp on it
           const int64_t pos = -(int64_t)item - 1;
+          const double w_c = last ? __ldg(W + r_c) : 0.0;
           double v = cg_range<VT, 32, PIPE>(a.ci, va, X, s_c, c_c, c_c, 0.0, ps, pk);
           if (lane == 0) {
             if (!first) v += __ldcg(B.spart + pos);
-            done_pos(pos, v);
+            if (last) finish_w(r_c, v, w_c);
+            else __stcg(B.spart + pos, v);
           }
         } else {
           const int32_t g = item;
           const int64_t idx = (int64_t)g * 32 + lane;
           const bool valid = idx < n;
+          const double w_c = (last && valid) ? __ldg(W + r_c) : 0.0;
           const int32_t s0 = s_c, cnt0 = c_c;
           if (gm_c <= 64) {
             const double init = (!first && valid) ? __ldcg(B.spart + idx) : 0.0;
             const double v = cg_range<VT, 1, PIPE>(a.ci, va, X, s0, cnt0, __reduce_max_sync(FULL, cnt0), init, ps, pk);
-            if (valid) done_pos(idx, v);
+            if (valid) {
+              if (last) finish_w(r_c, v, w_c);
+              else __stcg(B.spart + idx, v);
+            }
           } else {
             // 8 lanes per row, 4 rows per pass (groups whose longest row has more than 256
             // entries are split into single-row items when the items are built)
@@ -379,10 +385,13 @@ __device__ __forceinline__ void cg_spmv_body(const CgArgs& a, double* sm, int* i
               const int32_t cnt = __shfl_sync(FULL, cnt0, src);
               const int vld = __shfl_sync(FULL, (int)valid, src);
               double v = cg_range<VT, 8, PIPE>(a.ci, va, X, s, cnt, __reduce_max_sync(FULL, cnt), 0.0, ps, pk);
+              const int32_t r_s = __shfl_sync(FULL, r_c, src);
+              const double w_s = __shfl_sync(FULL, w_c, src);
               if ((lane & 7) == 0 && vld) {
                 const int64_t pos = (int64_t)g * 32 + src;
                 if (!first) v += __ldcg(B.spart + pos);
-                done_pos(pos, v);
+                if (last) finish_w(r_s, v, w_s);
+                else __stcg(B.spart + pos, v);
               }
             }
           }
@@ -392,6 +401,7 @@ __device__ __forceinline__ void cg_spmv_body(const CgArgs& a, double* sm, int* i
         s_c = s_n;
         c_c = c_n;
         gm_c = gm_n;
+        r_c = r_n;
       }
     }
   } else {
