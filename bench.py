@@ -463,7 +463,8 @@ def kernel_times(pc, Ad, bd, bs, prec, args):
         hp = pc.setup(Ad, bs, prec=prec)
         hp.pcg(bd, tol=args.tol, max_iter=args.maxit)
         kt = hp.trace(8)
-        order = {"binned": hp.row_binned(), "col_segments": hp.col_segments()}
+        order = {"binned": hp.row_binned(), "col_segments": hp.col_segments(),
+                 "fused_update": hp.shape()["fuse_update"] == 1}
         hp.destroy()
     finally:
         del os.environ["PC_CG_PROFILE"]
@@ -471,11 +472,14 @@ def kernel_times(pc, Ad, bd, bs, prec, args):
     return us[0], us[1], us[2], order
 
 
-def kernel_table(n, nnz, vb, bs, prec, spmv_us, prec_us, upd_us, peak, peak_kind, traffic, kernel_name):
+def kernel_table(n, nnz, vb, bs, prec, spmv_us, prec_us, upd_us, peak, peak_kind, traffic, kernel_name,
+                 fused=False):
     fb = 4 if prec != "fp64" else 8
     spmv_bytes = csr_bytes(n, nnz, vb) + 2 * 8 * n                      # CSR, p (read once), q
     prec_bytes = factor_bytes(n, bs, fb)[0] + 4 * 8 * n                   # M^{-1}, r, q in; r, z out
     upd_bytes = 5 * 8 * n                                                 # x, p, z in; x, p out
+    if fused:   # one kernel does both: its algorithmic bytes are the two kernels' together
+        prec_bytes += upd_bytes
     gbs = lambda b, us: b / (us * 1e-6) / 1e9 if us > 0 else 0.0        # noqa: E731
     achieved = gbs(spmv_bytes, spmv_us)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -485,8 +489,9 @@ def kernel_table(n, nnz, vb, bs, prec, spmv_us, prec_us, upd_us, peak, peak_kind
         "spmv": {"us": spmv_us, "GBs": achieved, "bytes": spmv_bytes},
         "precond": {"us": prec_us, "GBs": gbs(prec_bytes, prec_us), "bytes": prec_bytes,
                     "frac": gbs(prec_bytes, prec_us) / peak},
-        "update": {"us": upd_us, "GBs": gbs(upd_bytes, upd_us), "bytes": upd_bytes,
-                   "frac": gbs(upd_bytes, upd_us) / peak},
+        "update": ({"fused_into": "precond (x += alpha p and p = z + beta p as its tail)"} if fused else
+                   {"us": upd_us, "GBs": gbs(upd_bytes, upd_us), "bytes": upd_bytes,
+                    "frac": gbs(upd_bytes, upd_us) / peak}),
         "note": "profiling mode: kernels launched one by one with CUDA events around each; every step "
                 "starts with a 40 us spacer kernel so that the intervals exclude host launch latency",
     }
@@ -560,12 +565,14 @@ def run_ours(args):
     kname = ("cg_spmv_bin_pipe_kernel (binned rows; q = A p and p.q; one launch per CG iteration)"
              if spmv_order["binned"] else "cg_spmv_kernel (q = A p and p.q; one launch per CG iteration)")
     roofline, kernels = kernel_table(n, nnz, vb, args.bs, args.prec, spmv_us, prec_us, upd_us, peak, peak_kind,
-                                     traffic, kname)
+                                     traffic, kname, fused=spmv_order["fused_update"])
     # launches of this library's kernels per step: the CSR check, setup; the row-length statistic
     # (auto row order) and, when binned, the binning, cost split (3) and segment bounds; per
-    # round I1, I2, arm, T; 3 per iteration
+    # round I1, I2, arm, T; per iteration the SpMV and the preconditioner (with the update as its
+    # tail) or 3 with a separate update kernel
     order_launches = (1 if args.row_binning == "auto" else 0) + (5 if spmv_order["binned"] else 0)
-    launches = sum(2 + order_launches + 4 * (i["restarts"] + 1) + 3 * i["iterations"] for i in infos)
+    per_it = 2 if spmv_order["fused_update"] else 3
+    launches = sum(2 + order_launches + 4 * (i["restarts"] + 1) + per_it * i["iterations"] for i in infos)
     xr = x.cpu().numpy()
     true_res = float(np.linalg.norm(b - A.to_scipy() @ xr) / np.linalg.norm(b))   # report only
 
@@ -1111,7 +1118,7 @@ def powerlaw_result(pc, args, steps, warmup):
     kname = ("cg_spmv_bin_pipe_kernel (binned rows; q = A p and p.q; one launch per CG iteration)"
              if order["binned"] else "cg_spmv_kernel (q = A p and p.q; one launch per CG iteration)")
     roofline, kernels = kernel_table(n, nnz, vb, bs, args.prec, spmv_us, prec_us, upd_us, peak, peak_kind, None,
-                                     kname)
+                                     kname, fused=order["fused_update"])
     info = infos[-1]
     res = {"metric": METRIC, "value": value, "unit": "GB/s", "ms_per_step": ms, "steps": steps, "warmup": warmup,
            "config": {"workload": f"powerlaw_{n}_fp32vals", "n": n, "nnz": nnz, "block_size": bs,
@@ -1124,7 +1131,8 @@ def powerlaw_result(pc, args, steps, warmup):
            "frac_of_hbm_peak": value / peak, "roofline": roofline, "kernels": kernels, "spmv_order": order,
            "launch_shapes": shapes or "library defaults (--no-tune)",
            "generation_s": gen_s,
-           "gpu_launches": sum(2 + 6 + 4 * (i["restarts"] + 1) + 3 * i["iterations"] for i in infos)}
+           "gpu_launches": sum(2 + 6 + 4 * (i["restarts"] + 1) + (2 if order["fused_update"] else 3) * i["iterations"]
+                               for i in infos)}
     res["clocks"] = clk.summary()
     x64 = None
     if args.prec != "fp64" and not args.no_fp64_compare:

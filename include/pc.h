@@ -516,15 +516,24 @@ typedef struct {
                                  the deepest that fits 110 KB of shared memory per CTA)       */
   int32_t bin_pipe;           /* binned SpMV row loop: -1 default (pipelined), 0 plain,
                                  1 pipelined                                                  */
-  int32_t reserved;
+  int32_t fuse_update;        /* x += alpha p and p = z + beta p: 0 default (1 with FP64
+                                 factors, 2 otherwise), 1 fused into the warp-ring
+                                 preconditioner kernel (x updated unit by unit as it goes; p
+                                 after its CTAs have waited, under the wait budget, for its
+                                 last CTA's beta; one cooperative launch), 2 a separate
+                                 kernel.  Fused only where the preconditioner is the warp-ring
+                                 kernel (block sizes up to 32); pc_handle_shape reports 1 or
+                                 2, what the graph runs                                       */
   double us_per_iteration;    /* time per CG iteration measured for this shape (0: none)     */
 } pc_shape;
 
 /* pc_autotune - kernel-shape autotuner of the single-system solve.  Sets up a handle for A
  * (block_size, prec), then for each candidate shape (natural row order: SpMV CTAs per SM
- * {2, 3, 4, 6, 8} x ring stages {2, 3, 4}; binned: row loop {plain, pipelined} x ring stages)
+ * {2, 3, 4, 6, 8} x ring stages {2, 3, 4}; binned: row loop {plain, pipelined} x ring stages;
+ * each with the default update, then the best of them with the other update: fused or a
+ * separate kernel)
  * runs `iterations` CG iterations twice (right-hand side of ones, tolerance 0) and times the
- * second run with CUDA events; max_trials > 0 caps the candidates.  The fastest shape is
+ * second run with CUDA events; max_trials > 0 caps the candidates before that last trial.  The fastest shape is
  * recorded for A's key (block size, precision, ceil(log2 n), round(log2(nnz / n)), SM count
  * of the current device); handles with that key use it when they build their loop graph (at
  * their first solve), and when the environment variable PC_TUNE_CACHE names a file it is

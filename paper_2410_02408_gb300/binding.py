@@ -51,10 +51,10 @@ class pc_solve_info(ctypes.Structure):
 
 class pc_shape(ctypes.Structure):
     _fields_ = [("spmv_ctas_per_sm", ctypes.c_int32), ("ring_stages", ctypes.c_int32), ("bin_pipe", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("us_per_iteration", ctypes.c_double)]
+                ("fuse_update", ctypes.c_int32), ("us_per_iteration", ctypes.c_double)]
 
     def to_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
     @classmethod
     def from_dict(cls, d):
@@ -62,6 +62,7 @@ class pc_shape(ctypes.Structure):
         s.spmv_ctas_per_sm = int(d.get("spmv_ctas_per_sm", 0))
         s.ring_stages = int(d.get("ring_stages", 0))
         s.bin_pipe = int(d.get("bin_pipe", -1))
+        s.fuse_update = int(d.get("fuse_update", 0))
         s.us_per_iteration = float(d.get("us_per_iteration", 0.0))
         return s
 

@@ -682,7 +682,11 @@ static pc_status pcg_solve_graph(pc_handle* h, const double* b, double* x, doubl
     PC_TRY(pc::cg_graph_create(&h->graph, h->L, h->A.row_ptr, h->A.col_idx, h->A.val, h->val_f32, h->minv,
                                h->fac_f32, h->gbx, h->gbx + vs, h->cg, h->cg + vs, h->cg + 2 * vs, h->cg + 3 * vs,
                                h->gpart, h->gscal, &bin,
-                               pc::CgShape{h->shape_used.spmv_ctas_per_sm, h->shape_used.ring_stages}, st));
+                               pc::CgShape{h->shape_used.spmv_ctas_per_sm, h->shape_used.ring_stages,
+                                           h->shape_used.fuse_update},
+                               st));
+    // report what the graph runs: 1 fused update, 2 separate update kernel
+    h->shape_used.fuse_update = pc::cg_graph_fused(h->graph) ? 1 : 2;
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   PC_TRY(cudaEventCreate(&e0));
@@ -903,11 +907,22 @@ pc_status pc_autotune(const pc_csr* A, int32_t block_size, int32_t prec, int32_t
     }
     if (max_trials > 0 && (size_t)max_trials < cands.size()) cands.resize((size_t)max_trials);
   }
+  // the candidates run the default update (fused with FP64 factors, a separate kernel
+  // otherwise); the best of them is also tried with the other one
+  const size_t n_fused = cands.size();
   pc_shape bestc;
   memset(&bestc, 0, sizeof(bestc));
   bestc.bin_pipe = -1;
   double best_ms = 1e300;
-  for (size_t i = 0; s == PC_OK && i < cands.size(); ++i) {
+  for (size_t i = 0; s == PC_OK && i <= cands.size(); ++i) {
+    if (i == cands.size()) {
+      // bestc.fuse_update is what its graph ran (1 fused, 2 separate); a system whose
+      // preconditioner cannot take the fused tail resolves 1 to 2 again, a repeat of bestc
+      if (i != n_fused || i == 0) break;
+      pc_shape c = bestc;
+      c.fuse_update = bestc.fuse_update == 1 ? 2 : 1;
+      cands.push_back(c);
+    }
     // a new loop graph (and, for another row loop, a new binned split) with this shape
     if (h->graph) {
       pc::cg_graph_destroy(h->graph);
@@ -924,7 +939,7 @@ pc_status pc_autotune(const pc_csr* A, int32_t block_size, int32_t prec, int32_t
     if (s == PC_OK) s = run(&ms);
     if (s == PC_OK && ms < best_ms) {
       best_ms = ms;
-      bestc = cands[i];
+      bestc = h->shape_used;   // the candidate as its graph resolved it (fuse_update 1 or 2)
     }
   }
   cudaStreamSynchronize(st);

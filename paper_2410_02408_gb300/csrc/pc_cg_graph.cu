@@ -36,10 +36,10 @@ struct CgScalars {
   int32_t it, max_iter;
   int32_t status;   // ST_* of the solve
   int32_t done;     // 1: stop all further work of this round
-  int32_t xupd;     // 1: x += alpha p due in kernel C
-  int32_t pupd;     // 1: p = z + beta p due in kernel C
+  int32_t xupd;     // 1: x += alpha p due in kernel C (or the fused tail of kernel B)
+  int32_t pupd;     // 1: p = z + beta p due in kernel C (or the fused tail of kernel B)
   int32_t cont;     // loop condition
-  int32_t pad;
+  uint32_t gen;     // bumped by kernel B's last CTA once beta and the flags are set (fused tail)
   unsigned int cnt[4];   // last-CTA counters of I/A, B, T
 };
 
@@ -179,6 +179,7 @@ struct CgArgs {
   cudaGraphConditionalHandle cond;
   int32_t in_graph;    // 0 when the body kernels are launched one by one (profiling mode)
   CgBinned bin;        // binned SpMV order (bin.perm null: natural order)
+  long long budget;    // clock64 cycles a CTA waits for kernel B's last CTA (fused tail)
 };
 
 // MODE 0 (I1): r = b - A x, sum b^2.  MODE 1 (A): q = A p, sum p q.  MODE 2 (T): r = b - A x, sum r^2.
@@ -295,7 +296,14 @@ template <typename VT, int MODE, bool BIN, bool PIPE = false>
 __device__ __forceinline__ void cg_spmv_body(const CgArgs& a, double* sm, int* is_last_p) {
   int& is_last = *is_last_p;
   CgScalars* S = a.s;
-  if (MODE == 1 && *(volatile int*)&S->done) return;
+  if (MODE == 1 && *(volatile int*)&S->done) {
+    // stopped by another kernel of the round (a timed-out wait): end the loop here
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      S->cont = 0;
+      if (a.in_graph) cudaGraphSetConditional(a.cond, 0u);
+    }
+    return;
+  }
   const VT* va = reinterpret_cast<const VT*>(a.va);
   const int64_t n = a.lay.n;
   const double* X = MODE == 1 ? a.p : a.x;
@@ -481,6 +489,47 @@ static void launch_spmv_mode(int grid, cudaStream_t st, const CgArgs& a) {
   else cg_spmv_kernel<VT, MODE><<<grid, 256, 0, st>>>(a);
 }
 
+// Shared epilogue of the preconditioner kernels (last CTA, thread 0): update the scalars and
+// the loop condition from rz = r.z and rr = r.r.
+template <bool RESTART>
+__device__ __forceinline__ void cg_precond_epilogue(const CgArgs& a, double rz, double rr, bool zero_b) {
+  CgScalars* S = a.s;
+  const double bnorm = sqrt(S->bb);
+  S->rr = rr;
+  if (zero_b) {
+    S->status = ST_OK;
+    S->done = 1;
+    S->cont = 0;
+    S->rr = 0.0;
+    return;
+  }
+  const bool conv = sqrt(rr) <= S->tol * bnorm;
+  int cont = 0;
+  if (RESTART) {
+    S->rho = rz;
+    S->xupd = 0;
+    S->pupd = 0;
+  } else {
+    S->it += 1;
+    S->beta = conv ? 0.0 : rz / S->rho;
+    if (!conv) S->rho = rz;
+  }
+  if (conv) {
+    S->pupd = 0;
+  } else if (S->it >= S->max_iter) {
+    S->status = ST_NO_CONV;
+    S->pupd = 0;
+  } else if (!(S->rho > 0.0) || !isfinite(S->rho)) {
+    S->status = ST_BREAKDOWN;
+    S->pupd = 0;
+  } else {
+    S->pupd = RESTART ? 0 : 1;
+    cont = 1;
+  }
+  S->cont = cont;
+  if (!RESTART && a.in_graph) cudaGraphSetConditional(a.cond, (unsigned)cont);
+}
+
 // RESTART (I2): z = M^{-1} r, p = z, rho, rr.  Otherwise (B): r -= alpha q, z = M^{-1} r.
 template <typename FT, int BS, bool RESTART>
 __global__ void __launch_bounds__(256) cg_precond_kernel(const CgArgs a) {
@@ -531,83 +580,9 @@ __global__ void __launch_bounds__(256) cg_precond_kernel(const CgArgs a) {
   double v[2] = {v0, v1};
   if (!cg_last_cta<2>(v, a.part, &S->cnt[1], sm, &is_last)) return;
   if (threadIdx.x != 0) return;
-  const double bnorm = sqrt(S->bb);
-  const double rz = v[0];
-  S->rr = v[1];
-  if (zero_b) {
-    S->status = ST_OK;
-    S->done = 1;
-    S->cont = 0;
-    S->rr = 0.0;
-    return;
-  }
-  const bool conv = sqrt(v[1]) <= S->tol * bnorm;
-  int cont = 0;
-  if (RESTART) {
-    S->rho = rz;
-    S->xupd = 0;
-    S->pupd = 0;
-  } else {
-    S->it += 1;
-    S->beta = conv ? 0.0 : rz / S->rho;
-    if (!conv) S->rho = rz;
-  }
-  if (conv) {
-    S->pupd = 0;
-  } else if (S->it >= S->max_iter) {
-    S->status = ST_NO_CONV;
-    S->pupd = 0;
-  } else if (!(S->rho > 0.0) || !isfinite(S->rho)) {
-    S->status = ST_BREAKDOWN;
-    S->pupd = 0;
-  } else {
-    S->pupd = RESTART ? 0 : 1;
-    cont = 1;
-  }
-  S->cont = cont;
-  if (!RESTART && a.in_graph) cudaGraphSetConditional(a.cond, (unsigned)cont);
+  cg_precond_epilogue<RESTART>(a, v[0], v[1], zero_b);
 }
 
-// Shared epilogue of the preconditioner kernels (last CTA, thread 0): update the scalars and
-// the loop condition from rz = r.z and rr = r.r.
-template <bool RESTART>
-__device__ __forceinline__ void cg_precond_epilogue(const CgArgs& a, double rz, double rr, bool zero_b) {
-  CgScalars* S = a.s;
-  const double bnorm = sqrt(S->bb);
-  S->rr = rr;
-  if (zero_b) {
-    S->status = ST_OK;
-    S->done = 1;
-    S->cont = 0;
-    S->rr = 0.0;
-    return;
-  }
-  const bool conv = sqrt(rr) <= S->tol * bnorm;
-  int cont = 0;
-  if (RESTART) {
-    S->rho = rz;
-    S->xupd = 0;
-    S->pupd = 0;
-  } else {
-    S->it += 1;
-    S->beta = conv ? 0.0 : rz / S->rho;
-    if (!conv) S->rho = rz;
-  }
-  if (conv) {
-    S->pupd = 0;
-  } else if (S->it >= S->max_iter) {
-    S->status = ST_NO_CONV;
-    S->pupd = 0;
-  } else if (!(S->rho > 0.0) || !isfinite(S->rho)) {
-    S->status = ST_BREAKDOWN;
-    S->pupd = 0;
-  } else {
-    S->pupd = RESTART ? 0 : 1;
-    cont = 1;
-  }
-  S->cont = cont;
-  if (!RESTART && a.in_graph) cudaGraphSetConditional(a.cond, (unsigned)cont);
-}
 
 // Staged preconditioner kernel: a CTA walks tiles of TU warp units; thread 0 streams each
 // tile's M^{-1} blocks and its r (and q) rows into shared memory with bulk asynchronous copies,
@@ -732,6 +707,14 @@ __global__ void __launch_bounds__(256) cg_precond_tma_kernel(const CgArgs a, con
 // ahead; the warp applies M^{-1} from shared memory.  Warps never wait for each other until
 // the final reduction.  All operands were written before this kernel started, so the copies
 // need no cross-proxy ordering.
+//
+// FUSED (kernel B without a kernel C): each warp also applies x += alpha p to its units' rows
+// as it goes (alpha is known when the kernel starts); after the reduction every CTA waits for
+// the last CTA's decision (beta and the update flag, published by a release add on S->gen that
+// each CTA polls with acquire under a clock64 budget), then applies p = z + beta p to the rows
+// its warps just preconditioned, whose z they wrote themselves.  The
+// grid must be co-resident (a cooperative launch).  A wait that runs out of budget records
+// ST_TIMEOUT and stops the solve (done, and the next SpMV ends the loop).
 struct CgWarpPlan {
   int ns;          // stages per warp
   int stage;       // bytes per stage
@@ -742,13 +725,17 @@ struct CgWarpPlan {
 };
 constexpr int CGW_WARPS = 8;
 
-template <typename FT, int BS, bool RESTART>
+template <typename FT, int BS, bool RESTART, bool FUSED = false>
 __global__ void __launch_bounds__(256) cg_precond_wp_kernel(const CgArgs a, const CgWarpPlan pl) {
+  static_assert(!(RESTART && FUSED), "the restart kernel has no kernel C to fuse");
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ double sm[64];
   __shared__ int is_last;
+  __shared__ unsigned gen0;
+  __shared__ int go;
   CgScalars* S = a.s;
   if (*(volatile int*)&S->done) return;
+  if (FUSED && threadIdx.x == 0) gen0 = ld_acquire_u32(&S->gen);   // before this CTA arrives
   const Layout& L = a.lay;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -764,6 +751,20 @@ __global__ void __launch_bounds__(256) cg_precond_wp_kernel(const CgArgs a, cons
   constexpr int NSLOT = (BS > 0 && BS <= 32) ? 1 : 2;
   const int nslot = NSLOT == 1 ? 1 : L.S;
   const uint32_t fb = (uint32_t)(uM * (int64_t)sizeof(FT));
+  // FUSED: x += alpha p unit by unit, the unit's x and p rows (lane l: rows l and l + 32) loaded
+  // one unit ahead with plain loads
+  const bool xup = FUSED && ld_volatile_i32(&S->xupd);
+  double xn[NSLOT], pn[NSLOT];
+  auto xp_load = [&](int64_t i) {
+#pragma unroll
+    for (int t = 0; t < NSLOT; ++t) {
+      const int64_t row = (u0 + i) * L.U + lane + 32 * t;
+      const bool ok = lane + 32 * t < L.U && row < L.n;
+      xn[t] = ok ? a.x[row] : 0.0;
+      pn[t] = ok ? a.p[row] : 0.0;
+    }
+  };
+  if (xup && nu > 0) xp_load(0);
   auto issue = [&](int64_t i, int st) {   // lane 0: unit u0 + i into stage st (= i mod ns)
     const int64_t u = u0 + i;
     const int64_t row0 = u * L.U;
@@ -796,6 +797,15 @@ __global__ void __launch_bounds__(256) cg_precond_wp_kernel(const CgArgs a, cons
       break;   // this warp's partials stay short; the status reports the failure
     }
     const int64_t u = u0 + i;
+    double xc[NSLOT], pc[NSLOT];
+    if (xup) {
+#pragma unroll
+      for (int t = 0; t < NSLOT; ++t) {
+        xc[t] = xn[t];
+        pc[t] = pn[t];
+      }
+      if (i + 1 < nu) xp_load(i + 1);
+    }
     const unsigned char* sbuf = ring + (size_t)st * pl.stage;
     const double* sr = reinterpret_cast<const double*>(sbuf + pl.off_r);
     const double* sq = reinterpret_cast<const double*>(sbuf + pl.off_q);
@@ -826,6 +836,13 @@ __global__ void __launch_bounds__(256) cg_precond_wp_kernel(const CgArgs a, cons
       v0 = fma(rv[t], zv[t], v0);
       v1 = fma(rv[t], rv[t], v1);
     }
+    if (xup) {
+#pragma unroll
+      for (int t = 0; t < NSLOT; ++t) {
+        const int64_t row = u * L.U + lane + 32 * t;
+        if (lane + 32 * t < L.U && row < L.n) a.x[row] = fma(alpha, pc[t], xc[t]);
+      }
+    }
     __syncwarp();   // every lane is done with the stage before it is refilled
     if (lane == 0 && i + pl.ns < nu) issue(i + pl.ns, st);
     if (++st == pl.ns) {
@@ -834,9 +851,50 @@ __global__ void __launch_bounds__(256) cg_precond_wp_kernel(const CgArgs a, cons
     }
   }
   double v[2] = {v0, v1};
-  if (!cg_last_cta<2>(v, a.part, &S->cnt[1], sm, &is_last)) return;
-  if (threadIdx.x != 0) return;
-  cg_precond_epilogue<RESTART>(a, v[0], v[1], zero_b);
+  const bool last = cg_last_cta<2>(v, a.part, &S->cnt[1], sm, &is_last);
+  if constexpr (!FUSED) {
+    if (!last || threadIdx.x != 0) return;
+    cg_precond_epilogue<RESTART>(a, v[0], v[1], zero_b);
+  } else {
+    if (threadIdx.x == 0) {
+      go = 1;
+      if (last) {
+        cg_precond_epilogue<false>(a, v[0], v[1], false);
+        red_release_add_u32(&S->gen, 1u);
+      } else {
+        const long long t0 = clock64();
+        while (ld_acquire_u32(&S->gen) == gen0) {
+          if (clock64() - t0 > a.budget) {
+            atomicCAS(&S->status, ST_OK, ST_TIMEOUT);
+            S->done = 1;
+            go = 0;
+            break;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (!go) return;
+    if (!ld_volatile_i32(&S->pupd)) return;
+    const double beta = *(volatile const double*)&S->beta;
+    // the rest of kernel C on this warp's rows (x was updated unit by unit above): 4 rows per
+    // lane in flight
+    const int64_t r0 = u0 * L.U, r1 = min(u1 * (int64_t)L.U, L.n);
+    for (int64_t base = r0 + lane; base < r1; base += 4 * 32) {
+      double pv[4], zv[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int64_t row = min(base + t * 32, r1 - 1);
+        pv[t] = a.p[row];
+        zv[t] = __ldcg(a.z + row);
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int64_t row = base + t * 32;
+        if (row < r1) a.p[row] = fma(beta, pv[t], zv[t]);
+      }
+    }
+  }
 }
 
 // C: x += alpha p (if due); p = z + beta p (if due).
@@ -883,6 +941,9 @@ struct CgGraph {
   CgPrecondPlan pl;
   bool wp;               // warp-pipelined preconditioner kernel usable
   CgWarpPlan wpl;
+  int fuse;              // shape's fuse_update: 0 default, 1 fused, 2 separate kernel C
+  bool fac_f32;          // FP32 factors (the default then keeps kernel C separate)
+  bool fused;            // kernel C runs as the fused tail of kernel B (decided at capture)
 };
 
 // Plan of the warp-pipelined preconditioner: NS stages of one warp unit each per warp, as
@@ -951,9 +1012,60 @@ static cudaError_t launch_precond(cudaStream_t cs, const CgGraph* g) {
   return cudaGetLastError();
 }
 
+// Kernel B with kernel C fused into its tail: a cooperative launch (every CTA resident, which
+// its wait for the last CTA needs).
+template <typename FT, int BS>
+static cudaError_t launch_precond_fused(cudaStream_t cs, const CgGraph* g) {
+  auto k = cg_precond_wp_kernel<FT, BS, false, true>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, g->wpl.smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3((unsigned)g->g_prec);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = (size_t)g->wpl.smem;
+  cfg.stream = cs;
+  cudaLaunchAttribute attr[1];
+  memset(attr, 0, sizeof(attr));
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, g->args, g->wpl);
+}
+
+// Kernel C is fused into kernel B when the shape asks for it (by default with FP64 factors:
+// on the 128^3 diffusion matrix at bs 16 the fused kernel was 2% faster with FP64 factors and
+// 1.3% slower with FP32 factors, whose issue-bound apply pays for the extra x update) and B
+// is the warp-ring kernel; its grid is then capped at the CTAs that can be resident at once
+// (the warp split adapts to any grid), which the wait for the last CTA needs.
+template <typename FT, int BS>
+static bool fused_fits(CgGraph* g) {
+  if (g->fuse == 2 || (g->fuse == 0 && g->fac_f32) || !g->wp) return false;
+  auto k = cg_precond_wp_kernel<FT, BS, false, true>;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, g->wpl.smem) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 256, (size_t)g->wpl.smem) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  int dev = 0, sms = 0, coop = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (!coop || occ < 1) return false;
+  if ((int64_t)g->g_prec > (int64_t)occ * sms) g->g_prec = occ * sms;
+  return true;
+}
+
 template <typename VT, typename FT, int BS>
-static cudaError_t capture_body(cudaStream_t cs, const CgGraph* g) {
+static cudaError_t capture_body(cudaStream_t cs, CgGraph* g) {
+  g->fused = fused_fits<FT, BS>(g);
   launch_spmv_mode<VT, 1>(g->g_spmv, cs, g->args);
+  if (g->fused) return launch_precond_fused<FT, BS>(cs, g);
   cudaError_t e = launch_precond<FT, BS, false>(cs, g);
   if (e != cudaSuccess) return e;
   cg_update_kernel<<<g->g_upd, 256, 0, cs>>>(g->args);
@@ -961,7 +1073,7 @@ static cudaError_t capture_body(cudaStream_t cs, const CgGraph* g) {
 }
 
 template <typename VT, typename FT>
-static cudaError_t capture_body_bs(cudaStream_t cs, const CgGraph* g) {
+static cudaError_t capture_body_bs(cudaStream_t cs, CgGraph* g) {
   switch (g->args.lay.bs) {
     case 8: return capture_body<VT, FT, 8>(cs, g);
     case 16: return capture_body<VT, FT, 16>(cs, g);
@@ -1038,6 +1150,8 @@ cudaError_t cg_graph_create(void** out, const Layout& L, const int32_t* rp, cons
     g->g_prec = (int)std::min<int64_t>((L.n_units + 7) / 8, (int64_t)sms * 8);
   }
   g->g_upd = (int)std::min<int64_t>((n + 1023) / 1024, (int64_t)sms * 8);
+  g->fuse = shape.fuse_update;
+  g->fac_f32 = fac_f32;
   if (g->g_spmv < 1) g->g_spmv = 1;
   if (g->g_prec < 1) g->g_prec = 1;
   if (g->g_upd < 1) g->g_upd = 1;
@@ -1056,6 +1170,7 @@ cudaError_t cg_graph_create(void** out, const Layout& L, const int32_t* rp, cons
   a.part = part;
   a.s = reinterpret_cast<CgScalars*>(scal);
   a.in_graph = 1;
+  a.budget = wait_budget_cycles();
   if (bin && bin->perm) a.bin = *bin;
   else memset(&a.bin, 0, sizeof(a.bin));
   cudaError_t e = cudaGraphCreate(&g->graph, 0);
@@ -1113,6 +1228,8 @@ cudaError_t cg_graph_create(void** out, const Layout& L, const int32_t* rp, cons
   return cudaSuccess;
 }
 
+bool cg_graph_fused(const void* h) { return h && static_cast<const CgGraph*>(h)->fused; }
+
 void cg_graph_destroy(void* h) {
   CgGraph* g = static_cast<CgGraph*>(h);
   if (!g) return;
@@ -1166,14 +1283,14 @@ static cudaError_t eager_round_t(CgGraph* g, cudaStream_t st, double* ms, int* i
     cudaEventRecord(ev[0], st);
     launch_spmv_mode<VT, 1>(eg.g_spmv, st, eg.args);
     cudaEventRecord(ev[1], st);
-    e = launch_precond<FT, BS, false>(st, &eg);
+    e = eg.fused ? launch_precond_fused<FT, BS>(st, &eg) : launch_precond<FT, BS, false>(st, &eg);
     cudaEventRecord(ev[2], st);
-    cg_update_kernel<<<eg.g_upd, 256, 0, st>>>(eg.args);
+    if (!eg.fused) cg_update_kernel<<<eg.g_upd, 256, 0, st>>>(eg.args);   // fused: no kernel C
     cudaEventRecord(ev[3], st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&cont, &eg.args.s->cont, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     float t;
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < (eg.fused ? 2 : 3); ++i) {   // fused: no update kernel to time
       cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
       ms[i] += t;
     }

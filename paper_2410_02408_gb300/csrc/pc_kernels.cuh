@@ -190,11 +190,14 @@ struct CgBinned {
 struct CgShape {
   int32_t spmv_ctas_per_sm;   // natural-order SpMV: resident CTAs per SM (1..8; default 4)
   int32_t ring_stages;        // warp-ring preconditioner: stages per warp (2..4; default the deepest that fits)
+  int32_t fuse_update;        // 0 default (fused where possible), 1 fused, 2 separate update kernel
 };
 cudaError_t cg_graph_create(void** out, const Layout& L, const int32_t* rp, const int32_t* ci, const void* va,
                             bool val_f32, const void* minv, bool fac_f32, const double* b, double* x, double* r,
                             double* z, double* p, double* q, double* part, void* scal, const CgBinned* bin,
                             const CgShape& shape, cudaStream_t st);
+// True if the loop graph runs the x / p update as the tail of the preconditioner kernel.
+bool cg_graph_fused(const void* g);
 
 // Row binning (pc_rowbin.cu): rows sorted by length inside windows of ROWBIN_W rows.
 constexpr int ROWBIN_W = 2048;

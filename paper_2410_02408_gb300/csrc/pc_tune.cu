@@ -5,7 +5,7 @@
 // Key: (block size, precision, ceil(log2 n), round(log2(nnz / n)), SM count of the current
 // device).  File: one flat JSON object per line, for example
 //   {"kind": "cg", "bs": 16, "prec": 1, "log2n": 21, "log2deg": 3, "sms": 152,
-//    "spmv_ctas_per_sm": 4, "ring_stages": 4, "bin_pipe": -1, "us_per_iteration": 99.6}
+//    "spmv_ctas_per_sm": 4, "ring_stages": 4, "bin_pipe": -1, "fuse_update": 0, "us_per_iteration": 99.6}
 //   {"kind": "batch", "n_sys": 512, "n_rows": 17886587, "nnz": 223800205, "prec": 1, "sms": 152,
 //    "ctas_per_sm": 2, "team_max": 8, "setup_kb": 70, "split": 4}
 // Lines that do not parse are skipped.  Host code only.
@@ -111,8 +111,10 @@ bool parse_cg(const std::map<std::string, std::string>& kv) {
       !get_int(kv, "ring_stages", &ring) || !get_int(kv, "bin_pipe", &pipe))
     return false;
   get_num(kv, "us_per_iteration", &us);
+  int64_t fuse = 0;   // absent in files written before the field existed: the default
+  if (kv.count("fuse_update") && !get_int(kv, "fuse_update", &fuse)) return false;
   if (bs < 1 || bs > 64 || prec < 0 || prec > 2 || ctas < 0 || ctas > 8 || ring < 0 || ring > 4 || ring == 1 ||
-      pipe < -1 || pipe > 1)
+      pipe < -1 || pipe > 1 || fuse < 0 || fuse > 2)
     return false;
   TuneKey k{(int32_t)bs, (int32_t)prec, (int32_t)l2n, (int32_t)l2d, (int32_t)sms};
   pc_shape s;
@@ -120,6 +122,7 @@ bool parse_cg(const std::map<std::string, std::string>& kv) {
   s.spmv_ctas_per_sm = (int32_t)ctas;
   s.ring_stages = (int32_t)ring;
   s.bin_pipe = (int32_t)pipe;
+  s.fuse_update = (int32_t)fuse;
   s.us_per_iteration = us;
   put_cg_locked(k, s);
   return true;
@@ -208,7 +211,8 @@ extern "C" {
 pc_status pc_tune_set(int32_t block_size, int32_t prec, int64_t n, int64_t nnz, const pc_shape* shape) {
   if (!shape || block_size < 1 || block_size > 64 || prec < 0 || prec > 2 || n < 1 || nnz < 0) return PC_ERR_INVALID_ARG;
   if (shape->spmv_ctas_per_sm < 0 || shape->spmv_ctas_per_sm > 8 || shape->ring_stages < 0 || shape->ring_stages > 4 ||
-      shape->ring_stages == 1 || shape->bin_pipe < -1 || shape->bin_pipe > 1)
+      shape->ring_stages == 1 || shape->bin_pipe < -1 || shape->bin_pipe > 1 || shape->fuse_update < 0 ||
+      shape->fuse_update > 2)
     return PC_ERR_INVALID_ARG;
   pc::tune_record(pc::tune_key(block_size, prec, n, nnz), *shape);
   return PC_OK;
@@ -237,9 +241,10 @@ pc_status pc_tune_save(const char* path) {
     for (const pc::CgEntry& e : pc::g_cg) {
       snprintf(buf, sizeof buf,
                "{\"kind\": \"cg\", \"bs\": %d, \"prec\": %d, \"log2n\": %d, \"log2deg\": %d, \"sms\": %d, "
-               "\"spmv_ctas_per_sm\": %d, \"ring_stages\": %d, \"bin_pipe\": %d, \"us_per_iteration\": %.6g}\n",
+               "\"spmv_ctas_per_sm\": %d, \"ring_stages\": %d, \"bin_pipe\": %d, \"fuse_update\": %d, "
+               "\"us_per_iteration\": %.6g}\n",
                e.key.bs, e.key.prec, e.key.log2n, e.key.log2deg, e.key.sms, e.shape.spmv_ctas_per_sm,
-               e.shape.ring_stages, e.shape.bin_pipe, e.shape.us_per_iteration);
+               e.shape.ring_stages, e.shape.bin_pipe, e.shape.fuse_update, e.shape.us_per_iteration);
       out += buf;
     }
   }

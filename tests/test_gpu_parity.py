@@ -317,6 +317,24 @@ def test_pcg_bounded_wait_times_out_and_recovers(pc):
     assert info["status"] == 0
 
 
+def test_fused_update_wait_times_out_and_recovers(pc):
+    # the graph engine's bounded device-side wait: CTAs of the preconditioner kernel wait for
+    # its last CTA before the fused x / p update; a one-cycle budget makes the first CTAs give up
+    pc.set_cg_engine("default")
+    A = W.poisson2d(64)   # 128 warp units: 16 CTAs, so some CTA always waits
+    b = W.rhs(A.n, 0)
+    pc.set_wait_budget(1)
+    try:
+        x, info = pc.pcg(A, b, 16, check=False)
+    finally:
+        pc.set_wait_budget(0)
+    assert info["status"] == 5
+    x, info = pc.pcg(A, b, 16)
+    assert info["status"] == 0
+    o = oracle.pcg(A, b, 16, 1e-10)
+    assert rel(x.cpu().numpy(), o["x"]) <= 1e-10
+
+
 def test_pcg_handle_reuse_and_warm_restart(pc, engine):
     A = W.diffusion3d(12, 1.0)
     b = W.rhs(A.n, 0)

@@ -10,7 +10,7 @@ import pytest
 import paper_2410_02408_gb300 as pc
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-SHAPE = {"spmv_ctas_per_sm": 3, "ring_stages": 2, "bin_pipe": -1, "us_per_iteration": 97.5}
+SHAPE = {"spmv_ctas_per_sm": 3, "ring_stages": 2, "bin_pipe": -1, "fuse_update": 2, "us_per_iteration": 97.5}
 
 
 def _sms(tmp_path):
@@ -75,6 +75,7 @@ def test_load_skips_malformed_lines(tmp_path):
         '{"kind": "cg", "bs": 8}',                                    # missing fields
         good.replace('"ring_stages": 3', '"ring_stages": 1'),        # out of range
         good.replace('"bs": 8', '"bs": 8.5'),                        # not an integer
+        good.replace('"bin_pipe": -1', '"bin_pipe": -1, "fuse_update": 3'),   # out of range
         '{"kind": "other", "x": 1}',
         good,
         batch,
@@ -82,7 +83,9 @@ def test_load_skips_malformed_lines(tmp_path):
     ]) + "\n")
     assert pc.tune_load(str(path)) == 2
     got = pc.tune_get(8, "fp32", 4096, 4 * 4096)
-    assert got == {"spmv_ctas_per_sm": 6, "ring_stages": 3, "bin_pipe": -1, "us_per_iteration": 12.5}
+    # a line without fuse_update (files written before the field existed) takes the default 0
+    assert got == {"spmv_ctas_per_sm": 6, "ring_stages": 3, "bin_pipe": -1, "fuse_update": 0,
+                   "us_per_iteration": 12.5}
     # the batch line is kept and written back
     out = tmp_path / "again.jsonl"
     pc.tune_save(str(out))
@@ -94,7 +97,8 @@ def test_invalid_arguments(tmp_path):
     with pytest.raises(pc.PcError) as ei:
         pc.tune_set(16, "fp32", 1000, 7000, dict(SHAPE, ring_stages=1))
     assert ei.value.name == "invalid_arg"
-    for bad in (dict(SHAPE, spmv_ctas_per_sm=9), dict(SHAPE, bin_pipe=2), dict(SHAPE, ring_stages=5)):
+    for bad in (dict(SHAPE, spmv_ctas_per_sm=9), dict(SHAPE, bin_pipe=2), dict(SHAPE, ring_stages=5),
+                dict(SHAPE, fuse_update=3), dict(SHAPE, fuse_update=-1)):
         with pytest.raises(pc.PcError):
             pc.tune_set(16, "fp32", 1000, 7000, bad)
     with pytest.raises(pc.PcError):
