@@ -514,8 +514,12 @@ typedef struct {
   int32_t spmv_ctas_per_sm;   /* natural-order SpMV: resident CTAs per SM, 1..8 (default 4)  */
   int32_t ring_stages;        /* warp-ring preconditioner: stages per warp, 2..4 (default:
                                  the deepest that fits 110 KB of shared memory per CTA)       */
-  int32_t bin_pipe;           /* binned SpMV row loop: -1 default (pipelined), 0 plain,
-                                 1 pipelined                                                  */
+  int32_t bin_pipe;           /* binned SpMV row loop: -1 default (2), 0 plain, 1 pipelined,
+                                 2 pipelined with the groups of rows up to 64 entries read
+                                 from a sliced copy built at the first solve (entry k of the
+                                 group's 32 rows contiguous; 8 or 12 bytes per entry of those
+                                 rows, padded to each group's longest row); with column
+                                 segments 2 runs as 1                                         */
   int32_t fuse_update;        /* x += alpha p and p = z + beta p: 0 default (1 with FP64
                                  factors, 2 otherwise), 1 fused into the warp-ring
                                  preconditioner kernel (x updated unit by unit as it goes; p
@@ -529,7 +533,7 @@ typedef struct {
 
 /* pc_autotune - kernel-shape autotuner of the single-system solve.  Sets up a handle for A
  * (block_size, prec), then for each candidate shape (natural row order: SpMV CTAs per SM
- * {2, 3, 4, 6, 8} x ring stages {2, 3, 4}; binned: row loop {plain, pipelined} x ring stages;
+ * {2, 3, 4, 6, 8} x ring stages {2, 3, 4}; binned: row loop {plain, pipelined, sliced} x ring stages;
  * each with the default update, then the best of them with the other update: fused or a
  * separate kernel)
  * runs `iterations` CG iterations twice (right-hand side of ones, tolerance 0) and times the

@@ -49,8 +49,11 @@ struct pc_handle {
   int32_t* gmax;         // with perm: longest row of each 32-row group
   int32_t* bnd;          // with perm: column-segment entry boundaries by binned position
   double* spart;         // with nseg > 1: partial sums between segment sweeps
+  int32_t* scol;         // row loop 2: sliced copy of the one-lane-per-row groups (columns)
+  void* sval;            // ... (values, as the CSR's)
+  int64_t* sincl;        // ... (inclusive prefix of the slab sizes, per group)
   int32_t nseg;          // column segments of the binned SpMV
-  int32_t bin_pipe;      // the binned SpMV uses the pipelined row loop
+  int32_t bin_pipe;      // row loop of the binned SpMV: 0 plain, 1 pipelined, 2 pipelined + sliced
   int perm_checked;      // the row-length statistics have been taken
   double* gpart;         // per-CTA partials
   void* gscal;           // CG scalars
@@ -260,6 +263,9 @@ pc_status pc_destroy(pc_handle* h) {
   dfree(h->gmax);
   dfree(h->bnd);
   dfree(h->spart);
+  dfree(h->scol);
+  dfree(h->sval);
+  dfree(h->sincl);
   dfree(h->gpart);
   dfree(h->gscal);
   dfree(h->ref_ws);
@@ -535,19 +541,22 @@ static pc_status ensure_cg_workspace(pc_handle* h, cudaStream_t st) {
 // forces a count.
 static int col_segments() { return g_col_segments >= 1 ? g_col_segments : 1; }
 
-// Row loop of the binned SpMV: plain (column indices and values, then the gathers; 4 CTAs
-// per SM) or pipelined (the next round's column indices load during the gathers; 2 CTAs per
-// SM).  On the 8M-row power-law matrix the pipelined loop measured 1659 against 1694 us per
-// SpMV, so it is the default; PC_BIN_SPMV=pipe|plain overrides it.
-constexpr bool kBinPipeDefault = true;
+// Row loop of the binned SpMV: 0 plain (column indices and values, then the gathers; 4 CTAs
+// per SM), 1 pipelined (the next round's column indices load during the gathers; 2 CTAs per
+// SM), 2 pipelined with the one-lane-per-row groups read from a sliced copy (coalesced index
+// and value loads; the copy takes 8 or 12 bytes per entry of those groups, built at the
+// first solve).  On the 8M-row power-law matrix the pipelined loop measured 1659 against
+// 1694 us per SpMV for the plain one.  PC_BIN_SPMV=plain|pipe|sliced overrides the choice.
+constexpr int kBinLoopDefault = 2;
 
-// PC_BIN_SPMV first, then the handle's launch shape (bin_pipe 0 / 1), then the default.
-static bool bin_spmv_pipelined(int shape_pipe) {
+// PC_BIN_SPMV first, then the handle's launch shape (bin_pipe 0 / 1 / 2), then the default.
+static int bin_spmv_loop(int shape_pipe) {
   const char* e = getenv("PC_BIN_SPMV");
-  if (e && strcmp(e, "pipe") == 0) return true;
-  if (e && strcmp(e, "plain") == 0) return false;
-  if (shape_pipe == 0 || shape_pipe == 1) return shape_pipe == 1;
-  return kBinPipeDefault;
+  if (e && strcmp(e, "sliced") == 0) return 2;
+  if (e && strcmp(e, "pipe") == 0) return 1;
+  if (e && strcmp(e, "plain") == 0) return 0;
+  if (shape_pipe >= 0 && shape_pipe <= 2) return shape_pipe;
+  return kBinLoopDefault;
 }
 
 static void release_binning(pc_handle* h) {
@@ -558,6 +567,12 @@ static void release_binning(pc_handle* h) {
   dfree(h->gmax);
   dfree(h->bnd);
   dfree(h->spart);
+  dfree(h->scol);
+  dfree(h->sval);
+  dfree(h->sincl);
+  h->scol = nullptr;
+  h->sval = nullptr;
+  h->sincl = nullptr;
   h->perm = nullptr;
   h->gsplit = nullptr;
   h->gmax = nullptr;
@@ -584,7 +599,7 @@ static pc_status choose_row_order(pc_handle* h, cudaStream_t st) {
     bin = (double)waste > 1.25 * (double)h->A.nnz;
   }
   if (!bin) return PC_OK;
-  h->bin_pipe = bin_spmv_pipelined(h->shape_used.bin_pipe) ? 1 : 0;
+  h->bin_pipe = bin_spmv_loop(h->shape_used.bin_pipe);
   const int n_warps = pc::cg_spmv_bin_warps(h->bin_pipe != 0);
   const int64_t stride = vec_stride(n);
   const int64_t n_groups = (n + 31) / 32;
@@ -639,6 +654,31 @@ static pc_status choose_row_order(pc_handle* h, cudaStream_t st) {
     }
   }
   h->nseg = nseg;
+  if (h->bin_pipe == 2 && nseg == 1) {
+    // sliced copy of the one-lane-per-row groups
+    s = dalloc(&h->sincl, sizeof(int64_t) * (size_t)n_groups);
+    int64_t total = 0;
+    cudaError_t e2 = cudaSuccess;
+    if (s == PC_OK) e2 = pc::row_sliced_sizes(n, h->gmax, h->sincl, st);
+    if (s == PC_OK && e2 == cudaSuccess)
+      e2 = cudaMemcpyAsync(&total, h->sincl + n_groups - 1, sizeof(total), cudaMemcpyDeviceToHost, st);
+    if (s == PC_OK && e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
+    if (s == PC_OK && e2 == cudaSuccess) {
+      const size_t vb = h->val_f32 ? sizeof(float) : sizeof(double);
+      s = dalloc(&h->scol, sizeof(int32_t) * (size_t)(total > 0 ? total : 1));
+      if (s == PC_OK) s = dalloc(&h->sval, vb * (size_t)(total > 0 ? total : 1));
+      if (s == PC_OK)
+        e2 = pc::row_sliced_fill(n, h->bnd, stride, h->A.col_idx, h->A.val, h->val_f32 != 0, h->gmax, h->sincl,
+                                 h->scol, h->sval, st);
+    }
+    if (s == PC_OK && e2 != cudaSuccess) s = from_cuda(e2);
+    if (s != PC_OK) {
+      release_binning(h);
+      return s;
+    }
+  } else if (h->bin_pipe == 2) {
+    h->bin_pipe = 1;   // segments: the CSR walk
+  }
   return PC_OK;
 }
 
@@ -678,6 +718,9 @@ static pc_status pcg_solve_graph(pc_handle* h, const double* b, double* x, doubl
       bin.spart = h->spart;
       bin.nseg = h->nseg;
       bin.pipe = h->bin_pipe;
+      bin.scol = h->scol;
+      bin.sval = h->sval;
+      bin.sincl = h->sincl;
     }
     PC_TRY(pc::cg_graph_create(&h->graph, h->L, h->A.row_ptr, h->A.col_idx, h->A.val, h->val_f32, h->minv,
                                h->fac_f32, h->gbx, h->gbx + vs, h->cg, h->cg + vs, h->cg + 2 * vs, h->cg + 3 * vs,
@@ -891,7 +934,7 @@ pc_status pc_autotune(const pc_csr* A, int32_t block_size, int32_t prec, int32_t
     memset(&c, 0, sizeof(c));
     c.bin_pipe = -1;
     if (h->perm) {
-      for (int pipe : {1, 0})
+      for (int pipe : {2, 1, 0})
         for (int ring : {4, 3, 2}) {
           c.bin_pipe = pipe;
           c.ring_stages = ring;

@@ -165,6 +165,53 @@ __device__ __forceinline__ double cg_range_pipe(const int32_t* __restrict__ ci, 
   return acc;
 }
 
+// cg_range_pipe<VT, 1> over the sliced copy of a one-lane-per-row group: entry k of the lane's
+// row sits at base + 32 k + lane (the group's slab holds lim entries per lane, the rows'
+// entries in storage order, padded past each row's end), so each load instruction of the
+// warp reads one contiguous run of 32 entries instead of one cache line per lane.  Same
+// products in the same order as cg_range_pipe<VT, 1>.
+template <typename VT>
+__device__ __forceinline__ double cg_range_sliced(const int32_t* __restrict__ sc, const VT* __restrict__ sv,
+                                                  const double* __restrict__ x, int64_t base, int32_t cnt,
+                                                  int32_t lim, uint64_t ps, uint64_t pk) {
+  const int lane = threadIdx.x & 31;
+  const int32_t* __restrict__ cp = sc + base + lane;
+  const VT* __restrict__ vp = sv + base + lane;
+  double acc = 0.0;
+  if (lim > 0) {
+    int32_t c[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) c[t] = ld_hint(cp + 32 * min(t, lim - 1), ps);
+    for (int32_t k0 = 0; k0 < lim; k0 += 8) {
+      double xv[8];
+      VT v[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        xv[t] = ld_gather_hint(x + c[t], pk);
+        v[t] = ld_hint(vp + 32 * min(k0 + t, lim - 1), ps);
+      }
+      const int32_t k1 = k0 + 8;
+      int32_t cn[8];
+      if (k1 < lim) {   // warp-uniform
+#pragma unroll
+        for (int t = 0; t < 8; ++t) cn[t] = ld_hint(cp + 32 * min(k1 + t, lim - 1), ps);
+      }
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        if (k0 + t < lim) {   // warp-uniform
+          const double pr = fma(from_ft(v[t]), xv[t], acc);
+          acc = (k0 + t < cnt) ? pr : acc;
+        }
+      }
+      if (k1 < lim) {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) c[t] = cn[t];
+      }
+    }
+  }
+  return acc;
+}
+
 struct CgArgs {
   Layout lay;
   const int32_t* rp;
@@ -337,8 +384,10 @@ __device__ __forceinline__ void cg_spmv_body(const CgArgs& a, double* sm, int* i
       // ends with two (the permutation, then the vector entry it addresses).  A row item (< 0)
       // gives every lane that row's range and index; a group item gives each lane its row's
       // range and index and the group's longest row.
-      auto item_bounds = [&](int32_t item, int32_t& s_, int32_t& c_, int32_t& gm_, int32_t& r_) {
+      const bool sliced = B.scol != nullptr && nseg == 1;
+      auto item_bounds = [&](int32_t item, int32_t& s_, int32_t& c_, int32_t& gm_, int32_t& r_, int64_t& so_) {
         r_ = 0;
+        so_ = 0;
         if (item < 0) {
           const int64_t pos = -(int64_t)item - 1;
           s_ = ld_hint(lo_b + pos, ps);
@@ -351,16 +400,19 @@ __device__ __forceinline__ void cg_spmv_body(const CgArgs& a, double* sm, int* i
           c_ = idx < n ? ld_hint(hi_b + idx, ps) - s_ : 0;
           gm_ = ld_hint(B.gmax + item, ps);
           if (last && idx < n) r_ = ld_hint(B.perm + idx, ps);
+          if (sliced) so_ = ld_hint(B.sincl + item, ps);   // the slab ends there (one-lane groups)
         }
       };
       int32_t item = g0 < g1 ? ld_hint(B.items + g0, ps) : 0;            // warp-uniform
       int32_t item1 = g0 + 1 < g1 ? ld_hint(B.items + g0 + 1, ps) : 0;
       int32_t s_c = 0, c_c = 0, gm_c = 0, r_c = 0;
-      if (g0 < g1) item_bounds(item, s_c, c_c, gm_c, r_c);
+      int64_t so_c = 0;
+      if (g0 < g1) item_bounds(item, s_c, c_c, gm_c, r_c, so_c);
       for (int32_t it = g0; it < g1; ++it) {
         const int32_t item2 = it + 2 < g1 ? ld_hint(B.items + it + 2, ps) : 0;
         int32_t s_n = 0, c_n = 0, gm_n = 0, r_n = 0;
-        if (it + 1 < g1) item_bounds(item1, s_n, c_n, gm_n, r_n);
+        int64_t so_n = 0;
+        if (it + 1 < g1) item_bounds(item1, s_n, c_n, gm_n, r_n, so_n);
         if (item < 0) {
           // one row of a group of hub rows: the whole warp on it
           const int64_t pos = -(int64_t)item - 1;
@@ -379,7 +431,13 @@ __device__ __forceinline__ void cg_spmv_body(const CgArgs& a, double* sm, int* i
           const int32_t s0 = s_c, cnt0 = c_c;
           if (gm_c <= 64) {
             const double init = (!first && valid) ? __ldcg(B.spart + idx) : 0.0;
-            const double v = cg_range<VT, 1, PIPE>(a.ci, va, X, s0, cnt0, __reduce_max_sync(FULL, cnt0), init, ps, pk);
+            const int32_t lim = __reduce_max_sync(FULL, cnt0);
+            double v;
+            if (PIPE && sliced)   // slab of 32 x gm_c entries ending at so_c; every cnt0 <= gm_c
+              v = cg_range_sliced<VT>(B.scol, reinterpret_cast<const VT*>(B.sval), X, so_c - 32ll * gm_c, cnt0, gm_c,
+                                      ps, pk);
+            else
+              v = cg_range<VT, 1, PIPE>(a.ci, va, X, s0, cnt0, lim, init, ps, pk);
             if (valid) {
               if (last) finish_w(r_c, v, w_c);
               else __stcg(B.spart + idx, v);
@@ -410,6 +468,7 @@ __device__ __forceinline__ void cg_spmv_body(const CgArgs& a, double* sm, int* i
         c_c = c_n;
         gm_c = gm_n;
         r_c = r_n;
+        so_c = so_n;
       }
     }
   } else {

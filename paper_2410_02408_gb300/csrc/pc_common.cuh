@@ -120,6 +120,11 @@ __device__ __forceinline__ int32_t ld_hint(const int32_t* p, uint64_t pol) {
   asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
   return v;
 }
+__device__ __forceinline__ int64_t ld_hint(const int64_t* p, uint64_t pol) {
+  int64_t v;
+  asm("ld.global.nc.L2::cache_hint.s64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
+  return v;
+}
 __device__ __forceinline__ float ld_hint(const float* p, uint64_t pol) {
   float v;
   asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));

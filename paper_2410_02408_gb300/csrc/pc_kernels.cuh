@@ -184,6 +184,12 @@ struct CgBinned {
   double* spart;           // [n] partial sums between segment sweeps (nseg > 1), by position
   int32_t nseg;            // column segments swept one after another (1: whole rows)
   int32_t pipe;            // 1: pipelined row loop (gsplit sized for cg_spmv_bin_warps(true))
+  // Sliced copy of the one-lane-per-row groups (null: none; used with nseg 1 and the
+  // pipelined loop): group g (longest row gmax[g] <= 64) holds 32 * gmax[g] entries ending at
+  // sincl[g], entry k of the row at position 32 g + l at 32 k + l, padded past the row's end.
+  const int32_t* scol;
+  const void* sval;        // VT, as the CSR values
+  const int64_t* sincl;    // [ceil(n/32)] inclusive prefix of the slab sizes
 };
 // bin: null (or bin->perm null) for the natural row order.
 // Launch shape of the graph engine's loop kernels (0: the default of each field).
@@ -222,6 +228,14 @@ cudaError_t row_bin_items(int64_t n, const int32_t* rp, const int32_t* perm, con
 // int, zeroed by the caller) is set when some row's columns are not strictly increasing.
 cudaError_t row_seg_bounds(int64_t n, const int32_t* rp, const int32_t* ci, const int32_t* perm, int nseg,
                            int64_t seg_cols, int64_t stride, int32_t* bnd, int* unsorted, cudaStream_t st);
+// Sliced copy of the one-lane-per-row groups (CgBinned::scol): step 1 writes the inclusive
+// prefix of the slab sizes (32 * gmax[g] entries for gmax[g] <= 64, else 0) to sincl
+// [ceil(n/32)]; step 2 fills scol / sval (sincl's last entry of each, VT = float when
+// val_f32) from the whole-row bounds bnd (nseg 1): padding entries get column 0 and value 0.
+cudaError_t row_sliced_sizes(int64_t n, const int32_t* gmax, int64_t* sincl, cudaStream_t st);
+cudaError_t row_sliced_fill(int64_t n, const int32_t* bnd, int64_t stride, const int32_t* ci, const void* va,
+                            bool val_f32, const int32_t* gmax, const int64_t* sincl, int32_t* scol, void* sval,
+                            cudaStream_t st);
 // Warps of the binned SpMV grid (the number of work items of its split), plain or pipelined.
 int cg_spmv_bin_warps(bool pipe);
 void cg_graph_destroy(void* g);

@@ -307,4 +307,63 @@ cudaError_t row_bin_build(int64_t n, const int32_t* rp, int32_t* perm, cudaStrea
   return cudaGetLastError();
 }
 
+
+// Sliced copy of the one-lane-per-row groups.  Slab sizes: 32 * gmax[g] entries for groups
+// whose longest row has at most 64 entries, 0 for the others (they keep the CSR walk).
+__global__ void sliced_size_kernel(int64_t m, const int32_t* __restrict__ gmax, int64_t* __restrict__ size) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < m; g += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t gm = __ldg(gmax + g);
+    size[g] = gm <= 64 ? 32ll * gm : 0;
+  }
+}
+
+cudaError_t row_sliced_sizes(int64_t n, const int32_t* gmax, int64_t* sincl, cudaStream_t st) {
+  const int64_t m = (n + 31) / 32;
+  int64_t grid = (m + 255) / 256;
+  if (grid > (int64_t)device_sms() * 16) grid = (int64_t)device_sms() * 16;
+  if (grid < 1) grid = 1;
+  sliced_size_kernel<<<(unsigned)grid, 256, 0, st>>>(m, gmax, sincl);
+  cost_scan_kernel<<<1, 1024, 0, st>>>(m, sincl);
+  return cudaGetLastError();
+}
+
+// One warp per group with a slab: lane l copies the row at binned position 32 g + l, entry k to
+// 32 k + l of the slab (the stores of one k are one contiguous run), padding past the row's
+// end (and for positions past n) with column 0 and value 0.
+template <typename VT>
+__global__ void sliced_fill_kernel(int64_t n, const int32_t* __restrict__ bnd, int64_t stride,
+                                   const int32_t* __restrict__ ci, const VT* __restrict__ va,
+                                   const int32_t* __restrict__ gmax, const int64_t* __restrict__ sincl,
+                                   int32_t* __restrict__ scol, VT* __restrict__ sval) {
+  const int lane = threadIdx.x & 31;
+  const int64_t m = (n + 31) / 32;
+  for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < m;
+       g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int32_t gm = __ldg(gmax + g);
+    if (gm > 64 || gm <= 0) continue;   // warp-uniform
+    const int64_t base = __ldg(sincl + g) - 32ll * gm;
+    const int64_t pos = g * 32 + lane;
+    const int32_t lo = pos < n ? __ldg(bnd + pos) : 0;
+    const int32_t cnt = pos < n ? __ldg(bnd + stride + pos) - lo : 0;
+    for (int32_t k = 0; k < gm; ++k) {
+      const bool ok = k < cnt;
+      scol[base + 32ll * k + lane] = ok ? __ldg(ci + lo + k) : 0;
+      sval[base + 32ll * k + lane] = ok ? __ldg(va + lo + k) : VT(0);
+    }
+  }
+}
+
+cudaError_t row_sliced_fill(int64_t n, const int32_t* bnd, int64_t stride, const int32_t* ci, const void* va,
+                            bool val_f32, const int32_t* gmax, const int64_t* sincl, int32_t* scol, void* sval,
+                            cudaStream_t st) {
+  const unsigned grid = (unsigned)group_grid(n);
+  if (val_f32)
+    sliced_fill_kernel<float><<<grid, 256, 0, st>>>(n, bnd, stride, ci, static_cast<const float*>(va), gmax, sincl,
+                                                    scol, static_cast<float*>(sval));
+  else
+    sliced_fill_kernel<double><<<grid, 256, 0, st>>>(n, bnd, stride, ci, static_cast<const double*>(va), gmax,
+                                                     sincl, scol, static_cast<double*>(sval));
+  return cudaGetLastError();
+}
+
 }  // namespace pc

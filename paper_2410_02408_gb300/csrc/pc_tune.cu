@@ -114,7 +114,7 @@ bool parse_cg(const std::map<std::string, std::string>& kv) {
   int64_t fuse = 0;   // absent in files written before the field existed: the default
   if (kv.count("fuse_update") && !get_int(kv, "fuse_update", &fuse)) return false;
   if (bs < 1 || bs > 64 || prec < 0 || prec > 2 || ctas < 0 || ctas > 8 || ring < 0 || ring > 4 || ring == 1 ||
-      pipe < -1 || pipe > 1 || fuse < 0 || fuse > 2)
+      pipe < -1 || pipe > 2 || fuse < 0 || fuse > 2)
     return false;
   TuneKey k{(int32_t)bs, (int32_t)prec, (int32_t)l2n, (int32_t)l2d, (int32_t)sms};
   pc_shape s;
@@ -211,7 +211,7 @@ extern "C" {
 pc_status pc_tune_set(int32_t block_size, int32_t prec, int64_t n, int64_t nnz, const pc_shape* shape) {
   if (!shape || block_size < 1 || block_size > 64 || prec < 0 || prec > 2 || n < 1 || nnz < 0) return PC_ERR_INVALID_ARG;
   if (shape->spmv_ctas_per_sm < 0 || shape->spmv_ctas_per_sm > 8 || shape->ring_stages < 0 || shape->ring_stages > 4 ||
-      shape->ring_stages == 1 || shape->bin_pipe < -1 || shape->bin_pipe > 1 || shape->fuse_update < 0 ||
+      shape->ring_stages == 1 || shape->bin_pipe < -1 || shape->bin_pipe > 2 || shape->fuse_update < 0 ||
       shape->fuse_update > 2)
     return PC_ERR_INVALID_ARG;
   pc::tune_record(pc::tune_key(block_size, prec, n, nnz), *shape);

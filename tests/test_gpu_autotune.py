@@ -65,7 +65,7 @@ def test_autotune_binned_rows(pc):
     try:
         A = W.powerlaw_spd(n=30000, seed=5, w_max=500, cap=400, dtype=np.float64)
         best = pc.autotune(A, 32, "fp32", iterations=20)
-        assert best["bin_pipe"] in (0, 1) and best["ring_stages"] in (2, 3, 4)
+        assert best["bin_pipe"] in (0, 1, 2) and best["ring_stages"] in (2, 3, 4)
         b = W.rhs(A.n, 0)
         H = pc.setup(A, 32, prec="fp64")   # another precision: no recorded shape, defaults
         x, info = H.pcg(b, tol=1e-10)
@@ -73,7 +73,7 @@ def test_autotune_binned_rows(pc):
         H.destroy()
         o = oracle.pcg(A, b, 32, 1e-10)
         assert rel(x.cpu().numpy(), o["x"]) <= 1e-10
-        for pipe in (0, 1):
+        for pipe in (0, 1, 2):
             pc.tune_set(32, "fp64", A.n, A.nnz, {"spmv_ctas_per_sm": 0, "ring_stages": 2, "bin_pipe": pipe})
             H = pc.setup(A, 32, prec="fp64")
             x, info = H.pcg(b, tol=1e-10)

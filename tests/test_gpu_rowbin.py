@@ -122,12 +122,14 @@ def test_unsorted_columns_are_rejected(pc, powerlaw):
     assert np.linalg.norm(x - r["x"]) <= 1e-10 * np.linalg.norm(r["x"])
 
 
-@pytest.mark.parametrize("loop", ["pipe", "plain"])
+@pytest.mark.parametrize("loop", ["sliced", "pipe", "plain"])
 @pytest.mark.parametrize("segs", [1, 3])
 def test_both_row_loops_match_oracle(pc, powerlaw, segs, loop, monkeypatch):
-    """Both binned row loops give the oracle's answer, whole-row and in column segments: the
-    pipelined one (next round's column indices loaded during the gathers, 2 CTAs per SM, the
-    default) and the plain one (4 CTAs per SM), each with its own balanced split."""
+    """Every binned row loop gives the oracle's answer, whole-row and in column segments: the
+    pipelined one (next round's column indices loaded during the gathers, 2 CTAs per SM), the
+    same with the one-lane-per-row groups read from the sliced copy (the default; with
+    segments it runs as the pipelined one) and the plain one (4 CTAs per SM), each with its own
+    balanced split."""
     monkeypatch.setenv("PC_BIN_SPMV", loop)
     A = powerlaw
     x, info, binned, nseg = _solve(pc, A, 32, "on", segs=segs, want_segs=True)
@@ -138,7 +140,7 @@ def test_both_row_loops_match_oracle(pc, powerlaw, segs, loop, monkeypatch):
     assert abs(info["iterations"] - r["iterations"]) <= 1
 
 
-@pytest.mark.parametrize("loop", ["pipe", "plain"])
+@pytest.mark.parametrize("loop", ["sliced", "pipe", "plain"])
 def test_both_row_loops_on_a_stencil(pc, loop, monkeypatch):
     monkeypatch.setenv("PC_BIN_SPMV", loop)
     A = W.diffusion3d(24, 2.0)
@@ -146,3 +148,21 @@ def test_both_row_loops_on_a_stencil(pc, loop, monkeypatch):
     assert binned
     r = oracle.pcg(A, W.rhs(A.n, 0), 8, 1e-10)
     assert np.linalg.norm(x - r["x"]) <= 1e-10 * np.linalg.norm(r["x"])
+
+
+@pytest.mark.parametrize("vals", [np.float64, np.float32])
+def test_sliced_copy_gives_the_pipelined_loop_bit_for_bit(pc, vals, monkeypatch):
+    """The sliced copy only moves the one-lane-per-row groups' entries (entry k of the group's
+    32 rows contiguous, padded to the group's longest row): same products in the same order,
+    so the same iterates as the pipelined CSR walk.  30,001 rows: the last group is ragged."""
+    A = W.powerlaw_spd(n=30001, seed=7, w_max=1999, cap=2000, dtype=vals)
+    out = {}
+    for loop in ("pipe", "sliced"):
+        monkeypatch.setenv("PC_BIN_SPMV", loop)
+        x, info, binned = _solve(pc, A, 32, "on", prec="fp32")
+        assert binned and info["status_name"] == "ok"
+        out[loop] = (x, info["iterations"])
+    assert out["pipe"][1] == out["sliced"][1]
+    assert np.array_equal(out["pipe"][0], out["sliced"][0])
+    res = np.linalg.norm(W.rhs(A.n, 0) - oracle.spmv(A, out["sliced"][0])) / np.linalg.norm(W.rhs(A.n, 0))
+    assert res <= 1e-10

@@ -97,7 +97,7 @@ def test_invalid_arguments(tmp_path):
     with pytest.raises(pc.PcError) as ei:
         pc.tune_set(16, "fp32", 1000, 7000, dict(SHAPE, ring_stages=1))
     assert ei.value.name == "invalid_arg"
-    for bad in (dict(SHAPE, spmv_ctas_per_sm=9), dict(SHAPE, bin_pipe=2), dict(SHAPE, ring_stages=5),
+    for bad in (dict(SHAPE, spmv_ctas_per_sm=9), dict(SHAPE, bin_pipe=3), dict(SHAPE, ring_stages=5),
                 dict(SHAPE, fuse_update=3), dict(SHAPE, fuse_update=-1)):
         with pytest.raises(pc.PcError):
             pc.tune_set(16, "fp32", 1000, 7000, bad)
