@@ -519,7 +519,9 @@ typedef struct {
                                  from a sliced copy built at the first solve (entry k of the
                                  group's 32 rows contiguous; 8 or 12 bytes per entry of those
                                  rows, padded to each group's longest row); with column
-                                 segments 2 runs as 1                                         */
+                                 segments 2 runs as 1.  Natural row order: 2 walks a sliced
+                                 copy of all rows (groups of 32 consecutive rows; only when no
+                                 row exceeds 64 entries), any other value the CSR (default)   */
   int32_t fuse_update;        /* x += alpha p and p = z + beta p: 0 default (1 with FP64
                                  factors, 2 otherwise), 1 fused into the warp-ring
                                  preconditioner kernel (x updated unit by unit as it goes; p
@@ -534,8 +536,9 @@ typedef struct {
 /* pc_autotune - kernel-shape autotuner of the single-system solve.  Sets up a handle for A
  * (block_size, prec), then for each candidate shape (natural row order: SpMV CTAs per SM
  * {2, 3, 4, 6, 8} x ring stages {2, 3, 4}; binned: row loop {plain, pipelined, sliced} x ring stages;
- * each with the default update, then the best of them with the other update: fused or a
- * separate kernel)
+ * each with the default update; then the best of them with the other update, fused or a
+ * separate kernel, and in natural order with the other row walk, CSR or sliced copy, each
+ * kept only when at least 1% faster)
  * runs `iterations` CG iterations twice (right-hand side of ones, tolerance 0) and times the
  * second run with CUDA events; max_trials > 0 caps the candidates before that last trial.  The fastest shape is
  * recorded for A's key (block size, precision, ceil(log2 n), round(log2(nnz / n)), SM count

@@ -339,7 +339,100 @@ __device__ __forceinline__ void cg_rows_pipe(const CgArgs& a, const VT* __restri
   }
 }
 
-template <typename VT, int MODE, bool BIN, bool PIPE = false>
+// cg_rows_pipe over a sliced copy of the matrix (a.bin.scol with a.bin.perm null): the 32 rows
+// of a warp are one group of 32 consecutive rows, whose slab holds entry k of its row l at
+// 32 k + l, padded to the group's longest row and ending at sincl[group].  The rows' lengths
+// still come from the row pointers; every load of column indices and values then reads one
+// contiguous run per warp.  Same products in the same order as cg_rows_pipe.
+template <typename VT, typename FIN>
+__device__ __forceinline__ void cg_rows_sliced(const CgArgs& a, const double* __restrict__ x,
+                                               const double* __restrict__ w, FIN fin) {
+  const int64_t n = a.lay.n;
+  const int64_t S = (int64_t)gridDim.x * blockDim.x;
+  const int32_t* __restrict__ sc = a.bin.scol;
+  const VT* __restrict__ sv = reinterpret_cast<const VT*>(a.bin.sval);
+  const int64_t* __restrict__ si = a.bin.sincl;
+  const int lane = threadIdx.x & 31;
+  int64_t base = (int64_t)blockIdx.x * blockDim.x;
+  if (base >= n) return;
+  // the row's range, and its group's slab end (lanes past n take the last group's: every lane
+  // of a warp addresses the same slab)
+  auto row_range = [&](int64_t b, int32_t& s, int32_t& e, int64_t& so) {
+    const int64_t r = b + threadIdx.x;
+    s = 0;
+    e = 0;
+    if (r < n) {
+      s = __ldg(a.rp + r);
+      e = __ldg(a.rp + r + 1);
+    }
+    so = __ldg(si + (min(r, n - 1) >> 5));
+  };
+  // slab entry t of this lane's row (t clamped to the group's longest row gm; gm > 0)
+  auto slot = [&](int64_t so, int32_t gm, int t) { return so - 32ll * gm + 32ll * min(t, gm - 1) + lane; };
+  int32_t s0, e0, s1, e1;
+  int64_t o0, o1;
+  row_range(base, s0, e0, o0);
+  row_range(base + S, s1, e1, o1);
+  int32_t m0 = __reduce_max_sync(FULL, e0 - s0);
+  int32_t c[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) c[t] = m0 > 0 ? __ldg(sc + slot(o0, m0, t)) : 0;
+  for (; base < n; base += S) {
+    const int64_t row = base + threadIdx.x;
+    const bool valid = row < n;
+    const int32_t cnt = e0 - s0;
+    const int32_t wmax = m0;   // warp-uniform
+    VT v[8];
+    double xv[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      v[t] = wmax > 0 ? __ldg(sv + slot(o0, wmax, t)) : VT(0);
+      xv[t] = __ldg(x + c[t]);
+    }
+    const double wr = valid ? __ldg(w + row) : 0.0;
+    int32_t s2, e2;
+    int64_t o2;
+    row_range(base + 2 * S, s2, e2, o2);
+    const int32_t m1 = __reduce_max_sync(FULL, e1 - s1);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) c[t] = m1 > 0 ? __ldg(sc + slot(o1, m1, t)) : 0;
+    double sum = 0.0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      if (t < wmax) {
+        const double pr = fma(from_ft(v[t]), xv[t], sum);
+        sum = t < cnt ? pr : sum;
+      }
+    }
+    for (int32_t k0 = 8; k0 < wmax; k0 += 8) {
+      int32_t cc[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        cc[t] = __ldg(sc + slot(o0, wmax, k0 + t));
+        v[t] = __ldg(sv + slot(o0, wmax, k0 + t));
+      }
+#pragma unroll
+      for (int t = 0; t < 8; ++t) xv[t] = __ldg(x + cc[t]);
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        if (k0 + t < wmax) {
+          const double pr = fma(from_ft(v[t]), xv[t], sum);
+          sum = k0 + t < cnt ? pr : sum;
+        }
+      }
+    }
+    if (valid) fin(row, sum, wr);
+    s0 = s1;
+    e0 = e1;
+    o0 = o1;
+    m0 = m1;
+    s1 = s2;
+    e1 = e2;
+    o1 = o2;
+  }
+}
+
+template <typename VT, int MODE, bool BIN, bool PIPE = false, bool SL = false>
 __device__ __forceinline__ void cg_spmv_body(const CgArgs& a, double* sm, int* is_last_p) {
   int& is_last = *is_last_p;
   CgScalars* S = a.s;
@@ -473,7 +566,7 @@ __device__ __forceinline__ void cg_spmv_body(const CgArgs& a, double* sm, int* i
     }
   } else {
     // the epilogue's vector entry (p_i, or b_i) is loaded with the row's values
-    cg_rows_pipe<VT>(a, va, X, MODE == 1 ? a.p : a.b, [&](int64_t r_, double v_, double w_) {
+    auto fin = [&](int64_t r_, double v_, double w_) {
       if (MODE == 1) {
         a.q[r_] = v_;
         acc = fma(w_, v_, acc);
@@ -482,7 +575,9 @@ __device__ __forceinline__ void cg_spmv_body(const CgArgs& a, double* sm, int* i
         a.r[r_] = ri;
         acc = MODE == 0 ? fma(w_, w_, acc) : fma(ri, ri, acc);
       }
-    });
+    };
+    if constexpr (SL) cg_rows_sliced<VT>(a, X, MODE == 1 ? a.p : a.b, fin);
+    else cg_rows_pipe<VT>(a, va, X, MODE == 1 ? a.p : a.b, fin);
   }
   double v[1] = {acc};
   if (!cg_last_cta<1>(v, a.part, &S->cnt[MODE == 2 ? 2 : 0], sm, &is_last)) return;
@@ -510,11 +605,11 @@ __device__ __forceinline__ void cg_spmv_body(const CgArgs& a, double* sm, int* i
 // Natural order.  The pipelined row walk keeps two rows' loads live: up to 64 registers, 4 CTAs
 // per SM (the grid is capped there too: fewer, longer thread walks measured faster than a full
 // 8 CTAs per SM).
-template <typename VT, int MODE>
+template <typename VT, int MODE, bool SL = false>
 __global__ void __launch_bounds__(256, 4) cg_spmv_kernel(const CgArgs a) {
   __shared__ double sm[32];
   __shared__ int is_last;
-  cg_spmv_body<VT, MODE, false>(a, sm, &is_last);
+  cg_spmv_body<VT, MODE, false, false, SL>(a, sm, &is_last);
 }
 
 template <typename VT, int MODE>
@@ -545,6 +640,7 @@ static void launch_spmv_mode(int grid, cudaStream_t st, const CgArgs& a) {
   // the binned grid must match the split: one warp per work item
   if (a.bin.perm && a.bin.pipe) cg_spmv_bin_pipe_kernel<VT, MODE><<<cg_spmv_bin_warps(true) / 8, 256, 0, st>>>(a);
   else if (a.bin.perm) cg_spmv_bin_kernel<VT, MODE><<<cg_spmv_bin_warps(false) / 8, 256, 0, st>>>(a);
+  else if (a.bin.scol) cg_spmv_kernel<VT, MODE, true><<<grid, 256, 0, st>>>(a);   // natural order, sliced copy
   else cg_spmv_kernel<VT, MODE><<<grid, 256, 0, st>>>(a);
 }
 

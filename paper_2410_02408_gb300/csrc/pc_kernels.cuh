@@ -187,6 +187,7 @@ struct CgBinned {
   // Sliced copy of the one-lane-per-row groups (null: none; used with nseg 1 and the
   // pipelined loop): group g (longest row gmax[g] <= 64) holds 32 * gmax[g] entries ending at
   // sincl[g], entry k of the row at position 32 g + l at 32 k + l, padded past the row's end.
+  // With perm null (natural order) the groups are 32 consecutive rows, each with its slab.
   const int32_t* scol;
   const void* sval;        // VT, as the CSR values
   const int64_t* sincl;    // [ceil(n/32)] inclusive prefix of the slab sizes
@@ -233,6 +234,9 @@ cudaError_t row_seg_bounds(int64_t n, const int32_t* rp, const int32_t* ci, cons
 // [ceil(n/32)]; step 2 fills scol / sval (sincl's last entry of each, VT = float when
 // val_f32) from the whole-row bounds bnd (nseg 1): padding entries get column 0 and value 0.
 cudaError_t row_sliced_sizes(int64_t n, const int32_t* gmax, int64_t* sincl, cudaStream_t st);
+// Natural order: gmax[g] = the longest of rows 32 g .. 32 g + 31, and *dmax (device int,
+// zeroed by the caller) their maximum.  The fill then takes bnd = rp, stride = 1.
+cudaError_t row_natural_gmax(int64_t n, const int32_t* rp, int32_t* gmax, int* dmax, cudaStream_t st);
 cudaError_t row_sliced_fill(int64_t n, const int32_t* bnd, int64_t stride, const int32_t* ci, const void* va,
                             bool val_f32, const int32_t* gmax, const int64_t* sincl, int32_t* scol, void* sval,
                             cudaStream_t st);

@@ -366,4 +366,26 @@ cudaError_t row_sliced_fill(int64_t n, const int32_t* bnd, int64_t stride, const
   return cudaGetLastError();
 }
 
+// Longest row of each group of 32 consecutive rows (one warp per group) and their maximum.
+__global__ void natural_gmax_kernel(int64_t n, const int32_t* __restrict__ rp, int32_t* __restrict__ gmax,
+                                    int* dmax) {
+  const int lane = threadIdx.x & 31;
+  const int64_t m = (n + 31) / 32;
+  int mine = 0;
+  for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < m;
+       g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t row = g * 32 + lane;
+    const int32_t len = row < n ? __ldg(rp + row + 1) - __ldg(rp + row) : 0;
+    const int32_t gm = __reduce_max_sync(FULL, len);
+    if (lane == 0) gmax[g] = gm;
+    mine = gm > mine ? gm : mine;
+  }
+  if (lane == 0 && mine) atomicMax(dmax, mine);
+}
+
+cudaError_t row_natural_gmax(int64_t n, const int32_t* rp, int32_t* gmax, int* dmax, cudaStream_t st) {
+  natural_gmax_kernel<<<(unsigned)group_grid(n), 256, 0, st>>>(n, rp, gmax, dmax);
+  return cudaGetLastError();
+}
+
 }  // namespace pc

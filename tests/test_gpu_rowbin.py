@@ -166,3 +166,38 @@ def test_sliced_copy_gives_the_pipelined_loop_bit_for_bit(pc, vals, monkeypatch)
     assert np.array_equal(out["pipe"][0], out["sliced"][0])
     res = np.linalg.norm(W.rhs(A.n, 0) - oracle.spmv(A, out["sliced"][0])) / np.linalg.norm(W.rhs(A.n, 0))
     assert res <= 1e-10
+
+
+NATURAL_CASES = {
+    "diffusion23": lambda: W.diffusion3d(23, 2.0),                  # ragged: 12,167 rows
+    "poisson63": lambda: W.poisson2d(63),
+    "rows_to_64": lambda: W.powerlaw_spd(n=20001, seed=3, w_max=60, cap=64, dtype=np.float32),
+}
+
+
+@pytest.mark.parametrize("name", sorted(NATURAL_CASES))
+def test_natural_sliced_copy_gives_the_csr_walk_bit_for_bit(pc, name, monkeypatch):
+    """Natural row order over the sliced copy (groups of 32 consecutive rows, entry k of each
+    row at 32 k + lane): same products in the same order as the CSR walk, so the same iterates;
+    rows of up to 64 entries take several rounds of 8."""
+    A = NATURAL_CASES[name]()
+    bs = 16 if name != "rows_to_64" else 32
+    out = {}
+    for walk in ("csr", "sliced"):
+        monkeypatch.setenv("PC_NAT_SPMV", walk)
+        x, info, binned = _solve(pc, A, bs, "off", prec="fp32")
+        assert not binned and info["status_name"] == "ok"
+        out[walk] = (x, info["iterations"])
+    assert out["csr"][1] == out["sliced"][1]
+    assert np.array_equal(out["csr"][0], out["sliced"][0])
+    b = W.rhs(A.n, 0)
+    assert np.linalg.norm(b - oracle.spmv(A, out["sliced"][0])) <= 1e-10 * np.linalg.norm(b)
+
+
+def test_natural_sliced_copy_needs_rows_of_at_most_64_entries(pc, powerlaw, monkeypatch):
+    # longer rows: no sliced copy, the CSR walk runs (same answer as the oracle)
+    monkeypatch.setenv("PC_NAT_SPMV", "sliced")
+    x, info, binned = _solve(pc, powerlaw, 32, "off")
+    assert not binned and info["status_name"] == "ok"
+    r = oracle.pcg(powerlaw, W.rhs(powerlaw.n, 0), 32, 1e-10)
+    assert np.linalg.norm(x - r["x"]) <= 1e-10 * np.linalg.norm(r["x"])
