@@ -233,31 +233,35 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# Sources that define the profiled CG SpMV kernel: its recorded DRAM traffic stays valid
-# while these files are unchanged.
+# Sources that define the profiled CG SpMV kernels: a recorded DRAM traffic stays valid while
+# these files are unchanged (the binned one also depends on the row order and sliced copy).
 SPMV_SOURCES = ("pc_cg_graph.cu", "pc_common.cuh", "pc_kernels.cuh", "pc_tma.cuh")
+BIN_SPMV_SOURCES = SPMV_SOURCES + ("pc_rowbin.cu",)
+TRAFFIC_PROFILES = {"diffusion3d": ("cg_spmv_kernel_diffusion3d_128.md", SPMV_SOURCES),
+                    "powerlaw_8m": ("cg_spmv_bin_pipe_kernel_powerlaw_8m.md", BIN_SPMV_SOURCES)}
 
 
-def kernel_source_hash():
+def kernel_source_hash(sources=SPMV_SOURCES):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2410_02408_gb300", "csrc")
-    for fn in SPMV_SOURCES:
+    for fn in sources:
         with open(os.path.join(csrc, fn), "rb") as f:
             h.update(fn.encode())
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(bs, prec):
-    """DRAM bytes per launch of the SpMV kernel from the committed ncu summary, or None if
-    absent or if the kernel sources changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", "cg_spmv_kernel_diffusion3d_128.md")
+def profiled_traffic(workload):
+    """DRAM bytes per launch of the workload's SpMV kernel from the committed ncu summary, or
+    None if absent or if the kernel's sources changed since it was taken."""
+    name, sources = TRAFFIC_PROFILES[workload]
+    path = os.path.join(ROOT, "profiles", name)
     try:
         txt = open(path).read()
     except OSError:
         return None
     m = re.search(r"kernel_source_hash:\s*(\w+)", txt)
-    if not m or m.group(1) != kernel_source_hash():
+    if not m or m.group(1) != kernel_source_hash(sources):
         return None
     m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     return float(m.group(1)) if m else None
@@ -561,7 +565,10 @@ def run_ours(args):
     peak, peak_kind = measured_hbm()
     _, b_it, _ = step_bytes(n, nnz, args.bs, args.prec, iters, vb)
     spmv_us, prec_us, upd_us, spmv_order = kernel_times(pc, Ad, bd, args.bs, args.prec, args)
-    traffic = profiled_traffic(args.bs, args.prec) if args.workload == "diffusion3d" else None
+    # the committed ncu summaries cover the 128^3 matrix at bs 16 and the 8M-row power-law matrix
+    profiled = ((args.workload == "diffusion3d" and args.n == 128 and args.bs == 16)
+                or (args.workload == "powerlaw_8m" and args.pl_n == 8_000_000))
+    traffic = profiled_traffic(args.workload) if profiled else None
     kname = ("cg_spmv_bin_pipe_kernel (binned rows; q = A p and p.q; one launch per CG iteration)"
              if spmv_order["binned"] else "cg_spmv_kernel (q = A p and p.q; one launch per CG iteration)")
     roofline, kernels = kernel_table(n, nnz, vb, args.bs, args.prec, spmv_us, prec_us, upd_us, peak, peak_kind,
@@ -1117,7 +1124,8 @@ def powerlaw_result(pc, args, steps, warmup):
     spmv_us, prec_us, upd_us, order = kernel_times(pc, Ad, bd, bs, args.prec, args)
     kname = ("cg_spmv_bin_pipe_kernel (binned rows; q = A p and p.q; one launch per CG iteration)"
              if order["binned"] else "cg_spmv_kernel (q = A p and p.q; one launch per CG iteration)")
-    roofline, kernels = kernel_table(n, nnz, vb, bs, args.prec, spmv_us, prec_us, upd_us, peak, peak_kind, None,
+    traffic = profiled_traffic("powerlaw_8m") if n == 8_000_000 and args.prec != "fp64" else None
+    roofline, kernels = kernel_table(n, nnz, vb, bs, args.prec, spmv_us, prec_us, upd_us, peak, peak_kind, traffic,
                                      kname, fused=order["fused_update"])
     info = infos[-1]
     res = {"metric": METRIC, "value": value, "unit": "GB/s", "ms_per_step": ms, "steps": steps, "warmup": warmup,
