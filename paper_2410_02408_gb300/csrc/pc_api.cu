@@ -580,7 +580,7 @@ static pc_status build_natural_sliced(pc_handle* h, cudaStream_t st) {
   int64_t total = 0;
   if (s == PC_OK && e == cudaSuccess && gmax_all >= 1 && gmax_all <= 64) {
     s = dalloc(&h->sincl, sizeof(int64_t) * (size_t)n_groups);
-    if (s == PC_OK) e = pc::row_sliced_sizes(n, h->gmax, h->sincl, st);
+    if (s == PC_OK) e = pc::row_sliced_sizes(n, h->gmax, h->sincl, pc::BIN_LANE_ROWS, st);
     if (s == PC_OK && e == cudaSuccess)
       e = cudaMemcpyAsync(&total, h->sincl + n_groups - 1, sizeof(total), cudaMemcpyDeviceToHost, st);
     if (s == PC_OK && e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -590,7 +590,7 @@ static pc_status build_natural_sliced(pc_handle* h, cudaStream_t st) {
       if (s == PC_OK) s = dalloc(&h->sval, vb * (size_t)(total > 0 ? total : 1));
       if (s == PC_OK)
         e = pc::row_sliced_fill(n, h->A.row_ptr, 1, h->A.col_idx, h->A.val, h->val_f32 != 0, h->gmax, h->sincl,
-                                h->scol, h->sval, st);
+                                pc::BIN_LANE_ROWS, h->scol, h->sval, st);
     }
   }
   if (s == PC_OK && e != cudaSuccess) s = from_cuda(e);
@@ -676,7 +676,11 @@ static pc_status choose_row_order(pc_handle* h, cudaStream_t st) {
   int64_t m_items = 0;
   int64_t* icost = nullptr;
   cudaError_t e = pc::row_bin_build(n, h->A.row_ptr, h->perm, st);
-  if (e == cudaSuccess) e = pc::row_bin_group_stats(n, h->A.row_ptr, h->perm, gscr, h->gmax, gscr + n_groups, st);
+  // the sliced copy (row loop 2, whole rows) serves longer one-lane-per-row groups
+  const bool sliced = h->bin_pipe == 2 && nseg == 1;
+  const int lane_max = sliced ? pc::BIN_SLICED_LANE_ROWS : pc::BIN_LANE_ROWS;
+  if (e == cudaSuccess)
+    e = pc::row_bin_group_stats(n, h->A.row_ptr, h->perm, gscr, h->gmax, gscr + n_groups, lane_max, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&m_items, gscr + 2 * n_groups - 1, sizeof(m_items), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -711,12 +715,12 @@ static pc_status choose_row_order(pc_handle* h, cudaStream_t st) {
     }
   }
   h->nseg = nseg;
-  if (h->bin_pipe == 2 && nseg == 1) {
+  if (sliced) {
     // sliced copy of the one-lane-per-row groups
     s = dalloc(&h->sincl, sizeof(int64_t) * (size_t)n_groups);
     int64_t total = 0;
     cudaError_t e2 = cudaSuccess;
-    if (s == PC_OK) e2 = pc::row_sliced_sizes(n, h->gmax, h->sincl, st);
+    if (s == PC_OK) e2 = pc::row_sliced_sizes(n, h->gmax, h->sincl, lane_max, st);
     if (s == PC_OK && e2 == cudaSuccess)
       e2 = cudaMemcpyAsync(&total, h->sincl + n_groups - 1, sizeof(total), cudaMemcpyDeviceToHost, st);
     if (s == PC_OK && e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
@@ -726,7 +730,7 @@ static pc_status choose_row_order(pc_handle* h, cudaStream_t st) {
       if (s == PC_OK) s = dalloc(&h->sval, vb * (size_t)(total > 0 ? total : 1));
       if (s == PC_OK)
         e2 = pc::row_sliced_fill(n, h->bnd, stride, h->A.col_idx, h->A.val, h->val_f32 != 0, h->gmax, h->sincl,
-                                 h->scol, h->sval, st);
+                                 lane_max, h->scol, h->sval, st);
     }
     if (s == PC_OK && e2 != cudaSuccess) s = from_cuda(e2);
     if (s != PC_OK) {

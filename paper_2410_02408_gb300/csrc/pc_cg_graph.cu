@@ -522,7 +522,7 @@ __device__ __forceinline__ void cg_spmv_body(const CgArgs& a, double* sm, int* i
           const bool valid = idx < n;
           const double w_c = (last && valid) ? __ldg(W + r_c) : 0.0;
           const int32_t s0 = s_c, cnt0 = c_c;
-          if (gm_c <= 64) {
+          if (gm_c <= (sliced ? BIN_SLICED_LANE_ROWS : BIN_LANE_ROWS)) {
             const double init = (!first && valid) ? __ldcg(B.spart + idx) : 0.0;
             const int32_t lim = __reduce_max_sync(FULL, cnt0);
             double v;

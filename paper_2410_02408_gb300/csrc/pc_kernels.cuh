@@ -185,7 +185,7 @@ struct CgBinned {
   int32_t nseg;            // column segments swept one after another (1: whole rows)
   int32_t pipe;            // 1: pipelined row loop (gsplit sized for cg_spmv_bin_warps(true))
   // Sliced copy of the one-lane-per-row groups (null: none; used with nseg 1 and the
-  // pipelined loop): group g (longest row gmax[g] <= 64) holds 32 * gmax[g] entries ending at
+  // pipelined loop): group g (gmax[g] <= BIN_SLICED_LANE_ROWS) holds 32 * gmax[g] entries ending at
   // sincl[g], entry k of the row at position 32 g + l at 32 k + l, padded past the row's end.
   // With perm null (natural order) the groups are 32 consecutive rows, each with its slab.
   const int32_t* scol;
@@ -208,6 +208,12 @@ bool cg_graph_fused(const void* g);
 
 // Row binning (pc_rowbin.cu): rows sorted by length inside windows of ROWBIN_W rows.
 constexpr int ROWBIN_W = 2048;
+// Longest row of a 32-row group that the binned SpMV walks one lane per row: 64 over the CSR,
+// 256 over the sliced copy (whose loads stay coalesced and whose rounds are pipelined, so a
+// longer group costs rounds, not scattered loads); longer groups take 8 lanes per row (CSR
+// walk, up to 256) or are split into single-row items (above 256).
+constexpr int BIN_LANE_ROWS = 64;
+constexpr int BIN_SLICED_LANE_ROWS = 256;
 // d_out[0] += sum over 32-row groups of 32 * (longest row in the group).
 cudaError_t row_bin_waste(int64_t n, const int32_t* rp, unsigned long long* d_out, cudaStream_t st);
 // perm[n]: the rows of every window, stably sorted by length bucket.
@@ -219,7 +225,7 @@ cudaError_t row_bin_build(int64_t n, const int32_t* rp, int32_t* perm, cudaStrea
 // items (items [m_items]: g >= 0 for group g, -(pos + 1) for the row at binned position pos), their
 // cost prefix (icost, int64 [m_items]) and each warp's first item (isplit [n_warps + 1]).
 cudaError_t row_bin_group_stats(int64_t n, const int32_t* rp, const int32_t* perm, int64_t* gcost, int32_t* gmax,
-                                int64_t* gcount_incl, cudaStream_t st);
+                                int64_t* gcount_incl, int lane_max, cudaStream_t st);
 cudaError_t row_bin_items(int64_t n, const int32_t* rp, const int32_t* perm, const int32_t* gmax, const int64_t* gcost,
                           const int64_t* gcount_incl, int64_t m_items, int n_warps, int32_t* items, int64_t* icost,
                           int32_t* isplit, cudaStream_t st);
@@ -230,16 +236,16 @@ cudaError_t row_bin_items(int64_t n, const int32_t* rp, const int32_t* perm, con
 cudaError_t row_seg_bounds(int64_t n, const int32_t* rp, const int32_t* ci, const int32_t* perm, int nseg,
                            int64_t seg_cols, int64_t stride, int32_t* bnd, int* unsorted, cudaStream_t st);
 // Sliced copy of the one-lane-per-row groups (CgBinned::scol): step 1 writes the inclusive
-// prefix of the slab sizes (32 * gmax[g] entries for gmax[g] <= 64, else 0) to sincl
+// prefix of the slab sizes (32 * gmax[g] entries for gmax[g] <= lane_max, else 0) to sincl
 // [ceil(n/32)]; step 2 fills scol / sval (sincl's last entry of each, VT = float when
 // val_f32) from the whole-row bounds bnd (nseg 1): padding entries get column 0 and value 0.
-cudaError_t row_sliced_sizes(int64_t n, const int32_t* gmax, int64_t* sincl, cudaStream_t st);
+cudaError_t row_sliced_sizes(int64_t n, const int32_t* gmax, int64_t* sincl, int lane_max, cudaStream_t st);
 // Natural order: gmax[g] = the longest of rows 32 g .. 32 g + 31, and *dmax (device int,
 // zeroed by the caller) their maximum.  The fill then takes bnd = rp, stride = 1.
 cudaError_t row_natural_gmax(int64_t n, const int32_t* rp, int32_t* gmax, int* dmax, cudaStream_t st);
 cudaError_t row_sliced_fill(int64_t n, const int32_t* bnd, int64_t stride, const int32_t* ci, const void* va,
-                            bool val_f32, const int32_t* gmax, const int64_t* sincl, int32_t* scol, void* sval,
-                            cudaStream_t st);
+                            bool val_f32, const int32_t* gmax, const int64_t* sincl, int lane_max, int32_t* scol,
+                            void* sval, cudaStream_t st);
 // Warps of the binned SpMV grid (the number of work items of its split), plain or pipelined.
 int cg_spmv_bin_warps(bool pipe);
 void cg_graph_destroy(void* g);

@@ -107,7 +107,8 @@ __global__ void __launch_bounds__(ROWBIN_THREADS) row_bin_kernel(int64_t n, cons
 // they address), so the cost of an item is the length of its chain, weighted by the 256 entries
 // a warp of short rows handles per round, or its FP64 lane-operations if that is larger, plus a
 // per-item overhead.  Item kinds, as the SpMV walks them:
-//   a 32-row group whose longest row has <= 64 entries: one lane per row, 8 entries per lane and
+//   a 32-row group whose longest row has <= lane_max entries (64, or 256 over the sliced copy):
+//     one lane per row, 8 entries per lane and
 //     round: 1 + 2 ceil(max/8) round trips (the bounds load, then two per round);
 //   a group whose longest row has <= 256 entries: 8 lanes per row, 4 rows per pass, 8 passes,
 //     each taking the rounds of its longest row (64 entries per round);
@@ -123,7 +124,7 @@ __device__ __forceinline__ int64_t item_cost(int64_t ops, int64_t trips) {
 // whole-group item (unused for split groups).
 __global__ void group_stats_kernel(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ perm,
                                    int64_t* __restrict__ gcost, int32_t* __restrict__ gmax,
-                                   int64_t* __restrict__ gcount) {
+                                   int64_t* __restrict__ gcount, int lane_max) {
   const int lane = threadIdx.x & 31;
   const int64_t n_groups = (n + 31) / 32;
   for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < n_groups;
@@ -141,7 +142,7 @@ __global__ void group_stats_kernel(int64_t n, const int32_t* __restrict__ rp, co
     pm = max(pm, __shfl_xor_sync(FULL, pm, 2));
     const int32_t pass_trips = __reduce_add_sync(FULL, (lane & 3) == 0 ? 2 * ((pm + 63) / 64) : 0);
     int64_t ops, trips;
-    if (m <= 64) {
+    if (m <= lane_max) {
       ops = 32ll * m;
       trips = 1 + 2ll * ((m + 7) / 8);
     } else {
@@ -236,9 +237,9 @@ static int64_t group_grid(int64_t n) {
 }
 
 cudaError_t row_bin_group_stats(int64_t n, const int32_t* rp, const int32_t* perm, int64_t* gcost, int32_t* gmax,
-                                int64_t* gcount_incl, cudaStream_t st) {
+                                int64_t* gcount_incl, int lane_max, cudaStream_t st) {
   const int64_t m = (n + 31) / 32;
-  group_stats_kernel<<<(unsigned)group_grid(n), 256, 0, st>>>(n, rp, perm, gcost, gmax, gcount_incl);
+  group_stats_kernel<<<(unsigned)group_grid(n), 256, 0, st>>>(n, rp, perm, gcost, gmax, gcount_incl, lane_max);
   cost_scan_kernel<<<1, 1024, 0, st>>>(m, gcount_incl);
   return cudaGetLastError();
 }
@@ -309,20 +310,21 @@ cudaError_t row_bin_build(int64_t n, const int32_t* rp, int32_t* perm, cudaStrea
 
 
 // Sliced copy of the one-lane-per-row groups.  Slab sizes: 32 * gmax[g] entries for groups
-// whose longest row has at most 64 entries, 0 for the others (they keep the CSR walk).
-__global__ void sliced_size_kernel(int64_t m, const int32_t* __restrict__ gmax, int64_t* __restrict__ size) {
+// whose longest row has at most lane_max entries, 0 for the others (they keep the CSR walk).
+__global__ void sliced_size_kernel(int64_t m, const int32_t* __restrict__ gmax, int64_t* __restrict__ size,
+                                   int lane_max) {
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < m; g += (int64_t)gridDim.x * blockDim.x) {
     const int32_t gm = __ldg(gmax + g);
-    size[g] = gm <= 64 ? 32ll * gm : 0;
+    size[g] = gm <= lane_max ? 32ll * gm : 0;
   }
 }
 
-cudaError_t row_sliced_sizes(int64_t n, const int32_t* gmax, int64_t* sincl, cudaStream_t st) {
+cudaError_t row_sliced_sizes(int64_t n, const int32_t* gmax, int64_t* sincl, int lane_max, cudaStream_t st) {
   const int64_t m = (n + 31) / 32;
   int64_t grid = (m + 255) / 256;
   if (grid > (int64_t)device_sms() * 16) grid = (int64_t)device_sms() * 16;
   if (grid < 1) grid = 1;
-  sliced_size_kernel<<<(unsigned)grid, 256, 0, st>>>(m, gmax, sincl);
+  sliced_size_kernel<<<(unsigned)grid, 256, 0, st>>>(m, gmax, sincl, lane_max);
   cost_scan_kernel<<<1, 1024, 0, st>>>(m, sincl);
   return cudaGetLastError();
 }
@@ -334,13 +336,13 @@ template <typename VT>
 __global__ void sliced_fill_kernel(int64_t n, const int32_t* __restrict__ bnd, int64_t stride,
                                    const int32_t* __restrict__ ci, const VT* __restrict__ va,
                                    const int32_t* __restrict__ gmax, const int64_t* __restrict__ sincl,
-                                   int32_t* __restrict__ scol, VT* __restrict__ sval) {
+                                   int lane_max, int32_t* __restrict__ scol, VT* __restrict__ sval) {
   const int lane = threadIdx.x & 31;
   const int64_t m = (n + 31) / 32;
   for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < m;
        g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const int32_t gm = __ldg(gmax + g);
-    if (gm > 64 || gm <= 0) continue;   // warp-uniform
+    if (gm > lane_max || gm <= 0) continue;   // warp-uniform
     const int64_t base = __ldg(sincl + g) - 32ll * gm;
     const int64_t pos = g * 32 + lane;
     const int32_t lo = pos < n ? __ldg(bnd + pos) : 0;
@@ -354,15 +356,15 @@ __global__ void sliced_fill_kernel(int64_t n, const int32_t* __restrict__ bnd, i
 }
 
 cudaError_t row_sliced_fill(int64_t n, const int32_t* bnd, int64_t stride, const int32_t* ci, const void* va,
-                            bool val_f32, const int32_t* gmax, const int64_t* sincl, int32_t* scol, void* sval,
-                            cudaStream_t st) {
+                            bool val_f32, const int32_t* gmax, const int64_t* sincl, int lane_max, int32_t* scol,
+                            void* sval, cudaStream_t st) {
   const unsigned grid = (unsigned)group_grid(n);
   if (val_f32)
     sliced_fill_kernel<float><<<grid, 256, 0, st>>>(n, bnd, stride, ci, static_cast<const float*>(va), gmax, sincl,
-                                                    scol, static_cast<float*>(sval));
+                                                    lane_max, scol, static_cast<float*>(sval));
   else
     sliced_fill_kernel<double><<<grid, 256, 0, st>>>(n, bnd, stride, ci, static_cast<const double*>(va), gmax,
-                                                     sincl, scol, static_cast<double*>(sval));
+                                                     sincl, lane_max, scol, static_cast<double*>(sval));
   return cudaGetLastError();
 }
 

@@ -152,10 +152,11 @@ def test_both_row_loops_on_a_stencil(pc, loop, monkeypatch):
 
 @pytest.mark.parametrize("vals", [np.float64, np.float32])
 def test_sliced_copy_gives_the_pipelined_loop_bit_for_bit(pc, vals, monkeypatch):
-    """The sliced copy only moves the one-lane-per-row groups' entries (entry k of the group's
-    32 rows contiguous, padded to the group's longest row): same products in the same order,
-    so the same iterates as the pipelined CSR walk.  30,001 rows: the last group is ragged."""
-    A = W.powerlaw_spd(n=30001, seed=7, w_max=1999, cap=2000, dtype=vals)
+    """With rows of at most 64 entries both loops walk every group one lane per row; the sliced
+    copy only moves the entries (entry k of the group's 32 rows contiguous, padded to the
+    group's longest row): same products in the same order, so the same iterates.  30,001 rows:
+    the last group is ragged."""
+    A = W.powerlaw_spd(n=30001, seed=7, w_max=60, cap=64, dtype=vals)
     out = {}
     for loop in ("pipe", "sliced"):
         monkeypatch.setenv("PC_BIN_SPMV", loop)
@@ -166,6 +167,24 @@ def test_sliced_copy_gives_the_pipelined_loop_bit_for_bit(pc, vals, monkeypatch)
     assert np.array_equal(out["pipe"][0], out["sliced"][0])
     res = np.linalg.norm(W.rhs(A.n, 0) - oracle.spmv(A, out["sliced"][0])) / np.linalg.norm(W.rhs(A.n, 0))
     assert res <= 1e-10
+
+
+def test_sliced_copy_walks_rows_up_to_256_entries_one_lane_per_row(pc, monkeypatch):
+    """Over the sliced copy, groups whose rows have 65-256 entries are also walked one lane per
+    row (one FMA chain per row in storage order, as the oracle sums), where the CSR walk puts 8
+    lanes on a row and combines their partial sums: the iterates then agree to rounding, and
+    each matches the oracle's solution."""
+    A = W.powerlaw_spd(n=30001, seed=7, w_max=1999, cap=256, dtype=np.float64)
+    r = oracle.pcg(A, W.rhs(A.n, 0), 32, 1e-10)
+    out = {}
+    for loop in ("pipe", "sliced"):
+        monkeypatch.setenv("PC_BIN_SPMV", loop)
+        x, info, binned = _solve(pc, A, 32, "on")
+        assert binned and info["status_name"] == "ok"
+        assert abs(info["iterations"] - r["iterations"]) <= 1
+        assert np.linalg.norm(x - r["x"]) <= 1e-10 * np.linalg.norm(r["x"])
+        out[loop] = x
+    assert np.linalg.norm(out["pipe"] - out["sliced"]) <= 1e-12 * np.linalg.norm(out["pipe"])
 
 
 NATURAL_CASES = {
