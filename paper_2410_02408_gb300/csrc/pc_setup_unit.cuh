@@ -74,13 +74,14 @@ __host__ __device__ inline size_t setup_unit_smem(const Layout& L, size_t ft_byt
 }
 
 // rp/ci/va: CSR whose row r of this layout is rp[r]..rp[r+1]-1 and whose column indices
-// are relative to the same origin as the rows.  Mu (and Lu unless null) point at this
-// unit's slots of the factor arrays.  A pivot <= tol * (largest diagonal entry of its
-// block) makes the block count as failed: atomicMin(failed, block index); the pivot is
-// then replaced by 1 so that the factor stays finite.  FT is the arithmetic type (and the
-// type of the shared-memory tiles), ST the stored type (FP64 arithmetic can be stored as
-// FP32 factors).  TC (FP32 only): M^{-1} = L^{-T} L^{-1} is formed on the tensor cores from
-// TF32-rounded L^{-1} with FP32 accumulation (gram_tf32) instead of FP32 dot products.
+// are relative to the same origin as the rows, strictly increasing within each row.  Mu
+// (and Lu unless null) point at this unit's slots of the factor arrays.  A pivot <= tol *
+// (largest diagonal entry of its block) makes the block count as failed: atomicMin(failed,
+// block index); the pivot is then replaced by 1 so that the factor stays finite.  FT is the
+// arithmetic type (and the type of the shared-memory tiles), ST the stored type (FP64
+// arithmetic can be stored as FP32 factors).  TC (FP32 only): M^{-1} = L^{-T} L^{-1} is formed
+// on the tensor cores from TF32-rounded L^{-1} with FP32 accumulation (gram_tf32) instead of
+// FP32 dot products.
 template <typename VT, typename FT, typename ST = FT, bool TC = false>
 __device__ __forceinline__ void setup_unit(const Layout& L, int64_t u, const int32_t* __restrict__ rp,
                                            const int32_t* __restrict__ ci, const VT* __restrict__ va, double tol,
@@ -101,11 +102,21 @@ __device__ __forceinline__ void setup_unit(const Layout& L, int64_t u, const int
     const int i = rho % bs;
     const int64_t row = urow0 + rho;
     if (row < L.n) {
+      // the row's columns increase (every entry point checks the CSR first): binary-search
+      // the first column of the block, then copy until its last, so that a long row costs
+      // O(log length + bs) instead of its length
       const int64_t bstart = row - i;
-      const int32_t e0 = rp[row], e1 = rp[row + 1];
-      for (int32_t e = e0; e < e1; ++e) {
+      const int32_t e1 = rp[row + 1];
+      int32_t lo = rp[row], hi = e1;
+      while (lo < hi) {
+        const int32_t mid = lo + ((hi - lo) >> 1);
+        if ((int64_t)ci[mid] < bstart) lo = mid + 1;
+        else hi = mid;
+      }
+      for (int32_t e = lo; e < e1; ++e) {
         const int64_t c = ci[e];
-        if (c >= bstart && c < bstart + bs) As[rho * ld + (int)(c - bstart)] = (FT)va[e];
+        if (c >= bstart + bs) break;
+        As[rho * ld + (int)(c - bstart)] = (FT)va[e];
       }
     } else {
       As[rho * ld + i] = FT(1);
