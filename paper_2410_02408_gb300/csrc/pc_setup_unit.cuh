@@ -73,27 +73,20 @@ __host__ __device__ inline size_t setup_unit_smem(const Layout& L, size_t ft_byt
   return (size_t)2 * L.U * (L.bs + 1) * ft_bytes;
 }
 
-// rp/ci/va: CSR whose row r of this layout is rp[r]..rp[r+1]-1 and whose column indices
-// are relative to the same origin as the rows, strictly increasing within each row.  Mu
-// (and Lu unless null) point at this unit's slots of the factor arrays.  A pivot <= tol *
-// (largest diagonal entry of its block) makes the block count as failed: atomicMin(failed,
-// block index); the pivot is then replaced by 1 so that the factor stays finite.  FT is the
-// arithmetic type (and the type of the shared-memory tiles), ST the stored type (FP64
-// arithmetic can be stored as FP32 factors).  TC (FP32 only): M^{-1} = L^{-T} L^{-1} is formed
-// on the tensor cores from TF32-rounded L^{-1} with FP32 accumulation (gram_tf32) instead of
-// FP32 dot products.
-template <typename VT, typename FT, typename ST = FT, bool TC = false>
-__device__ __forceinline__ void setup_unit(const Layout& L, int64_t u, const int32_t* __restrict__ rp,
-                                           const int32_t* __restrict__ ci, const VT* __restrict__ va, double tol,
-                                           ST* __restrict__ Mu, ST* __restrict__ Lu, FT* As, FT* Xs, int lane,
-                                           unsigned long long* failed) {
+// Zero the unit's tiles (As, and Xs unless null), then extract its diagonal blocks from CSR
+// into As (dense rows, stride bs + 1; the identity on rows past n).  The row's columns
+// increase (every entry point checks the CSR first): binary-search the first column of the
+// block, then copy until its last, so that a long row costs O(log length + bs) instead of its
+// length.
+template <typename VT, typename FT>
+__device__ __forceinline__ void extract_unit(const Layout& L, int64_t urow0, const int32_t* __restrict__ rp,
+                                             const int32_t* __restrict__ ci, const VT* __restrict__ va, FT* As,
+                                             FT* Xs, int lane) {
   const int bs = L.bs;
   const int ld = bs + 1;
-  const int64_t urow0 = u * L.U;
-  // ---- zero, then extract (identity on rows past n)
   for (int t = lane; t < L.U * ld; t += 32) {
     As[t] = FT(0);
-    Xs[t] = FT(0);
+    if (Xs) Xs[t] = FT(0);
   }
   __syncwarp();
   for (int s = 0; s < L.S; ++s) {
@@ -102,9 +95,6 @@ __device__ __forceinline__ void setup_unit(const Layout& L, int64_t u, const int
     const int i = rho % bs;
     const int64_t row = urow0 + rho;
     if (row < L.n) {
-      // the row's columns increase (every entry point checks the CSR first): binary-search
-      // the first column of the block, then copy until its last, so that a long row costs
-      // O(log length + bs) instead of its length
       const int64_t bstart = row - i;
       const int32_t e1 = rp[row + 1];
       int32_t lo = rp[row], hi = e1;
@@ -123,6 +113,26 @@ __device__ __forceinline__ void setup_unit(const Layout& L, int64_t u, const int
     }
   }
   __syncwarp();
+}
+
+// rp/ci/va: CSR whose row r of this layout is rp[r]..rp[r+1]-1 and whose column indices
+// are relative to the same origin as the rows, strictly increasing within each row.  Mu
+// (and Lu unless null) point at this unit's slots of the factor arrays.  A pivot <= tol *
+// (largest diagonal entry of its block) makes the block count as failed: atomicMin(failed,
+// block index); the pivot is then replaced by 1 so that the factor stays finite.  FT is the
+// arithmetic type (and the type of the shared-memory tiles), ST the stored type (FP64
+// arithmetic can be stored as FP32 factors).  TC (FP32 only): M^{-1} = L^{-T} L^{-1} is formed
+// on the tensor cores from TF32-rounded L^{-1} with FP32 accumulation (gram_tf32) instead of
+// FP32 dot products.
+template <typename VT, typename FT, typename ST = FT, bool TC = false>
+__device__ __forceinline__ void setup_unit(const Layout& L, int64_t u, const int32_t* __restrict__ rp,
+                                           const int32_t* __restrict__ ci, const VT* __restrict__ va, double tol,
+                                           ST* __restrict__ Mu, ST* __restrict__ Lu, FT* As, FT* Xs, int lane,
+                                           unsigned long long* failed) {
+  const int bs = L.bs;
+  const int ld = bs + 1;
+  const int64_t urow0 = u * L.U;
+  extract_unit<VT, FT>(L, urow0, rp, ci, va, As, Xs, lane);
   // ---- per-block pivot scale: max diagonal entry of the block
   FT dmax[2] = {FT(0), FT(0)};
   for (int s = 0; s < L.S; ++s) {
