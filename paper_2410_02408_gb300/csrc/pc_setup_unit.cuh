@@ -177,6 +177,7 @@ __device__ __forceinline__ void setup_unit(const Layout& L, int64_t u, const int
       if (i > j) {
         const int gb = rho - i;
         const FT lij = As[rho * ld + j];
+#pragma unroll 4
         for (int k = j + 1; k <= i; ++k) As[rho * ld + k] = fma(-lij, As[(gb + k) * ld + j], As[rho * ld + k]);
       }
     }
@@ -190,6 +191,7 @@ __device__ __forceinline__ void setup_unit(const Layout& L, int64_t u, const int
     const int gb = rho - c;
     for (int i = c; i < bs; ++i) {
       FT acc = (i == c) ? FT(1) : FT(0);
+#pragma unroll 4
       for (int k = c; k < i; ++k) acc = fma(-As[(gb + i) * ld + k], Xs[(gb + k) * ld + c], acc);
       Xs[(gb + i) * ld + c] = acc / As[(gb + i) * ld + i];
     }
@@ -218,6 +220,7 @@ __device__ __forceinline__ void setup_unit(const Layout& L, int64_t u, const int
           acc = As[(gb + min(i, j)) * ld + max(i, j)];
         } else {
           const int m0 = i > j ? i : j;
+#pragma unroll 4
           for (int m = m0; m < bs; ++m) acc = fma(Xs[(gb + m) * ld + i], Xs[(gb + m) * ld + j], acc);
         }
       }
