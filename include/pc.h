@@ -19,7 +19,11 @@
  *     pc_apply / pcg_solve_h calls, so the caller keeps that CSR alive and unchanged
  *     until pc_destroy.
  *   - Handles and their workspaces are owned by the library: created by pc_setup,
- *     released by pc_destroy.
+ *     released by pc_destroy.  Their device memory comes from a memory pool of the library
+ *     (one per device) that keeps released memory for later handles rather than returning
+ *     it to the driver (an allocation that would fail first trims the pool); pc_destroy
+ *     waits for the device, as cudaFree does, and must run with the handle's device
+ *     current.
  *   - stream is a cudaStream_t passed as void* (NULL = legacy default stream).  Work is
  *     enqueued on it; calls that report a device-side status (setup, solve, kappa)
  *     synchronise the stream before returning.

@@ -113,11 +113,74 @@ pc_status from_cuda(cudaError_t e) {
     if (_e != cudaSuccess) return from_cuda(_e); \
   } while (0)
 
+// Device memory of the single-system handles comes from a memory pool of this library, one
+// per device, that keeps freed memory for later allocations instead of returning it to the
+// driver: a handle per solve (the one-call API) then costs no page mapping and unmapping
+// (3.2 ms of destroy alone on an 8M-row matrix with raw cudaMalloc / cudaFree).  The
+// semantics stay those of cudaMalloc / cudaFree: dalloc returns memory ready for any stream
+// (its stream-ordered allocation, on a private stream, is synchronized), dfree first waits
+// for the device (as cudaFree does) so that no kernel still reads the memory.  An allocation
+// that fails trims the pool's cached memory and tries once more.  Without pool support the
+// raw calls are used.
+struct LibPool {
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t stream = nullptr;
+  bool ok = false;
+};
+constexpr int kMaxDevices = 64;
+LibPool g_pools[kMaxDevices];
+std::mutex g_pool_mu;
+
+LibPool* lib_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  LibPool& lp = g_pools[dev];
+  if (!lp.ok && !lp.pool) {
+    int supported = 0;
+    cudaDeviceGetAttribute(&supported, cudaDevAttrMemoryPoolsSupported, dev);
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaError_t e = supported ? cudaMemPoolCreate(&lp.pool, &props) : cudaErrorNotSupported;
+    if (e == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;   // freed memory stays in the pool
+      e = cudaMemPoolSetAttribute(lp.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&lp.stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      lp.pool = reinterpret_cast<cudaMemPool_t>(1);   // tried: raw allocations from now on
+      return nullptr;
+    }
+    lp.ok = true;
+  }
+  return lp.ok ? &lp : nullptr;
+}
+
 template <typename T>
 pc_status dalloc(T** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc((void**)p, bytes);
+  LibPool* lp = lib_pool();
+  cudaError_t e;
+  if (lp) {
+    e = cudaMallocFromPoolAsync((void**)p, bytes, lp->pool, lp->stream);
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      cudaStreamSynchronize(lp->stream);
+      cudaMemPoolTrimTo(lp->pool, 0);
+      e = cudaMallocFromPoolAsync((void**)p, bytes, lp->pool, lp->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lp->stream);
+  } else {
+    e = cudaMalloc((void**)p, bytes);
+  }
   if (e != cudaSuccess) {
     *p = nullptr;
     cudaGetLastError();
@@ -127,7 +190,14 @@ pc_status dalloc(T** p, size_t bytes) {
 }
 
 void dfree(void* p) {
-  if (p) cudaFree(p);
+  if (!p) return;
+  LibPool* lp = lib_pool();
+  if (lp) {
+    cudaDeviceSynchronize();
+    cudaFreeAsync(p, lp->stream);
+  } else {
+    cudaFree(p);
+  }
 }
 
 bool csr_ok(const pc_csr* A) {
