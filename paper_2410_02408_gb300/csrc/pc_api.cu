@@ -650,7 +650,8 @@ static pc_status build_natural_sliced(pc_handle* h, cudaStream_t st) {
   int64_t total = 0;
   if (s == PC_OK && e == cudaSuccess && gmax_all >= 1 && gmax_all <= 64) {
     s = dalloc(&h->sincl, sizeof(int64_t) * (size_t)n_groups);
-    if (s == PC_OK) e = pc::row_sliced_sizes(n, h->gmax, h->sincl, pc::BIN_LANE_ROWS, st);
+    if (s == PC_OK)
+      e = pc::row_sliced_sizes(n, h->gmax, h->sincl, pc::BIN_LANE_ROWS, reinterpret_cast<int64_t*>(h->tmp), st);
     if (s == PC_OK && e == cudaSuccess)
       e = cudaMemcpyAsync(&total, h->sincl + n_groups - 1, sizeof(total), cudaMemcpyDeviceToHost, st);
     if (s == PC_OK && e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -750,7 +751,8 @@ static pc_status choose_row_order(pc_handle* h, cudaStream_t st) {
   const bool sliced = h->bin_pipe == 2 && nseg == 1;
   const int lane_max = sliced ? pc::BIN_SLICED_LANE_ROWS : pc::BIN_LANE_ROWS;
   if (e == cudaSuccess)
-    e = pc::row_bin_group_stats(n, h->A.row_ptr, h->perm, gscr, h->gmax, gscr + n_groups, lane_max, st);
+    e = pc::row_bin_group_stats(n, h->A.row_ptr, h->perm, gscr, h->gmax, gscr + n_groups, lane_max,
+                                reinterpret_cast<int64_t*>(h->tmp), st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&m_items, gscr + 2 * n_groups - 1, sizeof(m_items), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -760,7 +762,7 @@ static pc_status choose_row_order(pc_handle* h, cudaStream_t st) {
     if (s == PC_OK) s = dalloc(&icost, sizeof(int64_t) * (size_t)m_items);
     if (s == PC_OK)
       e = pc::row_bin_items(n, h->A.row_ptr, h->perm, h->gmax, gscr, gscr + n_groups, m_items, n_warps, h->items,
-                            icost, h->gsplit, st);
+                            icost, h->gsplit, reinterpret_cast<int64_t*>(h->tmp), st);
     if (s == PC_OK && e == cudaSuccess) e = cudaStreamSynchronize(st);
   }
   dfree(icost);
@@ -790,7 +792,7 @@ static pc_status choose_row_order(pc_handle* h, cudaStream_t st) {
     s = dalloc(&h->sincl, sizeof(int64_t) * (size_t)n_groups);
     int64_t total = 0;
     cudaError_t e2 = cudaSuccess;
-    if (s == PC_OK) e2 = pc::row_sliced_sizes(n, h->gmax, h->sincl, lane_max, st);
+    if (s == PC_OK) e2 = pc::row_sliced_sizes(n, h->gmax, h->sincl, lane_max, reinterpret_cast<int64_t*>(h->tmp), st);
     if (s == PC_OK && e2 == cudaSuccess)
       e2 = cudaMemcpyAsync(&total, h->sincl + n_groups - 1, sizeof(total), cudaMemcpyDeviceToHost, st);
     if (s == PC_OK && e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);

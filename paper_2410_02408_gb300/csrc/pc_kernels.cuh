@@ -224,11 +224,13 @@ cudaError_t row_bin_build(int64_t n, const int32_t* rp, int32_t* perm, cudaStrea
 // counts (gcount_incl, int64 [ceil(n/32)]; its last entry is the number of items).  Step 2: the
 // items (items [m_items]: g >= 0 for group g, -(pos + 1) for the row at binned position pos), their
 // cost prefix (icost, int64 [m_items]) and each warp's first item (isplit [n_warps + 1]).
+// scan_ws: scratch of ceil(m / 8192) int64 for the prefix sums over m entries (m: groups or
+// items).
 cudaError_t row_bin_group_stats(int64_t n, const int32_t* rp, const int32_t* perm, int64_t* gcost, int32_t* gmax,
-                                int64_t* gcount_incl, int lane_max, cudaStream_t st);
+                                int64_t* gcount_incl, int lane_max, int64_t* scan_ws, cudaStream_t st);
 cudaError_t row_bin_items(int64_t n, const int32_t* rp, const int32_t* perm, const int32_t* gmax, const int64_t* gcost,
                           const int64_t* gcount_incl, int64_t m_items, int n_warps, int32_t* items, int64_t* icost,
-                          int32_t* isplit, cudaStream_t st);
+                          int32_t* isplit, int64_t* scan_ws, cudaStream_t st);
 // Column segments of the binned SpMV: for the row at binned position idx, bnd[s * stride + idx]
 // is its first entry (s = 0), one past its last entry (s = nseg), or its first entry with
 // column >= s * seg_cols (0 < s < nseg; columns sorted within the row).  *unsorted (device
@@ -239,7 +241,8 @@ cudaError_t row_seg_bounds(int64_t n, const int32_t* rp, const int32_t* ci, cons
 // prefix of the slab sizes (32 * gmax[g] entries for gmax[g] <= lane_max, else 0) to sincl
 // [ceil(n/32)]; step 2 fills scol / sval (sincl's last entry of each, VT = float when
 // val_f32) from the whole-row bounds bnd (nseg 1): padding entries get column 0 and value 0.
-cudaError_t row_sliced_sizes(int64_t n, const int32_t* gmax, int64_t* sincl, int lane_max, cudaStream_t st);
+cudaError_t row_sliced_sizes(int64_t n, const int32_t* gmax, int64_t* sincl, int lane_max, int64_t* scan_ws,
+                             cudaStream_t st);
 // Natural order: gmax[g] = the longest of rows 32 g .. 32 g + 31, and *dmax (device int,
 // zeroed by the caller) their maximum.  The fill then takes bnd = rp, stride = 1.
 cudaError_t row_natural_gmax(int64_t n, const int32_t* rp, int32_t* gmax, int* dmax, cudaStream_t st);

@@ -187,25 +187,95 @@ __global__ void item_fill_kernel(int64_t n, const int32_t* __restrict__ rp, cons
   }
 }
 
-// Inclusive prefix sum of cost[0..m) in place (one CTA of 1024 threads: each thread scans a
-// contiguous stretch, then the stretch totals are scanned).
-__global__ void __launch_bounds__(1024) cost_scan_kernel(int64_t m, int64_t* cost) {
-  __shared__ int64_t tot[1024];
-  const int64_t per = (m + 1023) / 1024;
-  const int64_t lo = threadIdx.x * per;
-  const int64_t hi = lo + per < m ? lo + per : m;
-  int64_t run = 0;
-  for (int64_t i = lo; i < hi; ++i) run += cost[i];
-  tot[threadIdx.x] = run;
+// Inclusive prefix sum of cost[0..m) in place, in three launches: per chunk of
+// SCAN_CHUNK entries its total (one CTA each), an exclusive scan of the chunk totals (one
+// CTA), then each chunk's scan from its offset (each thread a contiguous run of SCAN_PER
+// entries, the runs' totals scanned across the CTA).  Integer sums: exact in any order.
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_PER = 8;
+constexpr int64_t SCAN_CHUNK = (int64_t)SCAN_THREADS * SCAN_PER;
+
+// Exclusive scan of one value per thread across the CTA (SCAN_THREADS threads); *total gets
+// the sum.  ws: 33 int64 of shared memory.
+__device__ __forceinline__ int64_t cta_exclusive_scan(int64_t v, int64_t* ws, int64_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t t = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) ws[warp] = incl;
   __syncthreads();
-  if (threadIdx.x == 0)
-    for (int i = 1; i < 1024; ++i) tot[i] += tot[i - 1];
+  if (warp == 0) {
+    int64_t w = ws[lane];
+    int64_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t t = __shfl_up_sync(FULL, wi, o);
+      if (lane >= o) wi += t;
+    }
+    ws[lane] = wi - w;   // exclusive offset of each warp
+    if (lane == 31) ws[32] = wi;
+  }
   __syncthreads();
-  run = threadIdx.x ? tot[threadIdx.x - 1] : 0;
-  for (int64_t i = lo; i < hi; ++i) {
+  const int64_t r = ws[warp] + incl - v;
+  *total = ws[32];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) scan_chunk_totals(int64_t m, const int64_t* __restrict__ cost,
+                                                                  int64_t* __restrict__ totals) {
+  __shared__ int64_t ws[33];
+  const int64_t c0 = (int64_t)blockIdx.x * SCAN_CHUNK;
+  int64_t v = 0;
+  for (int64_t i = c0 + threadIdx.x; i < m && i < c0 + SCAN_CHUNK; i += SCAN_THREADS) v += cost[i];
+  int64_t tot;
+  cta_exclusive_scan(v, ws, &tot);
+  if (threadIdx.x == 0) totals[blockIdx.x] = tot;
+}
+
+// Exclusive scan of the nc chunk totals in place (one CTA; nc <= SCAN_THREADS * SCAN_PER).
+__global__ void __launch_bounds__(SCAN_THREADS) scan_totals(int64_t nc, int64_t* __restrict__ totals) {
+  __shared__ int64_t ws[33];
+  const int64_t lo = (int64_t)threadIdx.x * SCAN_PER;
+  int64_t v = 0;
+  for (int64_t i = lo; i < lo + SCAN_PER && i < nc; ++i) v += totals[i];
+  int64_t tot;
+  int64_t run = cta_exclusive_scan(v, ws, &tot);
+  for (int64_t i = lo; i < lo + SCAN_PER && i < nc; ++i) {
+    const int64_t t = totals[i];
+    totals[i] = run;
+    run += t;
+  }
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) scan_chunks(int64_t m, int64_t* __restrict__ cost,
+                                                            const int64_t* __restrict__ offsets) {
+  __shared__ int64_t ws[33];
+  const int64_t lo = (int64_t)blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_PER;
+  int64_t v = 0;
+  for (int64_t i = lo; i < lo + SCAN_PER && i < m; ++i) v += cost[i];
+  int64_t tot;
+  int64_t run = offsets[blockIdx.x] + cta_exclusive_scan(v, ws, &tot);
+  for (int64_t i = lo; i < lo + SCAN_PER && i < m; ++i) {
     run += cost[i];
     cost[i] = run;
   }
+}
+
+// Scratch the scan needs for m entries: one int64 per chunk.
+static int64_t scan_chunks_for(int64_t m) { return (m + SCAN_CHUNK - 1) / SCAN_CHUNK; }
+
+static cudaError_t inclusive_scan(int64_t m, int64_t* cost, int64_t* scratch, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  const int64_t nc = scan_chunks_for(m);
+  if (nc > SCAN_CHUNK) return cudaErrorInvalidValue;   // more than 2^26 entries: not needed here
+  scan_chunk_totals<<<(unsigned)nc, SCAN_THREADS, 0, st>>>(m, cost, scratch);
+  scan_totals<<<1, SCAN_THREADS, 0, st>>>(nc, scratch);
+  scan_chunks<<<(unsigned)nc, SCAN_THREADS, 0, st>>>(m, cost, scratch);
+  return cudaGetLastError();
 }
 
 // gsplit[w] = first item of warp w: the first item whose inclusive cost prefix exceeds
@@ -237,18 +307,20 @@ static int64_t group_grid(int64_t n) {
 }
 
 cudaError_t row_bin_group_stats(int64_t n, const int32_t* rp, const int32_t* perm, int64_t* gcost, int32_t* gmax,
-                                int64_t* gcount_incl, int lane_max, cudaStream_t st) {
+                                int64_t* gcount_incl, int lane_max, int64_t* scan_ws, cudaStream_t st) {
   const int64_t m = (n + 31) / 32;
   group_stats_kernel<<<(unsigned)group_grid(n), 256, 0, st>>>(n, rp, perm, gcost, gmax, gcount_incl, lane_max);
-  cost_scan_kernel<<<1, 1024, 0, st>>>(m, gcount_incl);
-  return cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
+  return e != cudaSuccess ? e : inclusive_scan(m, gcount_incl, scan_ws, st);
 }
 
 cudaError_t row_bin_items(int64_t n, const int32_t* rp, const int32_t* perm, const int32_t* gmax, const int64_t* gcost,
                           const int64_t* gcount_incl, int64_t m_items, int n_warps, int32_t* items, int64_t* icost,
-                          int32_t* isplit, cudaStream_t st) {
+                          int32_t* isplit, int64_t* scan_ws, cudaStream_t st) {
   item_fill_kernel<<<(unsigned)group_grid(n), 256, 0, st>>>(n, rp, perm, gmax, gcost, gcount_incl, items, icost);
-  cost_scan_kernel<<<1, 1024, 0, st>>>(m_items, icost);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = inclusive_scan(m_items, icost, scan_ws, st);
+  if (e != cudaSuccess) return e;
   group_split_kernel<<<(n_warps + 1 + 255) / 256, 256, 0, st>>>(m_items, icost, n_warps, isplit);
   return cudaGetLastError();
 }
@@ -319,14 +391,15 @@ __global__ void sliced_size_kernel(int64_t m, const int32_t* __restrict__ gmax, 
   }
 }
 
-cudaError_t row_sliced_sizes(int64_t n, const int32_t* gmax, int64_t* sincl, int lane_max, cudaStream_t st) {
+cudaError_t row_sliced_sizes(int64_t n, const int32_t* gmax, int64_t* sincl, int lane_max, int64_t* scan_ws,
+                             cudaStream_t st) {
   const int64_t m = (n + 31) / 32;
   int64_t grid = (m + 255) / 256;
   if (grid > (int64_t)device_sms() * 16) grid = (int64_t)device_sms() * 16;
   if (grid < 1) grid = 1;
   sliced_size_kernel<<<(unsigned)grid, 256, 0, st>>>(m, gmax, sincl, lane_max);
-  cost_scan_kernel<<<1, 1024, 0, st>>>(m, sincl);
-  return cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
+  return e != cudaSuccess ? e : inclusive_scan(m, sincl, scan_ws, st);
 }
 
 // One warp per group with a slab: lane l copies the row at binned position 32 g + l, entry k to
