@@ -405,3 +405,30 @@ def test_iterate_after_k_steps_matches_oracle(pc, engine, k):
     assert r["iterations"] == k
     xr = x.cpu().numpy()
     assert np.linalg.norm(xr - r["x"]) <= 1e-12 * np.linalg.norm(r["x"])
+
+
+def test_handles_reuse_the_library_memory_pool(pc):
+    # a handle's device memory goes back to the library's pool on destroy and serves the next
+    # handle: after the first setup / solve / destroy, repeating them takes no more device memory
+    import torch
+
+    A = W.diffusion3d(48, 2.0)
+    b = torch.from_numpy(W.rhs(A.n, 0)).cuda()
+    Ad = pc.csr(A)
+
+    def cycle():
+        H = pc.setup(Ad, 16, prec="fp32")
+        x, info = H.pcg(b, tol=1e-10)
+        H.destroy()
+        assert info["status"] == 0
+        return x
+
+    x0 = cycle()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        x = cycle()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 >= free0 - (8 << 20)   # allow torch's own small allocations
+    assert torch.equal(x, x0)
