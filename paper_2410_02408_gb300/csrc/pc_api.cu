@@ -125,7 +125,8 @@ pc_status from_cuda(cudaError_t e) {
 struct LibPool {
   cudaMemPool_t pool = nullptr;
   cudaStream_t stream = nullptr;
-  bool ok = false;
+  bool tried = false;   // creation attempted (once per device)
+  bool ok = false;      // pool and stream usable
 };
 constexpr int kMaxDevices = 64;
 LibPool g_pools[kMaxDevices];
@@ -139,7 +140,8 @@ LibPool* lib_pool() {
   }
   std::lock_guard<std::mutex> lk(g_pool_mu);
   LibPool& lp = g_pools[dev];
-  if (!lp.ok && !lp.pool) {
+  if (!lp.tried) {
+    lp.tried = true;
     int supported = 0;
     cudaDeviceGetAttribute(&supported, cudaDevAttrMemoryPoolsSupported, dev);
     cudaMemPoolProps props;
@@ -154,8 +156,7 @@ LibPool* lib_pool() {
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&lp.stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
-      cudaGetLastError();
-      lp.pool = reinterpret_cast<cudaMemPool_t>(1);   // tried: raw allocations from now on
+      cudaGetLastError();   // raw allocations from now on
       return nullptr;
     }
     lp.ok = true;
